@@ -1,0 +1,320 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle.
+
+Each test checks the oracle against a closed form, an independent formula
+(L'Huilier's theorem, signed ray crossings), a geometric invariant or brute
+force, so that a dropped term, a wrong sign or index or a transposed operand in
+oracle.c fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import zef_synth as zs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FOUR_PI = 4.0 * math.pi
+
+
+# ---------------------------------------------------------------- helpers
+def lhuilier(p, a, b, c):
+    """Solid angle of triangle (a, b, c) seen from p by L'Huilier's theorem on
+    the spherical excess, signed by the orientation of (a - p, b - p, c - p)."""
+    u = [x - p for x in (a, b, c)]
+    u = [x / np.linalg.norm(x) for x in u]
+
+    def ang(x, y):
+        return math.atan2(np.linalg.norm(np.cross(x, y)), float(np.dot(x, y)))
+
+    A, B, C = ang(u[1], u[2]), ang(u[0], u[2]), ang(u[0], u[1])
+    s = 0.5 * (A + B + C)
+    t = math.tan(s / 2) * math.tan((s - A) / 2) * math.tan((s - B) / 2) * math.tan((s - C) / 2)
+    E = 4.0 * math.atan(math.sqrt(max(t, 0.0)))
+    sign = np.sign(np.dot(u[0], np.cross(u[1], u[2])))
+    return sign * E
+
+
+def ray_winding(points, verts, tris, direction=(0.5773502691896258 + 1e-3 * math.pi,
+                                                0.5773502691896258 - 1e-3 * math.e,
+                                                0.5773502691896258)):
+    """Signed count of crossings of the ray p + s d (s > 0) with the oriented
+    triangles (Moller-Trumbore).  For a closed outward surface this is the
+    winding number: 1 inside, 0 outside."""
+    d = np.asarray(direction, dtype=np.float64)
+    d /= np.linalg.norm(d)
+    v = verts.astype(np.float64)
+    a, b, c = v[tris[:, 0]], v[tris[:, 1]], v[tris[:, 2]]
+    e1, e2 = b - a, c - a
+    pv = np.cross(d, e2)
+    det = np.einsum("ij,ij->i", e1, pv)
+    nrm = np.cross(e1, e2)
+    orient = -np.sign(np.einsum("ij,j->i", nrm, d))   # +1 if the ray leaves through the face
+    out = np.zeros(len(points), dtype=np.int64)
+    P = np.asarray(points, dtype=np.float64)
+    for s in range(0, len(P), 256):
+        p = P[s:s + 256]
+        tv = p[:, None, :] - a[None, :, :]
+        uu = np.einsum("pij,ij->pi", tv, pv) / det
+        qv = np.cross(tv, e1[None])
+        vv = np.einsum("j,pij->pi", d, qv) / det
+        tt = np.einsum("pij,ij->pi", qv, e2) / det
+        hit = (uu >= 0) & (vv >= 0) & (uu + vv <= 1) & (tt > 0)
+        out[s:s + 256] = -(hit * orient[None, :]).sum(1)
+    return out
+
+
+def load_golden():
+    with open(os.path.join(HERE, "golden", "closed_forms.json")) as f:
+        return json.load(f)["cases"]
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("case", load_golden(), ids=lambda c: c["name"])
+def test_closed_forms(oracle_mod, case):
+    terms = oracle_mod.triangle_terms(case["point"], case["verts"], case["tris"])
+    assert abs(terms.sum() - case["expected_total"]) < 1e-12
+    if "expected_each" in case:
+        np.testing.assert_allclose(terms, case["expected_each"], rtol=0, atol=1e-12)
+
+
+def test_lhuilier_random_triangles(oracle_mod):
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        tri = rng.uniform(-1, 1, size=(3, 3))
+        p = rng.uniform(-2, 2, size=3)
+        if min(np.linalg.norm(tri - p, axis=1)) < 0.05:
+            continue
+        got = oracle_mod.triangle_terms(p, tri, [[0, 1, 2]])[0]
+        want = lhuilier(p, *tri)
+        assert abs(got - want) < 1e-9, (got, want)
+
+
+def test_far_small_triangle(oracle_mod):
+    # Omega ~ area * cos(theta) / r^2 with relative error O((h / r)^2)
+    rng = np.random.default_rng(3)
+    for r in (10.0, 100.0, 1000.0):
+        h = 1.0
+        tri = np.array([[0, 0, 0], [h, 0, 0], [0, h, 0]], dtype=np.float64)
+        cen = tri.mean(0)
+        dirv = rng.standard_normal(3)
+        dirv /= np.linalg.norm(dirv)
+        p = cen + r * dirv
+        area = 0.5 * h * h
+        cos_t = np.dot(np.array([0, 0, 1.0]), cen - p) / r   # normal +z, R = centroid - p
+        approx = area * cos_t / r ** 2
+        got = oracle_mod.triangle_terms(p, tri, [[0, 1, 2]])[0]
+        assert abs(got - approx) <= 2.0 * (h / r) ** 2 * abs(area / r ** 2) + 1e-15
+
+
+def test_unit_sphere_inside_outside(oracle_mod):
+    w = zs.config0()
+    s = w.surfaces[0]
+    v = s.verts.astype(np.float64)
+    a, b, c = v[s.tris[:, 0]], v[s.tris[:, 1]], v[s.tris[:, 2]]
+    n = np.cross(b - a, c - a)
+    inr = np.min(np.abs(np.einsum("ij,ij->i", n, a)) / np.linalg.norm(n, axis=1))
+    outr = np.max(np.linalg.norm(v, axis=1))
+    r = np.linalg.norm(w.points.astype(np.float64), axis=1)
+    om = oracle_mod.solid_angle(w.points, s.verts, s.tris)
+    ins = r < inr
+    out = r > outr
+    assert ins.sum() > 1000 and out.sum() > 10000
+    np.testing.assert_allclose(om[ins], FOUR_PI, atol=1e-11)
+    np.testing.assert_allclose(om[out], 0.0, atol=1e-11)
+
+
+def test_winding_invariant_head_surfaces(oracle_mod):
+    w = zs.config1(npts_limit=0)
+    pts = zs.lattice_centroids(100, 2.0, (-100.0, -100.0, -100.0))
+    pts = pts[zs.sample_rows(pts, 4000, seed=5)]
+    for s in w.surfaces:
+        om = oracle_mod.solid_angle(pts, s.verts, s.tris)
+        k = np.round(om / FOUR_PI)
+        assert np.all(np.abs(om - FOUR_PI * k) < 1e-9)
+        assert set(np.unique(k)) <= {0.0, 1.0}
+        assert (k == 1).sum() > 100
+
+
+def test_orientation_flip_negates(oracle_mod):
+    s = zs.config0().surfaces[0]
+    pts = np.random.default_rng(1).uniform(-1.4, 1.4, size=(500, 3))
+    a = oracle_mod.solid_angle(pts, s.verts, s.tris)
+    b = oracle_mod.solid_angle(pts, s.verts, s.tris[:, [0, 2, 1]])
+    np.testing.assert_allclose(b, -a, rtol=0, atol=1e-12)
+
+
+def test_translation_invariance(oracle_mod):
+    s = zs.config0().surfaces[0]
+    pts = np.random.default_rng(2).uniform(-1.4, 1.4, size=(300, 3))
+    shift = np.array([3.25, -7.5, 11.125])
+    a = oracle_mod.solid_angle(pts, s.verts, s.tris)
+    b = oracle_mod.solid_angle(pts + shift, s.verts.astype(np.float64) + shift, s.tris)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-11)
+
+
+def test_triangle_order_only_changes_rounding(oracle_mod):
+    s = zs.config0().surfaces[0]
+    pts = np.random.default_rng(4).uniform(-1.4, 1.4, size=(300, 3))
+    perm = np.random.default_rng(5).permutation(s.tris.shape[0])
+    a = oracle_mod.solid_angle(pts, s.verts, s.tris)
+    b = oracle_mod.solid_angle(pts, s.verts, s.tris[perm])
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("shape", ["sphere", "torus", "ellipsoid"])
+def test_ray_parity_brute_force(oracle_mod, shape):
+    rng = np.random.default_rng(11)
+    if shape == "sphere":
+        s = zs.config0().surfaces[0]
+        v, t = s.verts, s.tris
+        pts = zs.config0().points[::3]
+    elif shape == "torus":
+        v, t = zs.torus(10.0, 3.0, 48, 24, seed=1, amp=0.8)
+        pts = rng.uniform(-14, 14, size=(6000, 3)).astype(np.float32)
+    else:
+        v, t = zs.perturbed_ellipsoid(10, (9.0, 7.0, 5.0), amp=1.0, seed=9)
+        pts = rng.uniform(-10, 10, size=(6000, 3)).astype(np.float32)
+    om = oracle_mod.solid_angle(pts, v, t)
+    wind = ray_winding(pts, v, t)
+    k = np.round(om / FOUR_PI).astype(np.int64)
+    assert np.array_equal(k, wind)
+    assert np.array_equal(oracle_mod.inside(om), wind == 1)
+    assert 0 < (wind == 1).sum() < len(pts)
+
+
+# ---------------------------------------------------------------- priority
+def _sphere(radius, freq, cid):
+    u, t = zs.geodesic_sphere(freq)
+    v = (u * radius).astype(np.float32)
+    return zs.Surface(cid, f"r{radius}", v, t.astype(np.int32))
+
+
+def test_priority_nested_ary_spheres(oracle_mod):
+    # Ary geometry radii 87 / 92 / 100 (Sec. 2.4); innermost first
+    surfs = [_sphere(87.0, 12, 3), _sphere(92.0, 12, 2), _sphere(100.0, 12, 1)]
+    rng = np.random.default_rng(8)
+    dirs = rng.standard_normal((3000, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    radii = rng.uniform(0, 110, size=3000)
+    pts = (dirs * radii[:, None]).astype(np.float32)
+    lab, om = oracle_mod.label_points(pts, surfs, [3, 2, 1])
+    r = np.linalg.norm(pts.astype(np.float64), axis=1)
+
+    def inr(s):
+        v = s.verts.astype(np.float64)
+        a, b, c = v[s.tris[:, 0]], v[s.tris[:, 1]], v[s.tris[:, 2]]
+        n = np.cross(b - a, c - a)
+        return np.min(np.abs(np.einsum("ij,ij->i", n, a)) / np.linalg.norm(n, axis=1))
+
+    bounds = [(inr(s), float(np.max(np.linalg.norm(s.verts.astype(np.float64), axis=1))))
+              for s in surfs]
+    analytic = np.full(len(pts), -9)
+    analytic[r > bounds[2][1]] = 0
+    analytic[(r < bounds[2][0]) & (r > bounds[1][1])] = 1
+    analytic[(r < bounds[1][0]) & (r > bounds[0][1])] = 2
+    analytic[r < bounds[0][0]] = 3
+    known = analytic != -9
+    assert known.sum() > 2500
+    assert np.array_equal(lab[known], analytic[known])
+    # points in the faceting shells: ray parity decides
+    amb = ~known
+    want = np.zeros(len(pts), dtype=np.int32)
+    for cid, s in zip([3, 2, 1], surfs):
+        w = ray_winding(pts[amb], s.verts, s.tris)
+        sub = want[amb]
+        sub[(sub == 0) & (w == 1)] = cid
+        want[amb] = sub
+    assert np.array_equal(lab[amb], want[amb])
+
+
+@pytest.mark.parametrize("order", [[1, 2], [2, 1]])
+def test_priority_intersecting_spheres(oracle_mod, order):
+    a = _sphere(10.0, 10, 1)
+    b = _sphere(10.0, 10, 2)
+    b.verts = (b.verts.astype(np.float64) + np.array([12.0, 0, 0])).astype(np.float32)
+    rng = np.random.default_rng(3)
+    lens = np.column_stack([rng.uniform(4.0, 8.0, 500), rng.uniform(-2, 2, 500),
+                            rng.uniform(-2, 2, 500)]).astype(np.float32)
+    only_a = np.column_stack([rng.uniform(-8, -2, 300), rng.uniform(-2, 2, 300),
+                              rng.uniform(-2, 2, 300)]).astype(np.float32)
+    outside = np.column_stack([rng.uniform(30, 40, 300), rng.uniform(-2, 2, 300),
+                               rng.uniform(-2, 2, 300)]).astype(np.float32)
+    lab, _ = oracle_mod.label_points(np.concatenate([lens, only_a, outside]), [a, b], order)
+    assert np.all(lab[:500] == order[0])
+    assert np.all(lab[500:800] == 1)
+    assert np.all(lab[800:] == 0)
+
+
+def test_nonfinite_points_get_minus_one(oracle_mod):
+    s = zs.config0().surfaces[0]
+    pts = np.array([[0, 0, 0], [np.nan, 0, 0], [0, np.inf, 0], [5, 5, 5]], dtype=np.float32)
+    lab, om = oracle_mod.label_points(pts, [s], [1])
+    assert lab.tolist() == [1, -1, -1, 0]
+
+
+# ---------------------------------------------------------------- refinement
+def _vol(nodes, t):
+    a, b, c, d = (nodes[t[i]].astype(np.float64) for i in range(4))
+    return float(np.dot(b - a, np.cross(c - a, d - a))) / 6.0
+
+
+def test_refine_single_tet_one_to_eight():
+    from oracle import refine
+    nodes = np.array([[0, 0, 0], [4, 0, 0], [0, 4, 0], [0, 0, 4], [9, 9, 9]], dtype=np.float32)
+    tets = np.array([[0, 1, 2, 3], [1, 2, 3, 4]], dtype=np.int32)
+    # node 0 differs from the rest: only tet 0 straddles a label boundary
+    new_nodes, out, flagged = refine.refine_level(nodes, tets, np.array([1, 2, 2, 2, 2]))
+    assert flagged.tolist() == [0]
+    assert new_nodes.shape == (6, 3)
+    assert out.shape == (2 + 7, 4)
+    allnodes = np.concatenate([nodes, new_nodes])
+    pv = _vol(nodes, tets[0])
+    kids = [out[0]] + [out[2 + i] for i in range(7)]
+    vols = [_vol(allnodes, k) for k in kids]
+    np.testing.assert_allclose(vols, pv / 8.0, rtol=1e-12)
+    assert np.array_equal(out[1], tets[1])
+    # every child vertex is a corner or an edge midpoint of the parent
+    mids = {tuple(((nodes[i].astype(float) + nodes[j]) / 2)) for i in range(4) for j in range(i + 1, 4)}
+    for k in kids:
+        for q in k:
+            pt = tuple(allnodes[q].astype(float))
+            assert q < 4 or pt in mids
+
+
+def test_refine_plane_split_flag_count(oracle_mod):
+    from oracle import refine
+    c = 0.37
+    L = 50.0
+    box_v = np.array([[-L, -L, -L], [c, -L, -L], [c, L, -L], [-L, L, -L],
+                      [-L, -L, L], [c, -L, L], [c, L, L], [-L, L, L]], dtype=np.float32)
+    box_t = np.array([[0, 3, 2], [0, 2, 1], [4, 5, 6], [4, 6, 7], [0, 1, 5], [0, 5, 4],
+                      [2, 3, 7], [2, 7, 6], [1, 2, 6], [1, 6, 5], [0, 4, 7], [0, 7, 3]],
+                     dtype=np.int32)
+    surf = zs.Surface(1, "box", box_v, box_t)
+    nodes, tets = zs.lattice_5tet(6, 1.0, (-3.0, -3.0, -3.0))
+    n2, t2, lab, per = refine.refine_and_relabel(nodes, tets, [surf], [1], levels=2)
+    # brute force of level 1 from coordinates alone
+    x = nodes[:, 0].astype(np.float64)[tets]
+    want = int(((x.min(1) < c) & (x.max(1) > c)).sum())
+    assert per[0]["flagged"] == want
+    assert np.array_equal(lab, np.where(n2[:, 0] < c, 1, 0))
+    # conservation of volume
+    vol0 = sum(_vol(nodes, t) for t in tets)
+    vol2 = sum(_vol(n2, t) for t in t2)
+    assert abs(vol0 - vol2) < 1e-9 * vol0
+    assert min(_vol(n2, t) for t in t2) > 0
+    # level 2 flags exactly the level-1 children that still straddle the plane
+    assert per[1]["flagged"] > 0
+
+
+def test_refine_incremental_labels_equal_full_relabel(oracle_mod):
+    from oracle import refine
+    s = zs.config0().surfaces[0]
+    nodes, tets = zs.lattice_5tet(5, 0.6, (-1.5, -1.5, -1.5))
+    n2, t2, lab, per = refine.refine_and_relabel(nodes, tets, [s], [1], levels=2)
+    full, _ = oracle_mod.label_points(n2, [s], [1])
+    assert np.array_equal(lab, full)
+    assert per[0]["new_nodes"] > 0
