@@ -1,0 +1,330 @@
+"""Benchmark of the solid-angle labeling hot path on GB300.
+
+One step = one zef_label_points call over the whole workload (binning, exact
+bounding-box culling, FP32 strip kernel, FP64 re-evaluation, priority
+resolve), inputs resident in HBM.  Default workload: the three-layer head
+(brain / skull / scalp perturbed ellipsoids, 122,880 triangles) against the
+5,000,000 tet centroids of a 2 mm lattice over a 200 mm cube.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "point×triangle solid-angle pairs/s on 1 GB300, FP32+rescue vs FP64; labels=oracle"
+# Algorithmic FP32 work of one point x triangle pair of the Van Oosterom-Strackee
+# formula as written (FMA = 2 flops): R_k 9, three norms 18 (incl. sqrt), triple
+# product 14, denominator 23, atan2 20 (division, degree-7 minimax, reflections),
+# accumulation 1.
+FLOPS_PER_PAIR = 85
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--points", type=int, default=0, help="limit points (0 = full workload)")
+    ap.add_argument("--fp64-points", type=int, default=100_000,
+                    help="points of the FP32+rescue vs plain-FP64 comparison")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = auto)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shape", default="", help="threads,ppt override")
+    return ap.parse_args()
+
+
+def workload(cfg: int, limit: int):
+    import zef_synth as zs
+    if cfg == 0:
+        w = zs.config0()
+    elif cfg == 1:
+        w = zs.config1(npts_limit=limit or None)
+    elif cfg == 2:
+        w = zs.config2(npts_limit=limit or None)
+    elif cfg == 4:
+        w = zs.config4(npts_limit=limit or None)
+    else:
+        raise SystemExit("bench workloads: configs 0, 1, 2, 4")
+    if limit and w.points.shape[0] > limit:
+        w.points = w.points[:limit]
+    return w
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(w, sample: int, seed: int = 3):
+    """Oracle pairs/s on a seeded sample of the workload (all host cores)."""
+    import oracle
+    import zef_synth as zs
+    oracle.build()
+    idx = zs.sample_rows(w.points, sample, seed=seed)
+    pts = w.points[idx]
+    t0 = time.perf_counter()
+    oracle.label_points(pts, w.surfaces, w.priority)
+    dt = time.perf_counter() - t0
+    pairs = len(pts) * w.total_tris
+    return pairs / dt, dt, len(pts), oracle.max_threads()
+
+
+def auto_sample(w, target_s: float = 12.0):
+    """Size the oracle sample for about target_s seconds of CPU work."""
+    rate, dt, n, _ = cpu_oracle_rate(w, 256, seed=1)
+    return int(max(256, min(len(w.points), rate * target_s / w.total_tris)))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload(args.config, args.points)
+    sample = args.cpu_sample or auto_sample(w, 8.0)
+    times = []
+    for k in range(args.warmup + args.steps):
+        rate, dt, n, cores = cpu_oracle_rate(w, sample, seed=100 + k)
+        if k >= args.warmup:
+            times.append(dt)
+    T = float(np.sum(times))
+    pairs = sample * w.total_tris * args.steps
+    value = pairs / T
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "points_per_step": sample, "triangles": w.total_tris,
+                       "compartments": len(w.surfaces)},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} seeded points of the workload per step, all "
+                                       f"{w.total_tris} triangles each (no culling)"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2203_10000_gb300 import zef
+
+    w = workload(args.config, args.points)
+    N = int(w.points.shape[0])
+    ctx = zef.Context(local)
+    for s in w.surfaces:
+        ctx.add_compartment(s.id, s.verts, s.tris)
+    ctx.set_priority(w.priority)
+    pts_h = np.ascontiguousarray(w.points)
+    pts = torch.from_numpy(pts_h).to(dev)
+    labels = torch.empty(N, dtype=torch.int32, device=dev)
+    opts = zef.make_opts()
+    if args.shape:
+        t, p = (int(x) for x in args.shape.split(","))
+        opts = zef.make_opts(block_threads=t, points_per_thread=p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up (also the stats of the workload, which are deterministic)
+    st = None
+    for _ in range(max(3, args.warmup)):
+        _, _, st = ctx.label_points(pts, labels=labels, opts=opts, stats=True)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    ms_label = []
+    ms_rescue = []
+    barrier()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        _, _, s2 = ctx.label_points(pts, labels=labels, opts=opts, stats=True)
+        ms_label.append(s2["ms_label"])
+        ms_rescue.append(s2["ms_rescue"])
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    pairs = st["pairs_evaluated"]
+    value = pairs * ws / (ms_step * 1e-3)
+
+    # roofline of the FP32 kernel (events around it on the context stream)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    fp32_pairs = st["pairs_evaluated"] - st["pairs_rescued"]
+    ms_lab = float(np.mean(ms_label))
+    achieved = fp32_pairs * FLOPS_PER_PAIR / (ms_lab * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(f"config{args.config}")
+        except Exception:
+            traffic = None
+
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "points": N, "triangles": w.total_tris,
+                       "compartments": len(w.surfaces),
+                       "l2": "flushed between steps (256 MB device write inside the timed region)",
+                       "shape": [st["block_threads"], st["points_per_thread"]]},
+            "pairs_evaluated_per_step": pairs, "pairs_nominal_per_step": st["pairs_nominal"],
+            "nominal_pairs_per_s": st["pairs_nominal"] * ws / (ms_step * 1e-3),
+            "points_per_s": N * ws / (ms_step * 1e-3),
+            "uncertain_pairs_per_step": st["uncertain_pairs"], "rescued_pairs_per_step": st["pairs_rescued"],
+            "ms_label_kernel": ms_lab, "ms_rescue": float(np.mean(ms_rescue)),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops, "traffic": traffic,
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (max clock)",
+                         "flops_per_pair": FLOPS_PER_PAIR,
+                         "frac_at_sampled_clock": (achieved / (sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                                   if clocks.get("sm_mhz") else None)},
+            "gpu_launches": 16 * args.steps, "clocks": clocks}
+
+    # FP32 + rescue vs the plain FP64 kernel on the same subset
+    if args.fp64_points > 0 and rank == 0:
+        nsub = min(N, args.fp64_points)
+        sub = pts[:nsub].contiguous()
+        lab_sub = torch.empty(nsub, dtype=torch.int32, device=dev)
+        _, _, s32 = ctx.label_points(sub, labels=lab_sub, opts=opts, stats=True)
+        l32 = lab_sub.clone()
+        _, _, s64 = ctx.label_points(sub, labels=lab_sub, opts=zef.make_opts(precision=zef.ZEF_FP64_PLAIN),
+                                     stats=True)
+        same = bool(torch.equal(l32, lab_sub))
+        line["fp64_plain"] = {"points": nsub, "ms_fp32_rescue": s32["ms_total"], "ms_fp64_plain": s64["ms_total"],
+                              "speedup": s64["ms_total"] / s32["ms_total"], "labels_equal": same,
+                              "fp64_pairs_per_s": s64["pairs_evaluated"] / (s64["ms_total"] * 1e-3)}
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    if not args.no_e2e:
+        lab_h = np.empty(N, dtype=np.int32)
+        ctx.label_points(pts_h, labels=lab_h, opts=opts, stats=False)
+        barrier()
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 3))
+        for _ in range(ke):
+            ctx.label_points(pts_h, labels=lab_h, opts=opts, stats=False)
+        barrier()
+        te = (time.perf_counter() - t0) / ke
+        line["e2e"] = {"value": pairs * ws / te, "unit": "pairs/s", "h2d_bytes_per_step": int(N * 12),
+                       "d2h_bytes_per_step": int(N * 4), "ms_per_step": te * 1e3,
+                       "labels_equal_device_run": bool(np.array_equal(lab_h, labels.cpu().numpy()))}
+
+    if rank == 0 and not args.no_cpu:
+        sample = args.cpu_sample or auto_sample(w, 12.0)
+        rate, dt, n, cores = cpu_oracle_rate(w, sample)
+        line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{n} seeded points x all {w.total_tris} triangles "
+                                          f"({dt:.1f} s, no culling)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * zef.h -- C ABI of the GB300 solid-angle labeling library (libzef).
+ *
+ * The library decides which closed compartment surface encloses each query
+ * point of a tetrahedral mesh, following Galaz Prieto et al., "Multi-compartment
+ * human head modeling: generating adaptive tetrahedral mesh with GPU
+ * acceleration" (arXiv:2203.10000):
+ *
+ *   Sec. 2.1.3, Eq. 1   s(p) = Omega(p) / 4 pi, Omega the solid angle that the
+ *                       closed surface subtends at p; p is enclosed when
+ *                       s >= T.  Here T = 1/2 with a strict comparison:
+ *                       inside  <=>  Omega > 2 pi.  Omega is evaluated per
+ *                       triangle in closed form (Van Oosterom & Strackee,
+ *                       IEEE TBME 30(2), 1983) and summed over the surface.
+ *   Sec. 2.1            nested compartments take precedence from the innermost
+ *                       to the outermost; where boundaries intersect, the one
+ *                       first in the layer hierarchy wins; a temporary
+ *                       bounding box is the outermost compartment (label 0).
+ *   Sec. 2.1.2, 2.1.3   refinement of the tets on a tissue boundary and
+ *                       recursive re-labeling of the new nodes only.
+ *
+ * Conventions shared by every call
+ *   - Every call returns a zef_status.  On failure the outputs are
+ *     unspecified, the context stays usable and zef_last_error() describes the
+ *     failure.
+ *   - Array arguments may live in host memory or in device memory of the
+ *     context's device; the library detects which (cudaPointerGetAttributes).
+ *     The caller keeps ownership of every buffer it passes.  All arrays are
+ *     dense, row-major, C-contiguous.
+ *   - When every array argument of a call is device memory the call is
+ *     asynchronous on the context's stream, except that a non-NULL stats
+ *     argument makes it synchronize.  With any host array the call
+ *     synchronizes before it returns.
+ *   - Coordinates are float32 in any consistent unit (the workloads use mm).
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef ZEF_H
+#define ZEF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZEF_VERSION_MAJOR 1
+#define ZEF_VERSION_MINOR 0
+
+/* Maximum number of compartments in one context (bit masks are 64 bits). */
+#define ZEF_MAX_COMPARTMENTS 64
+
+typedef struct zef_ctx zef_ctx; /* opaque; owns all device memory it allocates */
+
+typedef enum zef_status {
+    ZEF_OK = 0,
+    ZEF_ERR_INVALID_ARG = 1,          /* null/negative/inconsistent argument */
+    ZEF_ERR_SURFACE_NOT_CLOSED = 2,   /* an undirected edge not used by exactly two
+                                         triangles in opposite directions */
+    ZEF_ERR_SURFACE_ORIENTATION = 3,  /* signed volume <= 0 and no ZEF_AUTO_ORIENT */
+    ZEF_ERR_OOM = 4,                  /* device or host allocation failed */
+    ZEF_ERR_CUDA = 5,                 /* a CUDA runtime call failed */
+    ZEF_ERR_TIMEOUT = 6,              /* a bounded device wait expired (the kernel
+                                         stopped early and reported it) */
+    ZEF_ERR_NOT_READY = 7,            /* no compartment registered */
+    ZEF_ERR_CAPACITY = 8              /* refinement needs more nodes/tets than the
+                                         caller's capacities */
+} zef_status;
+
+/* zef_add_compartment flags */
+#define ZEF_AUTO_ORIENT 1u /* flip every triangle when the signed volume is negative */
+
+/* Arithmetic of zef_label_points */
+typedef enum zef_precision {
+    ZEF_FP32_RESCUE = 0, /* FP32 solid angles with compensated accumulation;
+                            pairs whose result is not certain are re-evaluated
+                            in FP64 over the full surface (default) */
+    ZEF_FP64_PLAIN = 1,  /* every pair in FP64 (the plain baseline kernel) */
+    ZEF_FP32_ONLY = 2    /* FP32 without the FP64 re-evaluation (diagnostics) */
+} zef_precision;
+
+typedef struct zef_label_opts {
+    /* |Omega32 - 2 pi| < margin marks a (point, compartment) pair uncertain.
+       Default 1e-3 (<= 0 selects the default). */
+    float margin;
+    /* A pair is also uncertain when Omega32 is farther than winding_tol from
+       the nearest multiple of 4 pi (Omega of a closed surface at a point off
+       the surface is 4 pi times an integer).  Default 4e-6. */
+    float winding_tol;
+    /* zef_precision */
+    int32_t precision;
+    /* Threads per block and points per thread of the FP32 kernel; 0 = the
+       autotuned choice.  Valid: threads 128 or 256, points 2, 4 or 8. */
+    int32_t block_threads;
+    int32_t points_per_thread;
+    int32_t reserved[3];
+} zef_label_opts;
+
+typedef struct zef_label_stats {
+    int64_t points;            /* N */
+    int64_t nonfinite_points;  /* points with a NaN/Inf coordinate (label -1) */
+    int64_t pairs_nominal;     /* N * sum_c T_c */
+    int64_t pairs_evaluated;   /* point x triangle pairs computed (FP32 + FP64) */
+    int64_t pairs_rescued;     /* point x triangle pairs re-evaluated in FP64 */
+    int64_t uncertain_pairs;   /* (point, compartment) pairs sent to FP64 */
+    int64_t work_items;        /* (compartment, point tile) items after culling */
+    int64_t tiles;             /* point tiles */
+    int32_t block_threads;     /* launch shape used */
+    int32_t points_per_thread;
+    float ms_total;            /* device time of the call (CUDA events) */
+    float ms_label;            /* device time of the main labeling kernel */
+    float ms_rescue;           /* device time of the FP64 re-evaluation */
+    float reserved;
+} zef_label_stats;
+
+/* Mesh for zef_refine_and_relabel.  All four arrays must be device memory or
+   all host memory.  Capacities bound the growth: nodes grow by at most six
+   per flagged tet and level, tets by seven. */
+typedef struct zef_mesh {
+    float *nodes;          /* [node_capacity][3] */
+    int32_t *tets;         /* [tet_capacity][4], 0-based node indices */
+    int32_t *node_labels;  /* [node_capacity] */
+    int64_t num_nodes;     /* in: current count; out: count after refinement */
+    int64_t num_tets;      /* in/out likewise */
+    int64_t node_capacity;
+    int64_t tet_capacity;
+    int32_t labels_valid;  /* nonzero: node_labels[0, num_nodes) already hold
+                              labels; 0: label every node first */
+    int32_t reserved;
+} zef_mesh;
+
+typedef struct zef_level_stats {
+    int64_t flagged_tets;   /* tets whose four node labels were not all equal */
+    int64_t new_nodes;      /* unique edge midpoints added and labeled */
+    int64_t nodes;          /* node count after the level */
+    int64_t tets;           /* tet count after the level */
+    int64_t pairs_evaluated;
+    int64_t uncertain_pairs;
+} zef_level_stats;
+
+/* Pass as `device` to zef_create for a host-only context: it makes no CUDA
+   call; compartments can be registered and validated, while labeling and
+   refinement return ZEF_ERR_NOT_READY. */
+#define ZEF_HOST_ONLY (-1)
+
+/* Create a context on CUDA device `device` (or ZEF_HOST_ONLY).  `cuda_stream`
+   is a cudaStream_t of that device to run on (for example a PyTorch stream);
+   NULL makes the context create its own non-blocking stream.  *out is NULL on
+   failure. */
+zef_status zef_create(zef_ctx **out, int device, void *cuda_stream);
+
+/* Release every resource of the context.  NULL is ignored. */
+void zef_destroy(zef_ctx *ctx);
+
+/* Message of the last failing call on this context (static text for a NULL
+   context).  Valid until the next call on the context. */
+const char *zef_last_error(const zef_ctx *ctx);
+
+/* Register a closed triangulated compartment surface (Sec. 2.1.3: dS closed).
+     id     > 0, unique within the context; it is the label of enclosed points
+     verts  [nv][3] float32
+     tris   [nt][3] int32, 0-based; every undirected edge must be used by
+            exactly two triangles, in opposite directions (closed, oriented)
+     flags  ZEF_AUTO_ORIENT or 0
+   Outward orientation (positive signed volume) is required unless
+   ZEF_AUTO_ORIENT is set, in which case an inward surface is flipped.  The
+   data are copied; the call synchronizes.  Registration order is the default
+   priority order. */
+zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int64_t nv,
+                               const int32_t *tris, int64_t nt, uint32_t flags);
+
+/* Number of registered compartments and their total triangle count. */
+zef_status zef_compartment_info(const zef_ctx *ctx, int32_t *num_compartments,
+                                int64_t *total_triangles);
+
+/* Set the layer hierarchy (Sec. 2.1): `ids` is a permutation of all
+   registered ids; ids[0] has the highest priority, i.e. a point enclosed by
+   several compartments gets the first of them in this list.  Host array. */
+zef_status zef_compartment_priority(zef_ctx *ctx, const int32_t *ids, int32_t n);
+
+/* Label N query points (Sec. 2.1.3 initial labeling, Sec. 2.1 priority).
+     pts     [n][3] float32
+     labels  [n] int32 out: id of the first compartment in priority order
+             whose surface encloses the point (Omega > 2 pi); 0 when none;
+             -1 for a point with a non-finite coordinate
+     omega   nullable; [C][n] float32 out, row r = the r-th compartment in
+             priority order: the solid angle Omega in steradians (0 exactly
+             where the point is outside the compartment's bounding box)
+     opts    nullable = defaults;  stats nullable (non-NULL synchronizes) */
+zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
+                            float *omega, const zef_label_opts *opts, zef_label_stats *stats);
+
+/* Recursive refinement and re-labeling (Sec. 2.1.2, Sec. 2.1.3 item 2):
+   `levels` times, every tet whose four node labels are not all equal is split
+   into eight (one new node per edge midpoint, shared between tets), and only
+   the new nodes are labeled.  The flagged tet's slot receives its first child;
+   the other seven are appended.  The level loop runs as one CUDA graph with
+   device-resident counts.  per_level: nullable, `levels` entries. */
+zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels,
+                                  const zef_label_opts *opts, zef_level_stats *per_level);
+
+/* Wait for the context's stream and report any error a kernel recorded
+   (ZEF_ERR_TIMEOUT, ZEF_ERR_CAPACITY). */
+zef_status zef_synchronize(zef_ctx *ctx);
+
+/* Library version, encoded as major * 1000 + minor. */
+int32_t zef_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZEF_H */

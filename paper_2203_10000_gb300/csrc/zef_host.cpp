@@ -1,0 +1,690 @@
+// Host side of libzef: context, surface registration (Sec. 2.1.3: closed
+// segmentation boundaries), priority (Sec. 2.1), argument checking and the C
+// entry points.  All arithmetic of the labeling path runs in the kernels of
+// zef_label.cu / zef_refine.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <unordered_map>
+
+#include "zef_debug.h"
+#include "zef_internal.h"
+
+using namespace zef;
+
+namespace zef {
+
+zef_status fail(zef_ctx *ctx, zef_status st, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+zef_status cuda_fail(zef_ctx *ctx, cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  zef_status st = (e == cudaErrorMemoryAllocation) ? ZEF_ERR_OOM : ZEF_ERR_CUDA;
+  return fail(ctx, st, m);
+}
+
+}  // namespace zef
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+namespace {
+
+const char *kNullCtxMsg = "zef: null context";
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (dev < 0) return;  // host-only context
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Is p device memory (device or managed) of `device`?  Host otherwise.
+bool is_device_ptr(const void *p, int device) {
+  if (device < 0) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice) return a.device == device;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------- strips
+// Greedy triangle strips over a closed oriented manifold mesh.  A strip is a
+// vertex sequence s0, s1, s2, ... whose consecutive triples are triangles;
+// every triangle appears in exactly one strip.
+struct Stripper {
+  const int32_t *tris;
+  int64_t nt;
+  std::vector<int64_t> nbr;  // [t*3 + e] triangle across edge e = (v_e, v_{e+1})
+
+  // neighbour of triangle t across the undirected edge {a, b}; -1 if none
+  int64_t across(int64_t t, int32_t a, int32_t b) const {
+    const int32_t *f = tris + 3 * t;
+    for (int e = 0; e < 3; ++e) {
+      int32_t x = f[e], y = f[(e + 1) % 3];
+      if ((x == a && y == b) || (x == b && y == a)) return nbr[3 * t + e];
+    }
+    return -1;
+  }
+  static int32_t third(const int32_t *f, int32_t a, int32_t b) {
+    for (int e = 0; e < 3; ++e)
+      if (f[e] != a && f[e] != b) return f[e];
+    return -1;
+  }
+  // length (triangles) of the strip starting at t with first vertex f[r]
+  template <bool Commit>
+  int64_t walk(int64_t t, int r, std::vector<uint8_t> &used, std::vector<int32_t> *seq,
+               std::vector<int64_t> *tri_seq) {
+    const int32_t *f = tris + 3 * t;
+    int32_t s0 = f[r], s1 = f[(r + 1) % 3], s2 = f[(r + 2) % 3];
+    std::vector<int64_t> touched;
+    int64_t len = 1;
+    if (Commit) {
+      seq->push_back(s0);
+      seq->push_back(s1);
+      seq->push_back(s2);
+      tri_seq->push_back(t);
+      used[t] = 1;
+    } else {
+      used[t] = 2;
+      touched.push_back(t);
+    }
+    int64_t cur = t;
+    int32_t a = s1, b = s2;
+    for (;;) {
+      int64_t nx = across(cur, a, b);
+      if (nx < 0 || used[nx]) break;
+      int32_t c = third(tris + 3 * nx, a, b);
+      if (Commit) {
+        seq->push_back(c);
+        tri_seq->push_back(nx);
+        used[nx] = 1;
+      } else {
+        used[nx] = 2;
+        touched.push_back(nx);
+      }
+      ++len;
+      cur = nx;
+      a = b;
+      b = c;
+    }
+    if (!Commit)
+      for (int64_t q : touched) used[q] = 0;
+    return len;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- entry points
+extern "C" {
+
+int32_t zef_version(void) { return ZEF_VERSION_MAJOR * 1000 + ZEF_VERSION_MINOR; }
+
+const char *zef_last_error(const zef_ctx *ctx) {
+  if (!ctx) return kNullCtxMsg;
+  return ctx->err.c_str();
+}
+
+zef_status zef_create(zef_ctx **out, int device, void *cuda_stream) {
+  if (!out) return ZEF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (device == ZEF_HOST_ONLY) {
+    zef_ctx *h = new (std::nothrow) zef_ctx();
+    if (!h) return ZEF_ERR_OOM;
+    h->device = ZEF_HOST_ONLY;
+    *out = h;
+    return ZEF_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return ZEF_ERR_INVALID_ARG;
+  }
+  zef_ctx *ctx = new (std::nothrow) zef_ctx();
+  if (!ctx) return ZEF_ERR_OOM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  zef_status st = ZEF_OK;
+  do {
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaDeviceGetAttribute"); break; }
+    if (cuda_stream) {
+      ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaStreamCreate"); break; }
+      ctx->own_stream = true;
+    }
+    e = cudaMalloc(&ctx->d_status, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaMalloc(status)"); break; }
+    e = cudaMemset(ctx->d_status, 0, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaMemset(status)"); break; }
+    e = cudaMallocHost(&ctx->h_counters, CNT_COUNT_ * sizeof(int64_t));
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaMallocHost"); break; }
+    for (auto &ev : ctx->ev) {
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaEventCreate"); break; }
+    }
+  } while (0);
+  if (st != ZEF_OK) {
+    zef_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return ZEF_OK;
+}
+
+void zef_destroy(zef_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->device == ZEF_HOST_ONLY) {
+    delete ctx;
+    return;
+  }
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  auto fr = [](void *p) {
+    if (p) cudaFree(p);
+  };
+  fr(ctx->d_entries);
+  fr(ctx->d_tris);
+  fr(ctx->d_comps);
+  fr(ctx->d_row_ids);
+  fr(ctx->d_lpt);
+  fr(ctx->d_status);
+  LabelBuffers &b = ctx->lb;
+  fr(b.spts); fr(b.perm); fr(b.keys); fr(b.in_mask); fr(b.unc_mask); fr(b.tile_box);
+  fr(b.hist); fr(b.flags); fr(b.block_sums); fr(b.items); fr(b.unc_list); fr(b.counters);
+  fr(b.labels_tmp); fr(b.pts_tmp); fr(b.omega_tmp);
+  for (auto &p : ctx->rf_buf) fr(p);
+  if (ctx->rf_exec) cudaGraphExecDestroy(ctx->rf_exec);
+  if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+  for (auto &ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  cudaGetLastError();
+  delete ctx;
+}
+
+zef_status zef_compartment_info(const zef_ctx *ctx, int32_t *num_compartments, int64_t *total) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  if (num_compartments) *num_compartments = (int32_t)ctx->comps.size();
+  if (total) {
+    int64_t s = 0;
+    for (auto &c : ctx->comps) s += c.nt;
+    *total = s;
+  }
+  return ZEF_OK;
+}
+
+zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int64_t nv,
+                               const int32_t *tris, int64_t nt, uint32_t flags) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (id <= 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "compartment id must be > 0");
+  for (auto &c : ctx->comps)
+    if (c.id == id) return fail(ctx, ZEF_ERR_INVALID_ARG, "duplicate compartment id");
+  if ((int)ctx->comps.size() >= ZEF_MAX_COMPARTMENTS)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "too many compartments (max 64)");
+  if (!verts || !tris || nv < 4 || nt < 4)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "a closed surface needs >= 4 vertices and >= 4 triangles");
+  if (nt > (int64_t)1 << 28 || nv > (int64_t)1 << 30)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "surface too large");
+  if (flags & ~ZEF_AUTO_ORIENT) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown flags");
+  DeviceGuard g(ctx->device);
+
+  std::vector<float> V(3 * nv);
+  std::vector<int32_t> T(3 * nt);
+  if (is_device_ptr(verts, ctx->device)) {
+    CK(cudaMemcpy(V.data(), verts, V.size() * sizeof(float), cudaMemcpyDeviceToHost), "copy verts");
+  } else {
+    std::memcpy(V.data(), verts, V.size() * sizeof(float));
+  }
+  if (is_device_ptr(tris, ctx->device)) {
+    CK(cudaMemcpy(T.data(), tris, T.size() * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy tris");
+  } else {
+    std::memcpy(T.data(), tris, T.size() * sizeof(int32_t));
+  }
+  for (float x : V)
+    if (!std::isfinite(x)) return fail(ctx, ZEF_ERR_INVALID_ARG, "non-finite vertex coordinate");
+  for (int64_t t = 0; t < nt; ++t) {
+    int32_t a = T[3 * t], b = T[3 * t + 1], c = T[3 * t + 2];
+    if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv)
+      return fail(ctx, ZEF_ERR_INVALID_ARG, "triangle index out of range");
+    if (a == b || b == c || a == c)
+      return fail(ctx, ZEF_ERR_SURFACE_NOT_CLOSED, "degenerate triangle (repeated vertex)");
+  }
+
+  // closedness: every directed edge once, and its reverse present
+  std::vector<uint64_t> de(3 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int e = 0; e < 3; ++e)
+      de[3 * t + e] = ((uint64_t)(uint32_t)T[3 * t + e] << 32) | (uint32_t)T[3 * t + (e + 1) % 3];
+  std::vector<int64_t> order(3 * nt);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return de[x] < de[y]; });
+  for (size_t i = 1; i < order.size(); ++i)
+    if (de[order[i]] == de[order[i - 1]])
+      return fail(ctx, ZEF_ERR_SURFACE_NOT_CLOSED,
+                  "surface not closed/oriented: a directed edge is used twice");
+  auto find_edge = [&](uint64_t key) -> int64_t {
+    size_t lo = 0, hi = order.size();
+    while (lo < hi) {
+      size_t mid = (lo + hi) / 2;
+      if (de[order[mid]] < key) lo = mid + 1; else hi = mid;
+    }
+    if (lo < order.size() && de[order[lo]] == key) return order[lo];
+    return -1;
+  };
+  Stripper sp;
+  sp.nbr.assign(3 * nt, -1);
+  for (int64_t i = 0; i < 3 * nt; ++i) {
+    uint64_t k = de[i];
+    uint64_t rk = (k << 32) | (k >> 32);
+    int64_t j = find_edge(rk);
+    if (j < 0)
+      return fail(ctx, ZEF_ERR_SURFACE_NOT_CLOSED,
+                  "surface not closed: an edge has no opposite half-edge");
+    sp.nbr[i] = j / 3;
+  }
+
+  // orientation: signed volume in double
+  double vol = 0.0;
+  for (int64_t t = 0; t < nt; ++t) {
+    const float *a = &V[3 * T[3 * t]], *b = &V[3 * T[3 * t + 1]], *c = &V[3 * T[3 * t + 2]];
+    double cx = (double)b[1] * c[2] - (double)b[2] * c[1];
+    double cy = (double)b[2] * c[0] - (double)b[0] * c[2];
+    double cz = (double)b[0] * c[1] - (double)b[1] * c[0];
+    vol += (double)a[0] * cx + (double)a[1] * cy + (double)a[2] * cz;
+  }
+  if (!(vol > 0.0)) {
+    if (!(flags & ZEF_AUTO_ORIENT) || vol == 0.0)
+      return fail(ctx, ZEF_ERR_SURFACE_ORIENTATION,
+                  "surface has non-positive signed volume (inward orientation)");
+    for (int64_t t = 0; t < nt; ++t) std::swap(T[3 * t + 1], T[3 * t + 2]);
+    // neighbour table follows the flipped edges: edge e=(v0,v1)->(v0,v2) etc.
+    for (int64_t t = 0; t < nt; ++t) {
+      int64_t n0 = sp.nbr[3 * t], n1 = sp.nbr[3 * t + 1], n2 = sp.nbr[3 * t + 2];
+      sp.nbr[3 * t] = n2;      // (v0, v2)
+      sp.nbr[3 * t + 1] = n1;  // (v2, v1)
+      sp.nbr[3 * t + 2] = n0;  // (v1, v0)
+    }
+  }
+
+  CompHost ch;
+  ch.id = id;
+  ch.nv = nv;
+  ch.nt = nt;
+  for (int k = 0; k < 3; ++k) {
+    ch.lo[k] = std::numeric_limits<float>::infinity();
+    ch.hi[k] = -std::numeric_limits<float>::infinity();
+  }
+  for (int64_t i = 0; i < 3 * nt; ++i) {
+    const float *p = &V[3 * T[i]];
+    for (int k = 0; k < 3; ++k) {
+      ch.lo[k] = std::min(ch.lo[k], p[k]);
+      ch.hi[k] = std::max(ch.hi[k], p[k]);
+    }
+  }
+
+  // strips
+  sp.tris = T.data();
+  sp.nt = nt;
+  std::vector<uint8_t> used(nt, 0);
+  std::vector<Entry> ent;
+  ent.reserve(nt + nt / 4 + 32);
+  int64_t nstrips = 0;
+  const float ninf = -std::numeric_limits<float>::infinity();
+  auto vtx = [&](int32_t v) { return &V[3 * (int64_t)v]; };
+  for (int64_t t = 0; t < nt; ++t) {
+    if (used[t]) continue;
+    int best_r = 0;
+    int64_t best_len = -1;
+    for (int r = 0; r < 3; ++r) {
+      int64_t len = sp.walk<false>(t, r, used, nullptr, nullptr);
+      if (len > best_len) { best_len = len; best_r = r; }
+    }
+    std::vector<int32_t> seq;
+    std::vector<int64_t> tseq;
+    sp.walk<true>(t, best_r, used, &seq, &tseq);
+    ++nstrips;
+    for (size_t k = 0; k < seq.size(); ++k) {
+      Entry e;
+      const float *p = vtx(seq[k]);
+      e.v = make_float4(p[0], p[1], p[2], 0.f);
+      e.n = make_float4(0.f, 0.f, 0.f, ninf);
+      if (k >= 2) {
+        const int32_t *f = &T[3 * tseq[k - 2]];
+        const float *a = vtx(f[0]), *b = vtx(f[1]), *c = vtx(f[2]);
+        double e1[3], e2[3];
+        for (int q = 0; q < 3; ++q) {
+          e1[q] = (double)b[q] - a[q];
+          e2[q] = (double)c[q] - a[q];
+        }
+        double nx = e1[1] * e2[2] - e1[2] * e2[1];
+        double ny = e1[2] * e2[0] - e1[0] * e2[2];
+        double nz = e1[0] * e2[1] - e1[1] * e2[0];
+        double nn = std::sqrt(nx * nx + ny * ny + nz * nz);
+        e.v.w = 1.f;
+        e.n = make_float4((float)nx, (float)ny, (float)nz, (float)(kKappa * nn));
+      }
+      ent.push_back(e);
+    }
+  }
+  while (ent.size() % kGroup) {
+    Entry e = ent.back();
+    e.v.w = 0.f;
+    e.n = make_float4(0.f, 0.f, 0.f, ninf);
+    ent.push_back(e);
+  }
+  ch.nstrips = nstrips;
+  ch.entry_off = (int64_t)ctx->h_entries.size();
+  ch.entry_cnt = (int64_t)ent.size();
+  ch.tri_off = (int64_t)(ctx->h_tris.size() / 3);
+  if (ch.entry_off + ch.entry_cnt > INT32_MAX || ch.tri_off + nt > INT32_MAX)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "total surface size exceeds the library limit");
+  ctx->h_entries.insert(ctx->h_entries.end(), ent.begin(), ent.end());
+  for (int64_t t = 0; t < nt; ++t)
+    for (int q = 0; q < 3; ++q) {
+      const float *p = vtx(T[3 * t + q]);
+      ctx->h_tris.push_back(make_float4(p[0], p[1], p[2], 0.f));
+    }
+  ctx->comps.push_back(ch);
+  ctx->priority.push_back(id);
+  ctx->dirty = true;
+  ctx->tune_cache.clear();
+  return ensure_uploaded(ctx);
+}
+
+zef_status zef_compartment_priority(zef_ctx *ctx, const int32_t *ids, int32_t n) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (!ids || n != (int32_t)ctx->comps.size())
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "priority must list every registered compartment once");
+  std::vector<int32_t> a(ids, ids + n), b;
+  for (auto &c : ctx->comps) b.push_back(c.id);
+  std::vector<int32_t> sa = a, sb = b;
+  std::sort(sa.begin(), sa.end());
+  std::sort(sb.begin(), sb.end());
+  if (sa != sb || std::adjacent_find(sa.begin(), sa.end()) != sa.end())
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "priority is not a permutation of the registered ids");
+  ctx->priority = a;
+  ctx->dirty = true;
+  DeviceGuard g(ctx->device);
+  return ensure_uploaded(ctx);
+}
+
+zef_status zef_synchronize(zef_ctx *ctx) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  if (ctx->device == ZEF_HOST_ONLY) return ZEF_OK;
+  DeviceGuard g(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  uint32_t st[2] = {0, 0};
+  CK(cudaMemcpy(st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost), "read status");
+  if (st[0]) {
+    CK(cudaMemset(ctx->d_status, 0, 2 * sizeof(uint32_t)), "clear status");
+    if (st[0] & ST_TIMEOUT)
+      return fail(ctx, ZEF_ERR_TIMEOUT, "a bounded device wait expired (site " + std::to_string(st[1]) + ")");
+    if (st[0] & ST_CAPACITY)
+      return fail(ctx, ZEF_ERR_CAPACITY, "refinement exceeded the mesh capacities");
+  }
+  return ZEF_OK;
+}
+
+zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels, float *omega,
+                            const zef_label_opts *opts, zef_label_stats *stats) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
+  if (n < 0 || (n > 0 && (!pts || !labels)))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad points/labels arguments");
+  if (n > ((int64_t)1 << 31) - 1) return fail(ctx, ZEF_ERR_INVALID_ARG, "too many points (max 2^31-1)");
+  zef_label_opts o;
+  if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
+  fill_default_opts(&o);
+  if (o.precision < 0 || o.precision > 2) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision");
+  if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n == 0) return ZEF_OK;
+  DeviceGuard g(ctx->device);
+  zef_status st = ensure_uploaded(ctx);
+  if (st) return st;
+  st = label_reserve(ctx, n);
+  if (st) return st;
+  const int C = (int)ctx->comps.size();
+  bool dpts = is_device_ptr(pts, ctx->device);
+  bool dlab = is_device_ptr(labels, ctx->device);
+  bool dom = omega ? is_device_ptr(omega, ctx->device) : true;
+  LabelBuffers &b = ctx->lb;
+  const float *d_pts = pts;
+  if (!dpts) {
+    CK(cudaMemcpyAsync(b.pts_tmp, pts, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice,
+                       ctx->stream), "copy points");
+    d_pts = b.pts_tmp;
+  }
+  int32_t *d_lab = dlab ? labels : b.labels_tmp;
+  float *d_om = omega;
+  if (omega && !dom) {
+    if (b.cap_omega < (int64_t)C * n) {
+      if (b.omega_tmp) cudaFree(b.omega_tmp);
+      b.omega_tmp = nullptr;
+      b.cap_omega = 0;
+      CK(cudaMalloc(&b.omega_tmp, (size_t)C * n * sizeof(float)), "cudaMalloc(omega)");
+      b.cap_omega = (int64_t)C * n;
+    }
+    d_om = b.omega_tmp;
+  }
+  LabelPlan plan;
+  plan.pts = d_pts;
+  plan.labels = d_lab;
+  plan.omega = d_om;
+  plan.omega_ld = n;
+  plan.n_cap = n;
+  plan.d_n = b.counters + CNT_N;
+  plan.d_off = b.counters + CNT_OFF;
+  plan.opts = o;
+  bool need_tune = false;
+  plan.shape = choose_shape(ctx, o, n, &need_tune);
+  plan.timed = stats != nullptr;
+  if (need_tune) {
+    st = autotune(ctx, plan, &plan.shape);
+    if (st) return st;
+  }
+  st = label_set_count(ctx, n, 0);
+  if (st) return st;
+  st = label_enqueue(ctx, plan);
+  if (st) return st;
+  if (!dlab)
+    CK(cudaMemcpyAsync(labels, d_lab, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
+       "copy labels");
+  if (omega && !dom)
+    CK(cudaMemcpyAsync(omega, d_om, (size_t)C * n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream),
+       "copy omega");
+  if (stats || !dpts || !dlab || !dom) {
+    st = zef_synchronize(ctx);
+    if (st) return st;
+  }
+  if (stats) {
+    CK(cudaMemcpy(ctx->h_counters, b.counters, CNT_COUNT_ * sizeof(int64_t), cudaMemcpyDeviceToHost),
+       "read counters");
+    const int64_t *h = ctx->h_counters;
+    stats->points = n;
+    stats->nonfinite_points = h[CNT_NONFINITE];
+    int64_t tt = 0;
+    for (auto &c : ctx->comps) tt += c.nt;
+    stats->pairs_nominal = n * tt;
+    stats->pairs_rescued = h[CNT_PAIRS_RESCUE];
+    stats->pairs_evaluated = h[CNT_PAIRS_EVAL] + h[CNT_PAIRS_RESCUE];
+    stats->uncertain_pairs = h[CNT_UNC];
+    stats->work_items = h[CNT_ITEMS];
+    stats->tiles = h[CNT_TILES];
+    stats->block_threads = plan.shape.threads;
+    stats->points_per_thread = plan.shape.ppt;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+    stats->ms_total = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    stats->ms_label = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]);
+    stats->ms_rescue = ms;
+  }
+  return ZEF_OK;
+}
+
+zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_label_opts *opts,
+                                  zef_level_stats *per_level) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot refine");
+  if (!mesh || levels < 0 || levels > 32) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad mesh/levels");
+  if (!mesh->nodes || !mesh->tets || !mesh->node_labels || mesh->num_nodes < 0 || mesh->num_tets < 0 ||
+      mesh->num_nodes > mesh->node_capacity || mesh->num_tets > mesh->tet_capacity ||
+      mesh->node_capacity >= ((int64_t)1 << 31) || mesh->tet_capacity >= ((int64_t)1 << 31))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad mesh arrays or capacities");
+  zef_label_opts o;
+  if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
+  fill_default_opts(&o);
+  if (o.precision < 0 || o.precision > 2) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision");
+  if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
+  DeviceGuard g(ctx->device);
+  zef_status st = ensure_uploaded(ctx);
+  if (st) return st;
+  return refine_run(ctx, mesh, levels, o, per_level);
+}
+
+}  // extern "C"
+
+namespace zef {
+
+template <class T>
+zef_status ensure_buffer(zef_ctx *ctx, T **p, int64_t *cap, int64_t need) {
+  if (*p && *cap >= need) return ZEF_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  cudaError_t e = cudaMalloc((void **)p, (size_t)std::max<int64_t>(need, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    *cap = 0;
+    return cuda_fail(ctx, e, "cudaMalloc");
+  }
+  *cap = need;
+  return ZEF_OK;
+}
+template zef_status ensure_buffer<float>(zef_ctx *, float **, int64_t *, int64_t);
+
+zef_status ensure_uploaded(zef_ctx *ctx) {
+  if (ctx->device == ZEF_HOST_ONLY) return ZEF_OK;
+  if (!ctx->dirty) return ZEF_OK;
+  const int C = (int)ctx->comps.size();
+  if (C == 0) return ZEF_OK;
+  int64_t ne = (int64_t)ctx->h_entries.size();
+  int64_t ntv = (int64_t)ctx->h_tris.size();
+  if (ctx->d_entries_cap < ne) {
+    if (ctx->d_entries) cudaFree(ctx->d_entries);
+    ctx->d_entries = nullptr;
+    CK(cudaMalloc(&ctx->d_entries, ne * sizeof(Entry)), "cudaMalloc(entries)");
+    ctx->d_entries_cap = ne;
+  }
+  if (ctx->d_tris_cap < ntv) {
+    if (ctx->d_tris) cudaFree(ctx->d_tris);
+    ctx->d_tris = nullptr;
+    CK(cudaMalloc(&ctx->d_tris, ntv * sizeof(float4)), "cudaMalloc(tris)");
+    ctx->d_tris_cap = ntv;
+  }
+  if (!ctx->d_comps) {
+    CK(cudaMalloc(&ctx->d_comps, ZEF_MAX_COMPARTMENTS * sizeof(DevComp)), "cudaMalloc(comps)");
+    CK(cudaMalloc(&ctx->d_row_ids, ZEF_MAX_COMPARTMENTS * sizeof(int32_t)), "cudaMalloc(rows)");
+    CK(cudaMalloc(&ctx->d_lpt, ZEF_MAX_COMPARTMENTS * sizeof(int32_t)), "cudaMalloc(lpt)");
+  }
+  std::vector<DevComp> dc(C);
+  std::vector<int32_t> rows(C), lpt(C);
+  for (int i = 0; i < C; ++i) {
+    const CompHost &h = ctx->comps[i];
+    DevComp &d = dc[i];
+    for (int k = 0; k < 3; ++k) {
+      d.lo[k] = h.lo[k];
+      d.hi[k] = h.hi[k];
+    }
+    d.entry_off = (int32_t)h.entry_off;
+    d.entry_cnt = (int32_t)h.entry_cnt;
+    d.tri_off = (int32_t)h.tri_off;
+    d.tri_cnt = (int32_t)h.nt;
+    d.id = h.id;
+    d.row = -1;
+    for (int r = 0; r < C; ++r)
+      if (ctx->priority[r] == h.id) d.row = r;
+    rows[d.row] = h.id;
+  }
+  std::iota(lpt.begin(), lpt.end(), 0);
+  std::stable_sort(lpt.begin(), lpt.end(),
+                   [&](int a, int b) { return ctx->comps[a].nt > ctx->comps[b].nt; });
+  CK(cudaMemcpy(ctx->d_entries, ctx->h_entries.data(), ne * sizeof(Entry), cudaMemcpyHostToDevice),
+     "upload entries");
+  CK(cudaMemcpy(ctx->d_tris, ctx->h_tris.data(), ntv * sizeof(float4), cudaMemcpyHostToDevice),
+     "upload tris");
+  CK(cudaMemcpy(ctx->d_comps, dc.data(), C * sizeof(DevComp), cudaMemcpyHostToDevice), "upload comps");
+  CK(cudaMemcpy(ctx->d_row_ids, rows.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice), "upload rows");
+  CK(cudaMemcpy(ctx->d_lpt, lpt.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice), "upload lpt");
+  ctx->dirty = false;
+  return ZEF_OK;
+}
+
+}  // namespace zef
+
+// Copy of compartment `index`'s strip stream (8 floats per entry: vertex
+// x, y, z, weight, normal x, y, z, kappa) for host-side checks; returns the
+// entry count in *count and copies min(count, cap) entries.
+extern "C" zef_status zef_debug_strip_entries(const zef_ctx *ctx, int32_t index, float *out, int64_t cap,
+                                              int64_t *count) {
+  if (!ctx || index < 0 || index >= (int32_t)ctx->comps.size() || !count) return ZEF_ERR_INVALID_ARG;
+  const CompHost &c = ctx->comps[index];
+  *count = c.entry_cnt;
+  if (out) {
+    const int64_t m = std::min(cap, c.entry_cnt);
+    std::memcpy(out, ctx->h_entries.data() + c.entry_off, (size_t)m * sizeof(Entry));
+  }
+  return ZEF_OK;
+}
+
+// Strip statistics for diagnostics (not part of the public header's promises):
+// number of stream entries and strips of compartment `index`.
+extern "C" zef_status zef_debug_strip_stats(const zef_ctx *ctx, int32_t index, int64_t *entries,
+                                            int64_t *strips) {
+  if (!ctx || index < 0 || index >= (int32_t)ctx->comps.size()) return ZEF_ERR_INVALID_ARG;
+  if (entries) *entries = ctx->comps[index].entry_cnt;
+  if (strips) *strips = ctx->comps[index].nstrips;
+  return ZEF_OK;
+}
+
+extern "C" zef_status zef_debug_wait_probe(zef_ctx *ctx, int64_t limit_ns) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context");
+  if (limit_ns <= 0 || limit_ns > 2000000000LL) return fail(ctx, ZEF_ERR_INVALID_ARG, "limit must be in (0, 2 s]");
+  DeviceGuard g(ctx->device);
+  zef_status st = launch_wait_probe(ctx, limit_ns);
+  if (st) return st;
+  return zef_synchronize(ctx);
+}

@@ -1,0 +1,182 @@
+// Internal declarations of libzef (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "zef.h"
+
+namespace zef {
+
+// One strip-stream entry, 32 bytes (two float4, TMA-friendly):
+//   v = (x, y, z, weight): the vertex entering the sliding triangle window;
+//       weight 1 when the window (previous two vertices + this one) is a
+//       triangle of the surface, 0 for the two entries that prime a strip;
+//   n = (nx, ny, nz, kappa): that triangle's doubled-area normal with the
+//       surface's orientation, and kappa = KAPPA * |n| for the conditioning
+//       test; n = 0 and kappa = -inf on priming entries.
+struct __align__(16) Entry {
+  float4 v;
+  float4 n;
+};
+
+// Device view of one compartment.
+struct __align__(16) DevComp {
+  float lo[3];
+  float hi[3];
+  int32_t entry_off;  // first Entry of the compartment (multiple of 16)
+  int32_t entry_cnt;  // number of entries, padded to a multiple of 16
+  int32_t tri_off;    // first triangle in the plain triangle list
+  int32_t tri_cnt;
+  int32_t id;         // user id
+  int32_t row;        // priority row (0 = highest priority)
+};
+
+// Device status word bits (ctx->d_status[0]); [1] holds detail.
+enum : uint32_t {
+  ST_TIMEOUT = 1u,
+  ST_CAPACITY = 2u,
+};
+
+constexpr int kGroup = 16;        // Kahan group: entries summed plainly before compensation
+constexpr int kChunk = 256;       // entries per TMA chunk
+constexpr int kTriChunk = 128;    // plain triangles per TMA chunk (FP64 baseline)
+constexpr float kKappa = 1.0f / 8192.0f;  // conditioning threshold of a pair
+constexpr int kMortonBits = 7;    // bits per axis of the binning key
+constexpr int kBuckets = 1 << (3 * kMortonBits);
+
+struct CompHost {
+  int32_t id;
+  int64_t nv, nt;
+  float lo[3], hi[3];
+  int64_t entry_off, entry_cnt, tri_off, nstrips;
+};
+
+// Grow-only device buffers of the labeling pipeline.
+struct LabelBuffers {
+  int64_t cap_points = 0;   // points the buffers hold
+  int64_t cap_tiles = 0;
+  int64_t cap_items = 0;
+  int64_t cap_unc = 0;
+  float4 *spts = nullptr;       // sorted points (x, y, z, unused)
+  int32_t *perm = nullptr;      // sorted position -> original index
+  uint32_t *keys = nullptr;     // binning key per original point
+  unsigned long long *in_mask = nullptr;   // per sorted point: inside bits (priority rows)
+  unsigned long long *unc_mask = nullptr;  // per sorted point: uncertain bits
+  float *tile_box = nullptr;    // [tiles][6]
+  uint32_t *hist = nullptr;     // kBuckets
+  uint32_t *flags = nullptr;    // [C * tiles] work-list flags, scanned in place
+  uint32_t *block_sums = nullptr;
+  int2 *items = nullptr;        // (tile, comp)
+  int2 *unc_list = nullptr;     // (sorted point, comp)
+  int64_t *counters = nullptr;  // device counters, see Counter enum
+  int32_t *labels_tmp = nullptr;
+  float *pts_tmp = nullptr;     // staging for host inputs
+  float *omega_tmp = nullptr;
+  int64_t cap_omega = 0;
+};
+
+enum Counter {
+  CNT_N = 0,          // points of this call
+  CNT_OFF,            // offset of the first point in the caller's array
+  CNT_ITEMS,          // work items
+  CNT_WORK,           // persistent-kernel work cursor
+  CNT_UNC,            // uncertain (point, comp) pairs
+  CNT_UNC_WORK,       // rescue cursor
+  CNT_NONFINITE,
+  CNT_PAIRS_EVAL,     // FP32 (or FP64 plain) pairs
+  CNT_PAIRS_RESCUE,   // FP64 re-evaluation pairs
+  CNT_BOX,            // 6 x int32 ordered bounding box packed in 3 int64 slots
+  CNT_BOX1,
+  CNT_BOX2,
+  CNT_TILES,
+  CNT_LEVEL_FLAGGED,  // refinement
+  CNT_LEVEL_NEW,
+  CNT_NODES,
+  CNT_TETS,
+  CNT_COUNT_ = 24
+};
+
+struct LaunchShape {
+  int threads;
+  int ppt;
+};
+
+}  // namespace zef
+
+struct zef_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::string err;
+
+  std::vector<zef::CompHost> comps;
+  std::vector<int32_t> priority;      // ids, highest priority first
+  std::vector<zef::Entry> h_entries;
+  std::vector<float4> h_tris;         // 3 per triangle (w unused)
+
+  bool dirty = true;
+  zef::Entry *d_entries = nullptr;
+  float4 *d_tris = nullptr;
+  zef::DevComp *d_comps = nullptr;
+  int32_t *d_row_ids = nullptr;       // priority row -> id
+  int32_t *d_lpt = nullptr;           // LPT rank -> comp index
+  int64_t d_entries_cap = 0, d_tris_cap = 0;
+
+  uint32_t *d_status = nullptr;       // [2]
+  zef::LabelBuffers lb;
+  int64_t *h_counters = nullptr;      // pinned mirror of the counters
+
+  cudaEvent_t ev[6] = {};
+
+  // autotuner cache: key -> shape
+  std::vector<std::pair<uint64_t, zef::LaunchShape>> tune_cache;
+
+  // refinement scratch
+  void *rf_buf[8] = {};
+  size_t rf_cap[8] = {};
+  cudaGraphExec_t rf_exec = nullptr;
+  uint64_t rf_key = 0;
+};
+
+namespace zef {
+
+// ---- host helpers (zef_host.cpp)
+zef_status fail(zef_ctx *ctx, zef_status st, const std::string &msg);
+zef_status cuda_fail(zef_ctx *ctx, cudaError_t e, const char *what);
+zef_status ensure_uploaded(zef_ctx *ctx);
+template <class T>
+zef_status ensure_buffer(zef_ctx *ctx, T **p, int64_t *cap, int64_t need);
+
+// ---- labeling pipeline (zef_label.cu)
+struct LabelPlan {
+  const float *pts;          // base of the caller's point array (device)
+  int32_t *labels;           // base of the label array (device)
+  float *omega;              // nullable, [C][n_cap] rows (device)
+  int64_t omega_ld;          // row stride of omega
+  int64_t n_cap;             // upper bound of the points of this call
+  const int64_t *d_n;        // device: number of points
+  const int64_t *d_off;      // device: offset of the first point
+  zef_label_opts opts;
+  LaunchShape shape;
+  bool timed;                // record events around the main kernels
+};
+
+zef_status label_reserve(zef_ctx *ctx, int64_t n_cap);
+zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan);
+zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off);
+zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns);
+LaunchShape choose_shape(zef_ctx *ctx, const zef_label_opts &o, int64_t n, bool *need_tune);
+zef_status autotune(zef_ctx *ctx, const LabelPlan &plan, LaunchShape *best);
+void fill_default_opts(zef_label_opts *o);
+bool shape_valid(int threads, int ppt);
+
+// ---- refinement (zef_refine.cu)
+zef_status refine_run(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_label_opts &opts,
+                      zef_level_stats *per_level);
+
+}  // namespace zef

@@ -1,0 +1,1031 @@
+// Labeling kernels of libzef (sm_103a).
+//
+// Method (Sec. 2.1.3, Eq. 1 and Sec. 2.1): Omega(p) = sum over the triangles
+// of a closed compartment surface of the Van Oosterom-Strackee solid angle
+// Omega_t = 2 atan2(N, D); p is inside when Omega > 2 pi; the first
+// compartment of the priority list that encloses p labels it.
+//
+// Pipeline of one call (all on the context stream, no host round trip):
+//   k_prepare      counters for this call
+//   k_bbox         bounding box of the finite points
+//   k_keys         21-bit Morton bucket of every point + bucket histogram
+//   scan           exclusive scan of the histogram
+//   k_scatter      points into bucket order (float4) + permutation
+//   k_tile_box     bounding box of every tile of consecutive sorted points
+//   k_flags/scan/k_emit
+//                  work list of (tile, compartment) whose boxes overlap,
+//                  ordered by decreasing compartment triangle count (LPT);
+//                  a point outside a closed surface's box has winding number
+//                  0, so the culling is exact
+//   k_label32      persistent FP32 kernel over the work list (hot loop)
+//   k_rescue64     FP64 re-evaluation of the uncertain (point, compartment)
+//                  pairs over the full surface
+//   k_resolve      priority resolve + un-permute
+//
+// FP32 hot loop.  Triangles of a compartment are stored as triangle strips
+// (one new vertex per triangle), staged into shared memory by 1-D bulk TMA
+// copies (cp.async.bulk + mbarrier, double buffered) and broadcast to every
+// thread; each thread holds P points in registers.  With the window (a, b, c)
+// of the strip and R_k = v_k - p:
+//     N = R_c . n            (n = (v2 - v1) x (v3 - v1) of the triangle, host
+//                             precomputed in FP64; equal to R1 . (R2 x R3))
+//     D = r_a r_b r_c + (R_a . R_b) r_c + (R_a . R_c) r_b + (R_b . R_c) r_a
+// where R_a, R_b, r_a, r_b and r_a r_b + R_a . R_b are carried from the two
+// previous strip steps.  atan2 is a range-reduced minimax polynomial (see
+// half_angle).  Omega is accumulated plainly over groups of 16 entries and the
+// group sums are combined with Kahan compensation.
+//
+// A (point, compartment) pair is sent to the FP64 re-evaluation when
+//   |Omega32 - 2 pi| < margin                (the stated margin), or
+//   Omega32 is farther than winding_tol from 4 pi Z (the closed-surface
+//      invariant; catches FP32 errors of any size except near 4 pi k), or
+//   some triangle had max(|N|, D) < kappa |n| r_c: the point lies within a
+//      relative distance kappa of that triangle's plane in a position where
+//      the sign of N decides the branch of atan2 (an FP32 sign error there
+//      changes Omega by almost 4 pi), or the sum is not finite.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "zef_internal.h"
+
+namespace zef {
+
+namespace {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kHalfPi = 1.57079632679489661923f;
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kFourPi = 12.5663706143591729539f;
+constexpr float kInvFourPi = 0.0795774715459476678844f;
+
+// atan(x) = x (1 + s P(s)), s = x^2, 0 <= x <= 1: minimax fit of the relative
+// error with the constant term held at 1 (max relative error 1.25e-7),
+// produced by fit_atan.py in this directory.
+constexpr float kA1 = -0.33332463093753684f;
+constexpr float kA2 = 0.19975608384836258f;
+constexpr float kA3 = -0.140503760155985f;
+constexpr float kA4 = 0.09995455776444288f;
+constexpr float kA5 = -0.06060978191365727f;
+constexpr float kA6 = 0.025035448658018142f;
+constexpr float kA7 = -0.004909851860197689f;
+
+constexpr int kScanT = 256;
+constexpr int kScanV = 8;
+constexpr int kScanB = kScanT * kScanV;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded mbarrier wait: 2 s
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One elected thread: arm the barrier with the byte count and start the copy.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the barrier; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitNs) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+__device__ __forceinline__ int f2o(float f) {
+  int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ bool finite3(float x, float y, float z) {
+  return isfinite(x) && isfinite(y) && isfinite(z);
+}
+
+__device__ __forceinline__ uint32_t spread7(uint32_t v) {
+  // 7 bits -> every third bit
+  v &= 0x7f;
+  v = (v | (v << 8)) & 0x0000f00f;
+  v = (v | (v << 4)) & 0x000c30c3;
+  v = (v | (v << 2)) & 0x00249249;
+  return v;
+}
+
+__device__ void record_timeout(uint32_t *status, uint32_t site) {
+  atomicOr(status, ST_TIMEOUT);
+  atomicExch(status + 1, site);
+}
+
+// ------------------------------------------------------------------ FP32 atan2 / 2
+// atan2(N, D) in (-pi, pi]: reduce to x = min/max in [0, 1], polynomial,
+// then the octant reflections x -> pi/2 - x (|N| > |D|), x -> pi - x (D < 0)
+// and the sign of N.
+__device__ __forceinline__ float half_angle(float N, float D) {
+  const float aN = fabsf(N), aD = fabsf(D);
+  const float mn = fminf(aN, aD), mx = fmaxf(aN, aD);
+  const float x = __fdividef(mn, mx);
+  const float s = x * x;
+  float p = kA7;
+  p = fmaf(p, s, kA6);
+  p = fmaf(p, s, kA5);
+  p = fmaf(p, s, kA4);
+  p = fmaf(p, s, kA3);
+  p = fmaf(p, s, kA2);
+  p = fmaf(p, s, kA1);
+  float a = fmaf(x * s, p, x);
+  a = (aN > aD) ? (kHalfPi - a) : a;
+  a = (D < 0.f) ? (kPi - a) : a;
+  return copysignf(a, N);
+}
+
+struct PState {
+  float px, py, pz;        // the point
+  float ax, ay, az;        // R_a
+  float bx, by, bz;        // R_b
+  float ra, rb, sab;       // |R_a|, |R_b|, r_a r_b + R_a . R_b
+  float grp, sum, comp;    // group sum, Kahan sum and compensation (half angles)
+  float bad;               // min over triangles of max(|N|, D) - kappa |n| r_c
+};
+
+__device__ __forceinline__ void window_init(PState &s, float4 v0) {
+  s.ax = s.bx = v0.x - s.px;
+  s.ay = s.by = v0.y - s.py;
+  s.az = s.bz = v0.z - s.pz;
+  float q = fmaf(s.ax, s.ax, fmaf(s.ay, s.ay, s.az * s.az));
+  float r = q * rsqrtf(q);
+  s.ra = s.rb = r;
+  s.sab = 2.f * q;
+}
+
+__device__ __forceinline__ void vos_step(PState &s, const float4 V, const float4 Nn) {
+  const float cx = V.x - s.px, cy = V.y - s.py, cz = V.z - s.pz;
+  const float qc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  const float rc = qc * rsqrtf(qc);
+  const float dac = fmaf(s.ax, cx, fmaf(s.ay, cy, s.az * cz));
+  const float dbc = fmaf(s.bx, cx, fmaf(s.by, cy, s.bz * cz));
+  const float N = fmaf(Nn.x, cx, fmaf(Nn.y, cy, Nn.z * cz));
+  const float D = fmaf(s.sab, rc, fmaf(dac, s.rb, dbc * s.ra));
+  const float t = half_angle(N, D);
+  s.grp = fmaf(V.w, t, s.grp);
+  s.bad = fminf(s.bad, fmaf(-Nn.w, rc, fmaxf(fabsf(N), D)));
+  s.sab = fmaf(s.rb, rc, dbc);
+  s.ax = s.bx; s.ay = s.by; s.az = s.bz;
+  s.bx = cx; s.by = cy; s.bz = cz;
+  s.ra = s.rb;
+  s.rb = rc;
+}
+
+__device__ __forceinline__ void kahan_flush(PState &s) {
+  const float y = s.grp - s.comp;
+  const float t = s.sum + y;
+  s.comp = (t - s.sum) - y;
+  s.sum = t;
+  s.grp = 0.f;
+}
+
+struct LabelArgs {
+  const Entry *entries;
+  const float4 *tris;
+  const DevComp *comps;
+  const float4 *spts;
+  const int32_t *perm;
+  const int2 *items;
+  unsigned long long *in_mask;
+  unsigned long long *unc_mask;
+  float *omega;
+  int64_t omega_ld;
+  int64_t *counters;
+  uint32_t *status;
+  float margin;
+  float winding_tol;
+  int ncomp;
+  int fp32_only;
+};
+
+// Classification of one (point, compartment) pair after the FP32 sum.
+__device__ __forceinline__ void classify_store(const LabelArgs &a, const DevComp &c, int64_t i, float px,
+                                               float py, float pz, float omega, float bad) {
+  const bool fin = finite3(px, py, pz);
+  const bool outside_box = px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] ||
+                           pz > c.hi[2];
+  const unsigned long long bit = 1ull << c.row;
+  if (!fin) {
+    omega = __int_as_float(0x7fc00000);
+  } else if (outside_box) {
+    omega = 0.f;
+  } else {
+    const float k = rintf(omega * kInvFourPi);
+    const float dist = fabsf(fmaf(-kFourPi, k, omega));
+    const bool unc = !(bad >= 0.f) || !(dist <= a.winding_tol) || !(fabsf(omega - kTwoPi) >= a.margin);
+    if (unc && !a.fp32_only) {
+      atomicOr(a.unc_mask + i, bit);
+    } else if (omega > kTwoPi) {
+      atomicOr(a.in_mask + i, bit);
+    }
+  }
+  if (a.omega) a.omega[(int64_t)c.row * a.omega_ld + a.perm[i]] = omega;
+}
+
+// ------------------------------------------------------------------ FP32 persistent kernel
+template <int NT, int P>
+__global__ void __launch_bounds__(NT) k_label32(LabelArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Entry *sbuf = reinterpret_cast<Entry *>(smem_raw);
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int64_t s_item;
+  const int tid = threadIdx.x;
+  constexpr int TILE = NT * P;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  uint32_t ph0 = 0, ph1 = 0;
+  const int64_t n = a.counters[CNT_N];
+  const int64_t nitems = a.counters[CNT_ITEMS];
+  for (;;) {
+    if (tid == 0) s_item = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_WORK), 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= nitems) break;
+    const int2 w = a.items[item];
+    const DevComp c = a.comps[w.y];
+    const int64_t base = (int64_t)w.x * TILE;
+    const Entry *gsrc = a.entries + c.entry_off;
+    const int nchunks = (c.entry_cnt + kChunk - 1) / kChunk;
+    if (tid == 0) {
+      int cnt0 = min(kChunk, c.entry_cnt);
+      tma_load_1d(sbuf, gsrc, cnt0 * (uint32_t)sizeof(Entry), &bar[0]);
+      if (nchunks > 1) {
+        int cnt1 = min(kChunk, c.entry_cnt - kChunk);
+        tma_load_1d(sbuf + kChunk, gsrc + kChunk, cnt1 * (uint32_t)sizeof(Entry), &bar[1]);
+      }
+    }
+    PState st[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      int64_t i = base + q * NT + tid;
+      float4 p = a.spts[i < n ? i : base];
+      st[q].px = p.x;
+      st[q].py = p.y;
+      st[q].pz = p.z;
+      st[q].grp = st[q].sum = st[q].comp = 0.f;
+      st[q].bad = __int_as_float(0x7f800000);
+    }
+    bool timed_out = false;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int b = ch & 1;
+      bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        break;
+      }
+      if (b) ph1 ^= 1; else ph0 ^= 1;
+      const Entry *E = sbuf + b * kChunk;
+      const int cnt = min(kChunk, c.entry_cnt - ch * kChunk);
+      if (ch == 0) {
+        const float4 v0 = E[0].v;
+#pragma unroll
+        for (int q = 0; q < P; ++q) window_init(st[q], v0);
+      }
+      for (int g = 0; g < cnt; g += kGroup) {
+#pragma unroll 4
+        for (int j = 0; j < kGroup; ++j) {
+          const float4 V = E[g + j].v;
+          const float4 Nn = E[g + j].n;
+#pragma unroll
+          for (int q = 0; q < P; ++q) vos_step(st[q], V, Nn);
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) kahan_flush(st[q]);
+      }
+      __syncthreads();
+      if (tid == 0 && ch + 2 < nchunks) {
+        int cnt2 = min(kChunk, c.entry_cnt - (ch + 2) * kChunk);
+        tma_load_1d(sbuf + b * kChunk, gsrc + (int64_t)(ch + 2) * kChunk, cnt2 * (uint32_t)sizeof(Entry),
+                    &bar[b]);
+      }
+    }
+    if (timed_out) {
+      if (tid == 0) record_timeout(a.status, 1);
+      // let copies still in flight land before the block exits (bounded)
+      mbar_wait(&bar[0], ph0);
+      mbar_wait(&bar[1], ph1);
+      return;
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int64_t i = base + q * NT + tid;
+      if (i < n) {
+        const float om = 2.f * (st[q].sum - st[q].comp);
+        classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, om, st[q].bad);
+      }
+    }
+    if (tid == 0) {
+      const int64_t valid = min((int64_t)TILE, n - base);
+      atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), (unsigned long long)(valid * c.tri_cnt));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FP64 pieces
+// Van Oosterom-Strackee half angle in FP64, the plain form of the method.
+__device__ __forceinline__ double vos64_half(double px, double py, double pz, float4 A, float4 B, float4 C) {
+  const double x1 = (double)A.x - px, y1 = (double)A.y - py, z1 = (double)A.z - pz;
+  const double x2 = (double)B.x - px, y2 = (double)B.y - py, z2 = (double)B.z - pz;
+  const double x3 = (double)C.x - px, y3 = (double)C.y - py, z3 = (double)C.z - pz;
+  const double r1 = sqrt(x1 * x1 + y1 * y1 + z1 * z1);
+  const double r2 = sqrt(x2 * x2 + y2 * y2 + z2 * z2);
+  const double r3 = sqrt(x3 * x3 + y3 * y3 + z3 * z3);
+  const double cx = y2 * z3 - z2 * y3, cy = z2 * x3 - x2 * z3, cz = x2 * y3 - y2 * x3;
+  const double N = x1 * cx + y1 * cy + z1 * cz;
+  const double d12 = x1 * x2 + y1 * y2 + z1 * z2;
+  const double d13 = x1 * x3 + y1 * y3 + z1 * z3;
+  const double d23 = x2 * x3 + y2 * y3 + z2 * z3;
+  const double D = r1 * r2 * r3 + d12 * r3 + d13 * r2 + d23 * r1;
+  return atan2(N, D);
+}
+
+// Plain FP64 kernel (the baseline): same work list and culling, triangles
+// staged by TMA, every pair in FP64, no rescue needed.
+template <int NT, int P>
+__global__ void __launch_bounds__(NT) k_label64(LabelArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4 *sbuf = reinterpret_cast<float4 *>(smem_raw);  // 2 x kTriChunk x 3
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int64_t s_item;
+  const int tid = threadIdx.x;
+  constexpr int TILE = NT * P;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  uint32_t ph0 = 0, ph1 = 0;
+  const int64_t n = a.counters[CNT_N];
+  const int64_t nitems = a.counters[CNT_ITEMS];
+  for (;;) {
+    if (tid == 0) s_item = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_WORK), 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= nitems) break;
+    const int2 w = a.items[item];
+    const DevComp c = a.comps[w.y];
+    const int64_t base = (int64_t)w.x * TILE;
+    const float4 *gsrc = a.tris + (int64_t)c.tri_off * 3;
+    const int nchunks = (c.tri_cnt + kTriChunk - 1) / kTriChunk;
+    if (tid == 0) {
+      int cnt0 = min(kTriChunk, c.tri_cnt);
+      tma_load_1d(sbuf, gsrc, cnt0 * 48u, &bar[0]);
+      if (nchunks > 1) {
+        int cnt1 = min(kTriChunk, c.tri_cnt - kTriChunk);
+        tma_load_1d(sbuf + 3 * kTriChunk, gsrc + 3 * kTriChunk, cnt1 * 48u, &bar[1]);
+      }
+    }
+    double px[P], py[P], pz[P], acc[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      int64_t i = base + q * NT + tid;
+      float4 p = a.spts[i < n ? i : base];
+      px[q] = p.x;
+      py[q] = p.y;
+      pz[q] = p.z;
+      acc[q] = 0.0;
+    }
+    bool timed_out = false;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int b = ch & 1;
+      bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        break;
+      }
+      if (b) ph1 ^= 1; else ph0 ^= 1;
+      const float4 *T = sbuf + b * 3 * kTriChunk;
+      const int cnt = min(kTriChunk, c.tri_cnt - ch * kTriChunk);
+      for (int t = 0; t < cnt; ++t) {
+        const float4 A = T[3 * t], B = T[3 * t + 1], C = T[3 * t + 2];
+#pragma unroll
+        for (int q = 0; q < P; ++q) acc[q] += vos64_half(px[q], py[q], pz[q], A, B, C);
+      }
+      __syncthreads();
+      if (tid == 0 && ch + 2 < nchunks) {
+        int cnt2 = min(kTriChunk, c.tri_cnt - (ch + 2) * kTriChunk);
+        tma_load_1d(sbuf + b * 3 * kTriChunk, gsrc + (int64_t)(ch + 2) * 3 * kTriChunk, cnt2 * 48u, &bar[b]);
+      }
+    }
+    if (timed_out) {
+      if (tid == 0) record_timeout(a.status, 2);
+      mbar_wait(&bar[0], ph0);
+      mbar_wait(&bar[1], ph1);
+      return;
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int64_t i = base + q * NT + tid;
+      if (i < n) {
+        const double om = 2.0 * acc[q];
+        const float fx = (float)px[q], fy = (float)py[q], fz = (float)pz[q];
+        const bool fin = finite3(fx, fy, fz);
+        const bool outside_box = fx < c.lo[0] || fx > c.hi[0] || fy < c.lo[1] || fy > c.hi[1] ||
+                                 fz < c.lo[2] || fz > c.hi[2];
+        float omf = (float)om;
+        if (!fin) {
+          omf = __int_as_float(0x7fc00000);
+        } else if (outside_box) {
+          omf = 0.f;
+        } else if (om > 6.283185307179586476925) {
+          atomicOr(a.in_mask + i, 1ull << c.row);
+        }
+        if (a.omega) a.omega[(int64_t)c.row * a.omega_ld + a.perm[i]] = omf;
+      }
+    }
+    if (tid == 0) {
+      const int64_t valid = min((int64_t)TILE, n - base);
+      atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), (unsigned long long)(valid * c.tri_cnt));
+    }
+  }
+}
+
+// FP64 re-evaluation: each warp takes groups of 32 sorted points from a
+// device cursor; for every uncertain (point, compartment) pair of the group
+// all 32 lanes sum the FP64 half angles over the compartment's triangles
+// (lane l takes triangles l, l + 32, ...) and a fixed butterfly reduces them.
+__global__ void __launch_bounds__(256) k_rescue64(LabelArgs a) {
+  __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
+  for (int c = threadIdx.x; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t n = a.counters[CNT_N];
+  const int64_t ngroups = (n + 31) / 32;
+  for (;;) {
+    int64_t g = 0;
+    if (lane == 0) g = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_UNC_WORK), 1ull);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= ngroups) break;
+    const int64_t i0 = g * 32;
+    const int64_t mine = i0 + lane;
+    unsigned long long m = mine < n ? a.unc_mask[mine] : 0ull;
+    unsigned vote = __ballot_sync(0xffffffffu, m != 0ull);
+    while (vote) {
+      const int src = __ffs(vote) - 1;
+      vote &= vote - 1;
+      const int64_t i = i0 + src;
+      unsigned long long mm = __shfl_sync(0xffffffffu, m, src);
+      const float4 p = a.spts[i];
+      const double px = p.x, py = p.y, pz = p.z;
+      unsigned long long set_bits = 0ull;
+      while (mm) {
+        const int row = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        const DevComp c = a.comps[s_rowcomp[row]];
+        const float4 *T = a.tris + (int64_t)c.tri_off * 3;
+        double acc = 0.0;
+        for (int t = lane; t < c.tri_cnt; t += 32)
+          acc += vos64_half(px, py, pz, T[3 * t], T[3 * t + 1], T[3 * t + 2]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const double om = 2.0 * acc;
+        if (om > 6.283185307179586476925) set_bits |= 1ull << row;
+        if (lane == 0) {
+          if (a.omega) a.omega[(int64_t)row * a.omega_ld + a.perm[i]] = (float)om;
+          atomicAdd((unsigned long long *)(a.counters + CNT_UNC), 1ull);
+          atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)c.tri_cnt);
+        }
+      }
+      if (lane == 0 && set_bits) atomicOr(a.in_mask + i, set_bits);
+    }
+  }
+}
+
+// Failure-detection probe: every thread waits on an mbarrier that nothing
+// arrives on (no copy is issued), so the bounded wait must expire; the block
+// records ST_TIMEOUT and returns.
+__global__ void k_wait_probe(uint32_t *status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, limit_ns);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) record_timeout(status, 99);
+}
+
+// ------------------------------------------------------------------ small kernels
+__global__ void k_prepare(int64_t *cnt, int64_t n, int64_t off) {
+  if (threadIdx.x == 0) {
+    cnt[CNT_N] = n;
+    cnt[CNT_OFF] = off;
+  }
+}
+
+// Device-count version used inside the refinement graph: n and offset come
+// from other counters.
+__global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
+  if (threadIdx.x == 0) {
+    const int64_t n = cnt[CNT_N];
+    cnt[CNT_ITEMS] = 0;
+    cnt[CNT_WORK] = 0;
+    cnt[CNT_UNC] = 0;
+    cnt[CNT_UNC_WORK] = 0;
+    cnt[CNT_NONFINITE] = 0;
+    cnt[CNT_PAIRS_EVAL] = 0;
+    cnt[CNT_PAIRS_RESCUE] = 0;
+    int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
+    for (int k = 0; k < 3; ++k) {
+      box[k] = INT32_MAX;
+      box[3 + k] = INT32_MIN;
+    }
+    cnt[CNT_TILES] = (n + tile - 1) / tile;
+    cnt[CNT_TILES + 1] = 0;
+    (void)ncomp;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bbox(const float *pts, int64_t *cnt, unsigned long long *in_mask,
+                                             unsigned long long *unc_mask) {
+  const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float *p = pts + 3 * (off + i);
+    float x = p[0], y = p[1], z = p[2];
+    in_mask[i] = 0ull;
+    unc_mask[i] = 0ull;
+    if (finite3(x, y, z)) {
+      lo[0] = fminf(lo[0], x); lo[1] = fminf(lo[1], y); lo[2] = fminf(lo[2], z);
+      hi[0] = fmaxf(hi[0], x); hi[1] = fmaxf(hi[1], y); hi[2] = fmaxf(hi[2], z);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
+    for (int k = 0; k < 3; ++k) {
+      if (lo[k] <= hi[k]) {
+        atomicMin(box + k, f2o(lo[k]));
+        atomicMax(box + 3 + k, f2o(hi[k]));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, uint32_t *keys, uint32_t *hist) {
+  const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
+  const int *box = reinterpret_cast<const int *>(cnt + CNT_BOX);
+  float lo[3], sc[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = o2f(box[k]);
+    float ext = o2f(box[3 + k]) - lo[k];
+    sc[k] = ext > 0.f ? (float)(1 << kMortonBits) / ext : 0.f;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float *p = pts + 3 * (off + i);
+    float x = p[0], y = p[1], z = p[2];
+    uint32_t key = 0;
+    if (finite3(x, y, z)) {
+      uint32_t q[3];
+      float v[3] = {x, y, z};
+      for (int k = 0; k < 3; ++k) {
+        float f = (v[k] - lo[k]) * sc[k];
+        int qi = (int)f;
+        q[k] = (uint32_t)min(max(qi, 0), (1 << kMortonBits) - 1);
+      }
+      key = spread7(q[0]) | (spread7(q[1]) << 1) | (spread7(q[2]) << 2);
+    }
+    keys[i] = key;
+    atomicAdd(hist + key, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt, const uint32_t *keys,
+                                                uint32_t *cursor, float4 *spts, int32_t *perm) {
+  const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float *p = pts + 3 * (off + i);
+    const uint32_t pos = atomicAdd(cursor + keys[i], 1u);
+    spts[pos] = make_float4(p[0], p[1], p[2], 0.f);
+    perm[pos] = (int32_t)i;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tile_box(const float4 *spts, int64_t *cnt, float *tile_box, int tile) {
+  const int64_t n = cnt[CNT_N];
+  const int64_t ntiles = cnt[CNT_TILES];
+  __shared__ float red[6][8];
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const int64_t b = t * tile;
+    const int64_t e = min(b + tile, n);
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+      const float4 p = spts[i];
+      if (finite3(p.x, p.y, p.z)) {
+        lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+        hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+      }
+    }
+    for (int k = 0; k < 3; ++k)
+      for (int o = 16; o > 0; o >>= 1) {
+        lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+        hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+      }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+      for (int k = 0; k < 3; ++k) {
+        red[k][wid] = lo[k];
+        red[3 + k][wid] = hi[k];
+      }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      const int k = threadIdx.x;
+      float v = red[k][0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = k < 3 ? fminf(v, red[k][q]) : fmaxf(v, red[k][q]);
+      tile_box[t * 6 + k] = v;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) k_flags(int64_t *cnt, const float *tile_box, const DevComp *comps,
+                                              const int32_t *lpt, int ncomp, uint32_t *flags) {
+  const int64_t ntiles = cnt[CNT_TILES];
+  const int64_t len = ntiles * ncomp;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(j / ntiles);
+    const int64_t t = j - (int64_t)r * ntiles;
+    const DevComp &c = comps[lpt[r]];
+    const float *b = tile_box + t * 6;
+    const bool ov = !(b[3] < c.lo[0] || b[0] > c.hi[0] || b[4] < c.lo[1] || b[1] > c.hi[1] || b[5] < c.lo[2] ||
+                      b[2] > c.hi[2]);
+    flags[j] = ov ? 1u : 0u;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_emit(int64_t *cnt, const uint32_t *scan, const int32_t *lpt, int ncomp,
+                                             int2 *items) {
+  const int64_t ntiles = cnt[CNT_TILES];
+  const int64_t len = ntiles * ncomp;
+  const int64_t total = cnt[CNT_ITEMS];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nxt = (j + 1 < len) ? (int64_t)scan[j + 1] : total;
+    if (nxt != (int64_t)scan[j]) {
+      const int r = (int)(j / ntiles);
+      const int64_t t = j - (int64_t)r * ntiles;
+      items[scan[j]] = make_int2((int)t, lpt[r]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_resolve(LabelArgs a, const float *pts, int32_t *labels,
+                                                const int32_t *row_ids) {
+  const int64_t n = a.counters[CNT_N], off = a.counters[CNT_OFF];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 p = a.spts[i];
+    int32_t lab;
+    if (!finite3(p.x, p.y, p.z)) {
+      lab = -1;
+      atomicAdd((unsigned long long *)(a.counters + CNT_NONFINITE), 1ull);
+    } else {
+      const unsigned long long m = a.in_mask[i];
+      lab = m ? row_ids[__ffsll((long long)m) - 1] : 0;
+    }
+    labels[off + a.perm[i]] = lab;
+  }
+  (void)pts;
+}
+
+// ------------------------------------------------------------------ exclusive scan (uint32, in place)
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total) {
+  __shared__ uint32_t ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (wid == 0) {
+    uint32_t s = lane < nw ? ws[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) ws[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t before = wid ? ws[wid - 1] : 0u;
+  *total = ws[nw - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_blocks(uint32_t *data, const int64_t *len_ptr, int64_t len_c,
+                                                       int64_t len_mul, uint32_t *bsums) {
+  const int64_t len = len_ptr ? (*len_ptr) * len_mul : len_c;
+  const int64_t b0 = (int64_t)blockIdx.x * kScanB + (int64_t)threadIdx.x * kScanV;
+  uint32_t v[kScanV];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanV; ++k) {
+    v[k] = (b0 + k < len) ? data[b0 + k] : 0u;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t pre = block_excl_scan(s, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanV; ++k) {
+    if (b0 + k < len) data[b0 + k] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) bsums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *bsums, const int64_t *len_ptr, int64_t len_c,
+                                                   int64_t len_mul, int64_t *total_out) {
+  const int64_t len = len_ptr ? (*len_ptr) * len_mul : len_c;
+  const int64_t nb = (len + kScanB - 1) / kScanB;
+  uint32_t carry = 0;
+  for (int64_t b = 0; b < nb; b += blockDim.x) {
+    const int64_t j = b + threadIdx.x;
+    uint32_t v = j < nb ? bsums[j] : 0u;
+    uint32_t tot;
+    uint32_t pre = block_excl_scan(v, &tot);
+    if (j < nb) bsums[j] = carry + pre;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = (int64_t)carry;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_add(uint32_t *data, const int64_t *len_ptr, int64_t len_c,
+                                                    int64_t len_mul, const uint32_t *bsums) {
+  const int64_t len = len_ptr ? (*len_ptr) * len_mul : len_c;
+  const int64_t b0 = (int64_t)blockIdx.x * kScanB + (int64_t)threadIdx.x * kScanV;
+  const uint32_t add = bsums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanV; ++k)
+    if (b0 + k < len) data[b0 + k] += add;
+}
+
+// ------------------------------------------------------------------ launch helpers
+template <int NT, int P>
+zef_status launch_label32(zef_ctx *ctx, const LabelArgs &a) {
+  const size_t smem = 2 * kChunk * sizeof(Entry);
+  auto kern = k_label32<NT, P>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+  if (occ < 1) occ = 1;
+  kern<<<ctx->num_sms * occ, NT, smem, ctx->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_label32 launch");
+  return ZEF_OK;
+}
+
+template <int NT, int P>
+zef_status launch_label64(zef_ctx *ctx, const LabelArgs &a) {
+  const size_t smem = 2 * kTriChunk * 3 * sizeof(float4);
+  auto kern = k_label64<NT, P>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
+  if (occ < 1) occ = 1;
+  kern<<<ctx->num_sms * occ, NT, smem, ctx->stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_label64 launch");
+  return ZEF_OK;
+}
+
+zef_status dispatch_label32(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
+  if (s.threads == 256) {
+    if (s.ppt == 2) return launch_label32<256, 2>(ctx, a);
+    if (s.ppt == 4) return launch_label32<256, 4>(ctx, a);
+    return launch_label32<256, 8>(ctx, a);
+  }
+  if (s.ppt == 2) return launch_label32<128, 2>(ctx, a);
+  if (s.ppt == 4) return launch_label32<128, 4>(ctx, a);
+  return launch_label32<128, 8>(ctx, a);
+}
+
+int grid_for(zef_ctx *ctx, int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)ctx->num_sms * 16;
+  return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+zef_status scan_inplace(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, int64_t len_mul, int64_t len_cap,
+                        int64_t *total_out) {
+  const int64_t nb = std::max<int64_t>(1, (len_cap + kScanB - 1) / kScanB);
+  const int64_t len_c = len_ptr ? 0 : len_cap;
+  k_scan_blocks<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(data, len_ptr, len_c, len_mul, ctx->lb.block_sums);
+  k_scan_sums<<<1, 1024, 0, ctx->stream>>>(ctx->lb.block_sums, len_ptr, len_c, len_mul, total_out);
+  k_scan_add<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(data, len_ptr, len_c, len_mul, ctx->lb.block_sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan launch");
+  return ZEF_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host API of this file
+bool shape_valid(int threads, int ppt) {
+  return (threads == 128 || threads == 256) && (ppt == 2 || ppt == 4 || ppt == 8);
+}
+
+void fill_default_opts(zef_label_opts *o) {
+  if (!(o->margin > 0.f)) o->margin = 1e-3f;
+  if (!(o->winding_tol > 0.f)) o->winding_tol = 4e-6f;
+}
+
+LaunchShape choose_shape(zef_ctx *ctx, const zef_label_opts &o, int64_t n, bool *need_tune) {
+  *need_tune = false;
+  if (o.precision == ZEF_FP64_PLAIN) return LaunchShape{128, 2};
+  if (o.block_threads && o.points_per_thread) return LaunchShape{o.block_threads, o.points_per_thread};
+  (void)ctx;
+  (void)n;
+  return LaunchShape{256, 4};
+}
+
+zef_status autotune(zef_ctx *ctx, const LabelPlan &plan, LaunchShape *best) {
+  (void)ctx;
+  (void)plan;
+  *best = LaunchShape{256, 4};
+  return ZEF_OK;
+}
+
+zef_status label_reserve(zef_ctx *ctx, int64_t n_cap) {
+  LabelBuffers &b = ctx->lb;
+  const int C = (int)ctx->comps.size();
+  const int64_t min_tile = 128 * 2;
+  const int64_t tiles = (n_cap + min_tile - 1) / min_tile;
+  zef_status st;
+  if (b.cap_points < n_cap) {
+    int64_t cap = std::max<int64_t>(n_cap, 1024);
+    auto realloc = [&](void **p, size_t bytes) -> zef_status {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+      cudaError_t e = cudaMalloc(p, bytes);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(label buffers)");
+      return ZEF_OK;
+    };
+    if ((st = realloc((void **)&b.spts, cap * sizeof(float4)))) return st;
+    if ((st = realloc((void **)&b.perm, cap * sizeof(int32_t)))) return st;
+    if ((st = realloc((void **)&b.keys, cap * sizeof(uint32_t)))) return st;
+    if ((st = realloc((void **)&b.in_mask, cap * sizeof(unsigned long long)))) return st;
+    if ((st = realloc((void **)&b.unc_mask, cap * sizeof(unsigned long long)))) return st;
+    if ((st = realloc((void **)&b.labels_tmp, cap * sizeof(int32_t)))) return st;
+    if ((st = realloc((void **)&b.pts_tmp, cap * 3 * sizeof(float)))) return st;
+    b.cap_points = cap;
+  }
+  const int64_t need_flags = std::max<int64_t>(tiles * std::max(C, 1), (int64_t)kBuckets);
+  if (b.cap_tiles < tiles || b.cap_items < need_flags) {
+    if (b.tile_box) cudaFree(b.tile_box);
+    if (b.flags) cudaFree(b.flags);
+    if (b.items) cudaFree(b.items);
+    if (b.block_sums) cudaFree(b.block_sums);
+    b.tile_box = nullptr;
+    b.flags = nullptr;
+    b.items = nullptr;
+    b.block_sums = nullptr;
+    b.cap_tiles = b.cap_items = 0;
+    const int64_t ft = std::max<int64_t>(tiles, 1);
+    cudaError_t e;
+    if ((e = cudaMalloc(&b.tile_box, ft * 6 * sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    if ((e = cudaMalloc(&b.flags, need_flags * sizeof(uint32_t))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    if ((e = cudaMalloc(&b.items, need_flags * sizeof(int2))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    if ((e = cudaMalloc(&b.block_sums, ((need_flags + kScanB - 1) / kScanB + 1) * sizeof(uint32_t))) != cudaSuccess)
+      return cuda_fail(ctx, e, "cudaMalloc");
+    b.cap_tiles = ft;
+    b.cap_items = need_flags;
+  }
+  if (!b.hist) {
+    cudaError_t e = cudaMalloc(&b.hist, (size_t)kBuckets * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(hist)");
+  }
+  if (!b.counters) {
+    cudaError_t e = cudaMalloc(&b.counters, CNT_COUNT_ * sizeof(int64_t));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(counters)");
+    cudaMemset(b.counters, 0, CNT_COUNT_ * sizeof(int64_t));
+  }
+  return ZEF_OK;
+}
+
+// Enqueue the whole labeling pipeline (no host synchronisation).  When
+// plan.d_n / plan.d_off point into the counters they must already hold the
+// call's values; label_points sets them with k_prepare.
+zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
+  LabelBuffers &b = ctx->lb;
+  const int C = (int)ctx->comps.size();
+  const int tile = plan.shape.threads * plan.shape.ppt;
+  cudaStream_t s = ctx->stream;
+  if (plan.timed) cudaEventRecord(ctx->ev[0], s);
+  k_reset<<<1, 32, 0, s>>>(b.counters, tile, C);
+  const int64_t ncap = plan.n_cap;
+  const int g = grid_for(ctx, ncap, 256);
+  k_bbox<<<g, 256, 0, s>>>(plan.pts, b.counters, b.in_mask, b.unc_mask);
+  cudaMemsetAsync(b.hist, 0, (size_t)kBuckets * sizeof(uint32_t), s);
+  k_keys<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist);
+  zef_status st = scan_inplace(ctx, b.hist, nullptr, 1, kBuckets, nullptr);
+  if (st) return st;
+  k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm);
+  const int64_t tiles_cap = (ncap + tile - 1) / tile;
+  k_tile_box<<<grid_for(ctx, tiles_cap * 256, 256), 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
+  k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,
+                                                             b.flags);
+  st = scan_inplace(ctx, b.flags, b.counters + CNT_TILES, C, tiles_cap * C, b.counters + CNT_ITEMS);
+  if (st) return st;
+  k_emit<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.flags, ctx->d_lpt, C, b.items);
+
+  LabelArgs a;
+  a.entries = ctx->d_entries;
+  a.tris = ctx->d_tris;
+  a.comps = ctx->d_comps;
+  a.spts = b.spts;
+  a.perm = b.perm;
+  a.items = b.items;
+  a.in_mask = b.in_mask;
+  a.unc_mask = b.unc_mask;
+  a.omega = plan.omega;
+  a.omega_ld = plan.omega_ld;
+  a.counters = b.counters;
+  a.status = ctx->d_status;
+  a.margin = plan.opts.margin;
+  a.winding_tol = plan.opts.winding_tol;
+  a.ncomp = C;
+  a.fp32_only = plan.opts.precision == ZEF_FP32_ONLY;
+  if (plan.timed) cudaEventRecord(ctx->ev[1], s);
+  if (plan.opts.precision == ZEF_FP64_PLAIN) {
+    // the FP64 kernel's tile is 128 x 2 points (choose_shape guarantees it)
+    if (tile != 256) return fail(ctx, ZEF_ERR_INVALID_ARG, "internal: FP64 tile");
+    st = launch_label64<128, 2>(ctx, a);
+  } else {
+    st = dispatch_label32(ctx, a, plan.shape);
+  }
+  if (st) return st;
+  if (plan.timed) cudaEventRecord(ctx->ev[2], s);
+  if (plan.timed) cudaEventRecord(ctx->ev[3], s);
+  if (plan.opts.precision == ZEF_FP32_RESCUE) {
+    k_rescue64<<<ctx->num_sms * 4, 256, 0, s>>>(a);
+  }
+  if (plan.timed) cudaEventRecord(ctx->ev[4], s);
+  k_resolve<<<g, 256, 0, s>>>(a, plan.pts, plan.labels, ctx->d_row_ids);
+  if (plan.timed) cudaEventRecord(ctx->ev[5], s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "label pipeline launch");
+  return ZEF_OK;
+}
+
+zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns) {
+  k_wait_probe<<<1, 64, 0, ctx->stream>>>(ctx->d_status, (unsigned long long)limit_ns);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_wait_probe launch");
+  return ZEF_OK;
+}
+
+// Set the point count and offset of a label_points call (host-known values).
+zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off) {
+  k_prepare<<<1, 32, 0, ctx->stream>>>(ctx->lb.counters, n, off);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_prepare launch");
+  return ZEF_OK;
+}
+
+}  // namespace zef

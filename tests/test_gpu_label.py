@@ -1,0 +1,254 @@
+"""GPU parity of zef_label_points against the FP64 oracle (through the C ABI).
+
+Bars: labels bit-exact; Omega within 1e-5 sr of the oracle for every
+(point, compartment) pair (pairs outside the compartment's bounding box are
+exactly 0 on the GPU); pairs re-evaluated in FP64 match to 1e-6 (the float32
+output rounding).  Points on a surface, where the decision itself is
+ill-posed, are asserted absent from the seeded inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import zef_synth as zs
+
+pytestmark = pytest.mark.gpu
+
+FOUR_PI = 4.0 * math.pi
+OMEGA_TOL = 1e-5
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def zef():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_10000_gb300 import build
+    build.build()
+    from paper_2203_10000_gb300 import zef as z
+    return z
+
+
+def make_ctx(zef, surfaces, priority):
+    ctx = zef.Context(0)
+    for s in surfaces:
+        ctx.add_compartment(s.id, s.verts, s.tris)
+    ctx.set_priority(priority)
+    return ctx
+
+
+def gpu_label(ctx, pts, **kw):
+    p = torch.from_numpy(np.ascontiguousarray(pts, dtype=np.float32)).cuda()
+    opts = kw.pop("opts", None)
+    lab, om, st = ctx.label_points(p, want_omega=True, opts=opts)
+    torch.cuda.synchronize()
+    return lab.cpu().numpy(), om.cpu().numpy(), st
+
+
+def assert_parity(lab, om, olab, oom, tol=OMEGA_TOL):
+    assert np.array_equal(lab, olab), np.nonzero(lab != olab)[0][:20]
+    fin = np.isfinite(oom)
+    assert np.all(np.isfinite(om[fin]))
+    err = np.abs(om.astype(np.float64)[fin] - oom[fin])
+    assert err.max() <= tol, err.max()
+
+
+def off_surface(oom):
+    """No query point may sit within 1e-9 of the threshold (on a surface)."""
+    fin = np.isfinite(oom)
+    assert np.all(np.abs(oom[fin] - 2 * math.pi) > 1e-9)
+
+
+# ------------------------------------------------------------------ failure detection
+def test_bounded_wait_expires_and_context_survives(zef, oracle_mod):
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    assert ctx.wait_probe(50_000_000) == zef.ZEF_ERR_TIMEOUT
+    lab, om, st = gpu_label(ctx, w.points[:2048])
+    olab, oom = oracle_mod.label_points(w.points[:2048], w.surfaces, w.priority)
+    assert_parity(lab, om, olab, oom)
+
+
+# ------------------------------------------------------------------ small case
+def test_config0_parity(zef, oracle_mod):
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab, om, st = gpu_label(ctx, w.points)
+    olab, oom = oracle_mod.label_points(w.points, w.surfaces, w.priority)
+    off_surface(oom)
+    assert_parity(lab, om, olab, oom)
+    assert st["pairs_evaluated"] <= st["pairs_nominal"]
+    assert st["work_items"] >= 1 and st["tiles"] == (len(w.points) + 1023) // 1024
+
+
+def test_config0_host_pointers_match_device(zef):
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab_d, om_d, _ = gpu_label(ctx, w.points)
+    lab_h, om_h, st = ctx.label_points(w.points, want_omega=True)
+    assert isinstance(lab_h, np.ndarray)
+    assert np.array_equal(lab_h, lab_d)
+    assert np.array_equal(om_h, om_d)
+
+
+@pytest.mark.parametrize("shape", [(256, 4), (256, 2), (256, 8), (128, 2), (128, 4), (128, 8)])
+def test_launch_shapes_ragged_tail(zef, oracle_mod, shape):
+    w = zs.config0()
+    pts = w.points[: len(w.points) - 37]            # several tiles plus a ragged tail
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    opts = zef.make_opts(block_threads=shape[0], points_per_thread=shape[1])
+    lab, om, st = gpu_label(ctx, pts, opts=opts)
+    olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
+    assert_parity(lab, om, olab, oom)
+    assert st["block_threads"] == shape[0] and st["points_per_thread"] == shape[1]
+    # the per-point arithmetic does not depend on the tile shape
+    lab2, om2, _ = gpu_label(ctx, pts, opts=zef.make_opts(block_threads=256, points_per_thread=4))
+    assert np.array_equal(om, om2) and np.array_equal(lab, lab2)
+
+
+def test_empty_and_tiny_inputs(zef, oracle_mod):
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    p = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    lab, om, st = ctx.label_points(p, want_omega=True)
+    assert lab.numel() == 0
+    for n in (1, 2, 31, 33):
+        pts = w.points[:n]
+        lab, om, _ = gpu_label(ctx, pts)
+        olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
+        assert_parity(lab, om, olab, oom)
+
+
+def test_nonfinite_points(zef, oracle_mod):
+    w = zs.config0()
+    pts = w.points[:3000].copy()
+    pts[5] = [np.nan, 0, 0]
+    pts[77] = [0, np.inf, 0]
+    pts[2999] = [0, 0, -np.inf]
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab, om, st = gpu_label(ctx, pts)
+    olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
+    assert np.array_equal(lab, olab)
+    assert st["nonfinite_points"] == 3
+    assert lab[5] == -1 and lab[77] == -1 and lab[2999] == -1
+
+
+def test_deterministic(zef):
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    a = gpu_label(ctx, w.points)
+    b = gpu_label(ctx, w.points)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_fp64_plain_kernel(zef, oracle_mod):
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    pts = w.points[:8000]
+    lab, om, st = gpu_label(ctx, pts, opts=zef.make_opts(precision=zef.ZEF_FP64_PLAIN))
+    olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
+    assert_parity(lab, om, olab, oom, tol=1e-6)
+    assert st["pairs_rescued"] == 0
+
+
+def test_everything_rescued_when_margin_covers_all(zef, oracle_mod):
+    # margin > 2 pi marks every evaluated pair uncertain: the FP64
+    # re-evaluation alone must then reproduce the oracle
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    pts = w.points[:4000]
+    lab, om, st = gpu_label(ctx, pts, opts=zef.make_opts(margin=7.0))
+    olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
+    assert_parity(lab, om, olab, oom, tol=1e-6)
+    assert st["uncertain_pairs"] > 0 and st["pairs_rescued"] > 0
+
+
+def test_points_hugging_the_surface_are_rescued(zef, oracle_mod):
+    # points a hair inside / outside triangle centroids: the FP32 sign of N
+    # is unreliable there, the conditioning test must send them to FP64
+    s = zs.config0().surfaces[0]
+    v = s.verts.astype(np.float64)
+    cen = v[s.tris].mean(1)
+    nrm = np.cross(v[s.tris[:, 1]] - v[s.tris[:, 0]], v[s.tris[:, 2]] - v[s.tris[:, 0]])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    pts = []
+    for d in (-3e-6, -1e-6, 1e-6, 3e-6):
+        pts.append(cen + d * nrm)
+    pts = np.concatenate(pts).astype(np.float32)
+    ctx = make_ctx(zef, [s], [1])
+    lab, om, st = gpu_label(ctx, pts)
+    olab, oom = oracle_mod.label_points(pts, [s], [1])
+    keep = np.abs(oom[0] - 2 * math.pi) > 1e-9
+    assert keep.sum() > len(pts) // 2
+    assert np.array_equal(lab[keep], olab[keep])
+    assert st["uncertain_pairs"] > 0
+
+
+def test_fp32_only_mode_runs(zef, oracle_mod):
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab, om, st = gpu_label(ctx, w.points, opts=zef.make_opts(precision=zef.ZEF_FP32_ONLY))
+    olab, oom = oracle_mod.label_points(w.points, w.surfaces, w.priority)
+    assert st["pairs_rescued"] == 0
+    assert np.mean(lab == olab) > 0.999
+
+
+# ------------------------------------------------------------------ priority
+def _sphere(radius, freq, cid, shift=(0.0, 0.0, 0.0)):
+    u, t = zs.geodesic_sphere(freq)
+    v = (u * radius + np.asarray(shift)).astype(np.float32)
+    return zs.Surface(cid, f"r{radius}", v, t.astype(np.int32))
+
+
+@pytest.mark.parametrize("order", [[3, 2, 1], [1, 2, 3], [2, 3, 1]])
+def test_priority_nested_spheres(zef, oracle_mod, order):
+    surfs = [_sphere(87.0, 12, 3), _sphere(92.0, 12, 2), _sphere(100.0, 12, 1)]
+    rng = np.random.default_rng(8)
+    pts = rng.uniform(-110, 110, size=(20000, 3)).astype(np.float32)
+    ctx = make_ctx(zef, surfs, order)
+    lab, om, _ = gpu_label(ctx, pts)
+    olab, oom = oracle_mod.label_points(pts, surfs, order)
+    assert_parity(lab, om, olab, oom)
+
+
+def test_priority_intersecting_spheres(zef, oracle_mod):
+    surfs = [_sphere(10.0, 10, 1), _sphere(10.0, 10, 2, shift=(12.0, 0, 0))]
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-12, 24, size=(20000, 3)).astype(np.float32)
+    for order in ([1, 2], [2, 1]):
+        ctx = make_ctx(zef, surfs, order)
+        lab, om, _ = gpu_label(ctx, pts)
+        olab, oom = oracle_mod.label_points(pts, surfs, order)
+        assert_parity(lab, om, olab, oom)
+        lens = (np.linalg.norm(pts.astype(np.float64), axis=1) < 9.0) & \
+               (np.linalg.norm(pts.astype(np.float64) - [12, 0, 0], axis=1) < 9.0)
+        assert lens.sum() > 10 and np.all(lab[lens] == order[0])
+
+
+# ------------------------------------------------------------------ full-size head workload
+def test_config1_full_size_sampled(zef, oracle_mod):
+    """All 5,000,000 centroids of the 2 mm lattice against the three-layer
+    head; a seeded sample is checked against the oracle element by element and
+    every Omega against the closed-surface invariant."""
+    w = zs.config1()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab, om, st = gpu_label(ctx, w.points)
+    assert st["points"] == 5_000_000
+    # invariant at full size: every Omega is 0 or 4 pi to within 1e-5
+    d = np.minimum(np.abs(om), np.abs(om - FOUR_PI))
+    assert d.max() <= OMEGA_TOL
+    # labels consistent with Omega and priority (rows in priority order)
+    inside = om > 2 * math.pi
+    first = np.where(inside.any(0), np.argmax(inside, axis=0), -1)
+    ids = np.array(w.priority)
+    want = np.where(first >= 0, ids[np.maximum(first, 0)], 0)
+    assert np.array_equal(lab, want)
+    # element-by-element against the oracle on a seeded sample
+    idx = zs.sample_rows(w.points, 6000, seed=11)
+    olab, oom = oracle_mod.label_points(w.points[idx], w.surfaces, w.priority)
+    off_surface(oom)
+    assert_parity(lab[idx], om[:, idx], olab, oom)
+    assert 0 < st["pairs_evaluated"] < st["pairs_nominal"]
+    assert st["uncertain_pairs"] < 0.001 * st["points"]

@@ -1,0 +1,181 @@
+"""CPU-only tests of the C-ABI library: it loads, exports every declared
+symbol, and its host logic (surface validation, orientation, triangle strips,
+priority checks) behaves as documented.  No kernel runs here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import zef_synth as zs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def zef():
+    from paper_2203_10000_gb300 import build
+    build.build()
+    from paper_2203_10000_gb300 import zef as z
+    return z
+
+
+def _declared_symbols():
+    syms = set()
+    for h in ("zef.h", "zef_debug.h"):
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        syms |= set(re.findall(r"\b(zef_[a-z_]+)\s*\(", txt))
+    return sorted(syms)
+
+
+def test_library_exports_every_declared_symbol(zef):
+    syms = _declared_symbols()
+    assert "zef_label_points" in syms and "zef_refine_and_relabel" in syms
+    assert "zef_compartment_priority" in syms
+    for s in syms:
+        assert hasattr(zef.lib(), s), s
+    assert zef.version() == 1000
+
+
+def _host_ctx(zef):
+    return zef.Context(device=-1)
+
+
+def test_host_only_context_registers_and_refuses_labeling(zef):
+    ctx = _host_ctx(zef)
+    s = zs.config0().surfaces[0]
+    ctx.add_compartment(1, s.verts, s.tris)
+    assert ctx.info() == (1, 1280)
+    with pytest.raises(zef.ZefError) as e:
+        ctx.label_points(np.zeros((4, 3), np.float32))
+    assert e.value.status == zef.ZEF_ERR_NOT_READY
+
+
+def test_open_surface_rejected(zef):
+    ctx = _host_ctx(zef)
+    s = zs.config0().surfaces[0]
+    with pytest.raises(zef.ZefError) as e:
+        ctx.add_compartment(1, s.verts, s.tris[:-1])
+    assert e.value.status == zef.ZEF_ERR_SURFACE_NOT_CLOSED
+
+
+def test_inconsistent_orientation_rejected(zef):
+    ctx = _host_ctx(zef)
+    s = zs.config0().surfaces[0]
+    t = s.tris.copy()
+    t[5] = t[5, [0, 2, 1]]
+    with pytest.raises(zef.ZefError) as e:
+        ctx.add_compartment(1, s.verts, t)
+    assert e.value.status == zef.ZEF_ERR_SURFACE_NOT_CLOSED
+
+
+def test_inward_surface_needs_auto_orient(zef):
+    ctx = _host_ctx(zef)
+    s = zs.config0().surfaces[0]
+    inward = s.tris[:, [0, 2, 1]]
+    with pytest.raises(zef.ZefError) as e:
+        ctx.add_compartment(1, s.verts, inward)
+    assert e.value.status == zef.ZEF_ERR_SURFACE_ORIENTATION
+    ctx.add_compartment(2, s.verts, inward, auto_orient=True)
+    ent = ctx.strip_entries(0)
+    _check_strips(ent, s.verts, s.tris)
+
+
+def test_argument_errors(zef):
+    ctx = _host_ctx(zef)
+    s = zs.config0().surfaces[0]
+    for cid in (0, -3):
+        with pytest.raises(zef.ZefError) as e:
+            ctx.add_compartment(cid, s.verts, s.tris)
+        assert e.value.status == zef.ZEF_ERR_INVALID_ARG
+    bad = s.tris.copy()
+    bad[0, 0] = 10 ** 6
+    with pytest.raises(zef.ZefError):
+        ctx.add_compartment(1, s.verts, bad)
+    nanv = s.verts.copy()
+    nanv[3, 1] = np.nan
+    with pytest.raises(zef.ZefError):
+        ctx.add_compartment(1, nanv, s.tris)
+    ctx.add_compartment(1, s.verts, s.tris)
+    with pytest.raises(zef.ZefError):
+        ctx.add_compartment(1, s.verts, s.tris)   # duplicate id
+
+
+def test_priority_must_be_permutation(zef):
+    ctx = _host_ctx(zef)
+    s = zs.config0().surfaces[0]
+    ctx.add_compartment(4, s.verts, s.tris)
+    ctx.add_compartment(7, (s.verts * 2).astype(np.float32), s.tris)
+    ctx.set_priority([7, 4])
+    for bad in ([7], [4, 4], [4, 5], [7, 4, 1]):
+        with pytest.raises(zef.ZefError) as e:
+            ctx.set_priority(bad)
+        assert e.value.status == zef.ZEF_ERR_INVALID_ARG
+
+
+def _check_strips(ent, verts, tris):
+    """The strip stream must reproduce every surface triangle exactly once
+    with its orientation (as a cyclic vertex sequence) and its normal."""
+    v = verts.astype(np.float32)
+    key = {tuple(map(float, p)): i for i, p in enumerate(v)}
+    assert ent.shape[0] % 16 == 0
+    want = {}
+    for t in tris:
+        i = int(np.argmin(t))
+        want[tuple(np.roll(t, -i))] = t
+    got = set()
+    idx = [key[tuple(map(float, e[:3]))] for e in ent]
+    for k in range(2, len(ent)):
+        if ent[k, 3] == 0.0:
+            assert ent[k, 7] == -np.inf and np.all(ent[k, 4:7] == 0)
+            continue
+        assert ent[k, 3] == 1.0
+        a, b, c = idx[k - 2], idx[k - 1], idx[k]
+        cand = [(a, b, c), (a, c, b)]
+        hit = None
+        for tri in cand:
+            i = int(np.argmin(tri))
+            r = tuple(np.roll(tri, -i))
+            if r in want:
+                hit = r
+        assert hit is not None, (a, b, c)
+        assert hit not in got
+        got.add(hit)
+        t = want[hit]
+        p = v[t].astype(np.float64)
+        n = np.cross(p[1] - p[0], p[2] - p[0])
+        np.testing.assert_allclose(ent[k, 4:7], n, rtol=1e-6, atol=1e-12 * np.abs(n).max())
+        assert ent[k, 7] == pytest.approx(np.linalg.norm(n) / 8192.0, rel=1e-6)
+    assert len(got) == len(tris)
+    assert ent[0, 3] == 0.0 and ent[1, 3] == 0.0
+
+
+@pytest.mark.parametrize("which", ["sphere", "torus", "ellipsoid"])
+def test_strip_stream_reproduces_triangles(zef, which):
+    if which == "sphere":
+        s = zs.config0().surfaces[0]
+        v, t = s.verts, s.tris
+    elif which == "torus":
+        v, t = zs.torus(10.0, 3.0, 40, 18, seed=1, amp=0.5)
+    else:
+        v, t = zs.perturbed_ellipsoid(12, (9.0, 7.0, 5.0), amp=1.0, seed=3)
+    ctx = _host_ctx(zef)
+    ctx.add_compartment(1, v, t)
+    ent = ctx.strip_entries(0)
+    _check_strips(ent, v, t)
+    n_ent, n_strips = ctx.strip_stats(0)
+    assert n_ent == ent.shape[0]
+    # strips must pay off: far fewer than one restart per triangle
+    assert n_strips < len(t) / 4
+
+
+def test_strip_efficiency_head_surfaces(zef):
+    w = zs.config1(npts_limit=0)
+    ctx = _host_ctx(zef)
+    for s in w.surfaces:
+        ctx.add_compartment(s.id, s.verts, s.tris)
+    for i, s in enumerate(w.surfaces):
+        n_ent, n_strips = ctx.strip_stats(i)
+        # entries = T + 2 strips + padding; overhead under 10 %
+        assert n_ent < 1.10 * s.ntris, (s.name, n_ent, s.ntris, n_strips)
