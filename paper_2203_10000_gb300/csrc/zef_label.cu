@@ -479,31 +479,43 @@ __global__ void __launch_bounds__(NT) k_label64(LabelArgs a) {
   }
 }
 
-// FP64 re-evaluation: each warp takes groups of 32 sorted points from a
-// device cursor; for every uncertain (point, compartment) pair of the group
-// all 32 lanes sum the FP64 half angles over the compartment's triangles
-// (lane l takes triangles l, l + 32, ...) and a fixed butterfly reduces them.
-__global__ void __launch_bounds__(256) k_rescue64(LabelArgs a) {
+// FP64 re-evaluation.  Blocks take groups of 256 sorted points from a device
+// cursor; the uncertain (point, compartment) pairs of a group are gathered in
+// shared memory and each pair is summed by the whole block (thread k takes
+// triangles k, k + 256, ...; fixed-order reduction, so the result does not
+// depend on scheduling).
+constexpr int kRescueT = 256;
+__global__ void __launch_bounds__(kRescueT) k_rescue64(LabelArgs a) {
   __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
-  for (int c = threadIdx.x; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
+  __shared__ int64_t s_group;
+  __shared__ int s_cnt;
+  __shared__ int s_list[kRescueT];
+  __shared__ unsigned long long s_mask[kRescueT];
+  __shared__ double s_red[kRescueT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
   const int64_t n = a.counters[CNT_N];
-  const int64_t ngroups = (n + 31) / 32;
+  const int64_t ngroups = (n + kRescueT - 1) / kRescueT;
   for (;;) {
-    int64_t g = 0;
-    if (lane == 0) g = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_UNC_WORK), 1ull);
-    g = __shfl_sync(0xffffffffu, g, 0);
+    if (tid == 0) {
+      s_group = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_UNC_WORK), 1ull);
+      s_cnt = 0;
+    }
+    __syncthreads();
+    const int64_t g = s_group;
     if (g >= ngroups) break;
-    const int64_t i0 = g * 32;
-    const int64_t mine = i0 + lane;
-    unsigned long long m = mine < n ? a.unc_mask[mine] : 0ull;
-    unsigned vote = __ballot_sync(0xffffffffu, m != 0ull);
-    while (vote) {
-      const int src = __ffs(vote) - 1;
-      vote &= vote - 1;
-      const int64_t i = i0 + src;
-      unsigned long long mm = __shfl_sync(0xffffffffu, m, src);
+    const int64_t mine = g * kRescueT + tid;
+    const unsigned long long m = mine < n ? a.unc_mask[mine] : 0ull;
+    if (m) {
+      const int k = atomicAdd(&s_cnt, 1);
+      s_list[k] = tid;
+      s_mask[k] = m;
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int e = 0; e < cnt; ++e) {
+      const int64_t i = g * kRescueT + s_list[e];
+      unsigned long long mm = s_mask[e];
       const float4 p = a.spts[i];
       const double px = p.x, py = p.y, pz = p.z;
       unsigned long long set_bits = 0ull;
@@ -513,20 +525,27 @@ __global__ void __launch_bounds__(256) k_rescue64(LabelArgs a) {
         const DevComp c = a.comps[s_rowcomp[row]];
         const float4 *T = a.tris + (int64_t)c.tri_off * 3;
         double acc = 0.0;
-        for (int t = lane; t < c.tri_cnt; t += 32)
+        for (int t = tid; t < c.tri_cnt; t += kRescueT)
           acc += vos64_half(px, py, pz, T[3 * t], T[3 * t + 1], T[3 * t + 2]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        const double om = 2.0 * acc;
+        if (lane == 0) s_red[wid] = acc;
+        __syncthreads();
+        double om = 0.0;
+#pragma unroll
+        for (int w = 0; w < kRescueT / 32; ++w) om += s_red[w];
+        om *= 2.0;
+        __syncthreads();
         if (om > 6.283185307179586476925) set_bits |= 1ull << row;
-        if (lane == 0) {
+        if (tid == 0) {
           if (a.omega) a.omega[(int64_t)row * a.omega_ld + a.perm[i]] = (float)om;
           atomicAdd((unsigned long long *)(a.counters + CNT_UNC), 1ull);
           atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)c.tri_cnt);
         }
       }
-      if (lane == 0 && set_bits) atomicOr(a.in_mask + i, set_bits);
+      if (tid == 0 && set_bits) atomicOr(a.in_mask + i, set_bits);
     }
+    __syncthreads();
   }
 }
 
@@ -722,6 +741,8 @@ __global__ void __launch_bounds__(256) k_resolve(LabelArgs a, const float *pts, 
     if (!finite3(p.x, p.y, p.z)) {
       lab = -1;
       atomicAdd((unsigned long long *)(a.counters + CNT_NONFINITE), 1ull);
+      if (a.omega)
+        for (int r = 0; r < a.ncomp; ++r) a.omega[(int64_t)r * a.omega_ld + a.perm[i]] = __int_as_float(0x7fc00000);
     } else {
       const unsigned long long m = a.in_mask[i];
       lab = m ? row_ids[__ffsll((long long)m) - 1] : 0;
@@ -958,6 +979,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   cudaStream_t s = ctx->stream;
   if (plan.timed) cudaEventRecord(ctx->ev[0], s);
   k_reset<<<1, 32, 0, s>>>(b.counters, tile, C);
+  // Omega of (point, compartment) pairs culled by the bounding boxes is 0
+  if (plan.omega) cudaMemsetAsync(plan.omega, 0, (size_t)C * plan.omega_ld * sizeof(float), s);
   const int64_t ncap = plan.n_cap;
   const int g = grid_for(ctx, ncap, 256);
   k_bbox<<<g, 256, 0, s>>>(plan.pts, b.counters, b.in_mask, b.unc_mask);
@@ -1003,7 +1026,7 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   if (plan.timed) cudaEventRecord(ctx->ev[2], s);
   if (plan.timed) cudaEventRecord(ctx->ev[3], s);
   if (plan.opts.precision == ZEF_FP32_RESCUE) {
-    k_rescue64<<<ctx->num_sms * 4, 256, 0, s>>>(a);
+    k_rescue64<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
   }
   if (plan.timed) cudaEventRecord(ctx->ev[4], s);
   k_resolve<<<g, 256, 0, s>>>(a, plan.pts, plan.labels, ctx->d_row_ids);

@@ -146,11 +146,11 @@ def test_deterministic(zef):
 def test_fp64_plain_kernel(zef, oracle_mod):
     w = zs.config0()
     ctx = make_ctx(zef, w.surfaces, w.priority)
-    pts = w.points[:8000]
+    pts = w.points[zs.sample_rows(w.points, 8000, seed=4)]
     lab, om, st = gpu_label(ctx, pts, opts=zef.make_opts(precision=zef.ZEF_FP64_PLAIN))
     olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
     assert_parity(lab, om, olab, oom, tol=1e-6)
-    assert st["pairs_rescued"] == 0
+    assert st["pairs_rescued"] == 0 and st["pairs_evaluated"] > 0
 
 
 def test_everything_rescued_when_margin_covers_all(zef, oracle_mod):
@@ -158,7 +158,7 @@ def test_everything_rescued_when_margin_covers_all(zef, oracle_mod):
     # re-evaluation alone must then reproduce the oracle
     w = zs.config0()
     ctx = make_ctx(zef, w.surfaces, w.priority)
-    pts = w.points[:4000]
+    pts = w.points[zs.sample_rows(w.points, 4000, seed=5)]
     lab, om, st = gpu_label(ctx, pts, opts=zef.make_opts(margin=7.0))
     olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
     assert_parity(lab, om, olab, oom, tol=1e-6)
