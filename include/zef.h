@@ -189,6 +189,31 @@ zef_status zef_compartment_priority(zef_ctx *ctx, const int32_t *ids, int32_t n)
 zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
                             float *omega, const zef_label_opts *opts, zef_label_stats *stats);
 
+/* Largest point count of one zef_label_points_noalloc call. */
+#define ZEF_NOALLOC_MAX_POINTS 65536
+
+/* zef_label_points that allocates nothing during the call.  The paper has no
+   counterpart; this exists for callers that cannot let a library allocate
+   device memory: cudaMalloc / cudaFree may synchronize the whole device and
+   stall every other stream (fatal to a latency-critical loop), and a
+   framework that owns a fixed device-memory budget through its own allocator
+   cannot have memory taken behind its back.
+     pts, labels, omega, opts, stats: as zef_label_points, but pts, labels and
+             omega must be DEVICE pointers (ZEF_ERR_INVALID_ARG otherwise)
+     n       0 <= n <= ZEF_NOALLOC_MAX_POINTS, else ZEF_ERR_INVALID_ARG
+   All scratch comes from one fixed-size array compiled into the library
+   (about 10.7 MB, held on every GPU that loads the library until the process
+   exits).  The compartments must already be registered (ZEF_ERR_NOT_READY
+   otherwise).  The first call on a device looks up the array's device
+   address (cudaGetSymbolAddress) and caches it: make that first call before
+   any stream capture.  Every call in the process shares the one array of its
+   device, which keeps the last call's contents; each call clears what must
+   start at zero.  Calls that overlap on the GPU (other streams, contexts or
+   host threads) race on the array and corrupt each other's results:
+   serialize them. */
+zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
+                                    float *omega, const zef_label_opts *opts, zef_label_stats *stats);
+
 /* Recursive refinement and re-labeling (Sec. 2.1.2, Sec. 2.1.3 item 2):
    `levels` times, every tet whose four node labels are not all equal is split
    into eight (one new node per edge midpoint, shared between tets), and only

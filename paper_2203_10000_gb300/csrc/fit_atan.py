@@ -35,4 +35,4 @@ if __name__ == "__main__":
     c, e = fit(d)
     print(f"degree {d}: max relative error {e:.3e}")
     for k, v in enumerate(c, 1):
-        print(f"constexpr float kA{k} = {v!r}f;")
+        print(f"constexpr float kA{k} = {float(v)!r}f;")

@@ -1,0 +1,186 @@
+// zef_label_points_noalloc: zef_label_points for callers that must not
+// allocate device memory during the call.
+//
+// Why: cudaMalloc / cudaFree can synchronize the whole device and stall every
+// stream on it, and some callers run under a fixed device-memory budget owned
+// by their own allocator.  A latency-critical loop, or a framework that hands
+// out every byte of device memory itself, cannot let the library allocate
+// behind its back.  zef_label_points grows its work buffers on demand; this
+// entry point instead takes all of its scratch from the file-scope array
+// below, whose size is fixed at compile time.
+//
+// The array is a static __device__ object: every GPU that loads the library
+// holds it (kScratchBytes, about 10.7 MB) until the process exits.  In host
+// code its name is only a host-side stand-in, so its device address is looked
+// up once per device with cudaGetSymbolAddress (device current) and cached.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "zef_internal.h"
+
+namespace {
+
+using namespace zef;
+
+constexpr int64_t kMaxPoints = ZEF_NOALLOC_MAX_POINTS;
+constexpr int64_t kMinTile = 128 * 2;                        // smallest tile of any shape
+constexpr int64_t kMaxTiles = (kMaxPoints + kMinTile - 1) / kMinTile;
+constexpr int64_t kMaxFlags = kMaxTiles * ZEF_MAX_COMPARTMENTS;
+constexpr int64_t kScanBlock = 2048;                         // elements per scan block
+constexpr int64_t kMaxBlockSums = (kBuckets > kMaxFlags ? kBuckets : kMaxFlags) / kScanBlock + 2;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// byte offsets of the pieces inside the scratch array
+constexpr size_t kOffSpts = 0;
+constexpr size_t kOffPerm = align256(kOffSpts + kMaxPoints * sizeof(float4));
+constexpr size_t kOffKeys = align256(kOffPerm + kMaxPoints * sizeof(int32_t));
+constexpr size_t kOffIn = align256(kOffKeys + kMaxPoints * sizeof(uint32_t));
+constexpr size_t kOffUnc = align256(kOffIn + kMaxPoints * sizeof(unsigned long long));
+constexpr size_t kOffBox = align256(kOffUnc + kMaxPoints * sizeof(unsigned long long));
+constexpr size_t kOffHist = align256(kOffBox + kMaxTiles * 6 * sizeof(float));
+constexpr size_t kOffFlags = align256(kOffHist + kBuckets * sizeof(uint32_t));
+constexpr size_t kOffSums = align256(kOffFlags + kMaxFlags * sizeof(uint32_t));
+constexpr size_t kOffItems = align256(kOffSums + kMaxBlockSums * sizeof(uint32_t));
+constexpr size_t kOffCnt = align256(kOffItems + kMaxFlags * sizeof(int2));
+constexpr size_t kScratchBytes = align256(kOffCnt + CNT_COUNT_ * sizeof(int64_t));
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void *g_addr[256] = {};  // device address of g_scratch, per device ordinal
+
+// Device address of g_scratch on `device` (which must be current).
+cudaError_t scratch_address(int device, void **out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+  if (!g_addr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    g_addr[device] = p;
+  }
+  *out = g_addr[device];
+  return cudaSuccess;
+}
+
+bool device_pointer(const void *p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice && a.device == device) || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
+                                               float *omega, const zef_label_opts *opts,
+                                               zef_label_stats *stats) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
+  if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
+  if (ctx->dirty) return fail(ctx, ZEF_ERR_NOT_READY, "compartments are not uploaded");
+  if (n < 0 || n > kMaxPoints)
+    return fail(ctx, ZEF_ERR_INVALID_ARG,
+                "zef_label_points_noalloc takes at most ZEF_NOALLOC_MAX_POINTS (65536) points");
+  if (n > 0 && (!pts || !labels)) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad points/labels arguments");
+  zef_label_opts o;
+  if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
+  fill_default_opts(&o);
+  if (o.precision < 0 || o.precision > 2) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision");
+  if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n == 0) return ZEF_OK;
+
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  struct Restore {
+    int d;
+    ~Restore() {
+      if (d >= 0) cudaSetDevice(d);
+    }
+  } restore{prev != ctx->device ? prev : -1};
+
+  if (!device_pointer(pts, ctx->device) || !device_pointer(labels, ctx->device) ||
+      (omega && !device_pointer(omega, ctx->device)))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "zef_label_points_noalloc needs device pointers");
+  void *base = nullptr;
+  cudaError_t e = scratch_address(ctx->device, &base);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(scratch)");
+  unsigned char *s = static_cast<unsigned char *>(base);
+
+  LabelBuffers view;
+  view.cap_points = kMaxPoints;
+  view.cap_tiles = kMaxTiles;
+  view.cap_items = kMaxFlags;
+  view.spts = reinterpret_cast<float4 *>(s + kOffSpts);
+  view.perm = reinterpret_cast<int32_t *>(s + kOffPerm);
+  view.keys = reinterpret_cast<uint32_t *>(s + kOffKeys);
+  view.in_mask = reinterpret_cast<unsigned long long *>(s + kOffIn);
+  view.unc_mask = reinterpret_cast<unsigned long long *>(s + kOffUnc);
+  view.tile_box = reinterpret_cast<float *>(s + kOffBox);
+  view.hist = reinterpret_cast<uint32_t *>(s + kOffHist);
+  view.flags = reinterpret_cast<uint32_t *>(s + kOffFlags);
+  view.block_sums = reinterpret_cast<uint32_t *>(s + kOffSums);
+  view.items = reinterpret_cast<int2 *>(s + kOffItems);
+  view.counters = reinterpret_cast<int64_t *>(s + kOffCnt);
+
+  LabelPlan plan;
+  plan.pts = pts;
+  plan.labels = labels;
+  plan.omega = omega;
+  plan.omega_ld = n;
+  plan.n_cap = n;
+  plan.d_n = view.counters + CNT_N;
+  plan.d_off = view.counters + CNT_OFF;
+  plan.opts = o;
+  if (o.precision == ZEF_FP64_PLAIN) plan.shape = LaunchShape{128, 2};
+  else if (o.block_threads) plan.shape = LaunchShape{o.block_threads, o.points_per_thread};
+  else plan.shape = LaunchShape{256, 4};
+  plan.timed = stats != nullptr;
+
+  // The pipeline enqueues its kernels with the pointers of ctx->lb; point it
+  // at the static scratch for the duration of the enqueue only.  Every piece
+  // that must start at zero is cleared by the pipeline itself (counters,
+  // histogram, masks, Omega).
+  LabelBuffers saved = ctx->lb;
+  ctx->lb = view;
+  zef_status st = label_set_count(ctx, n, 0);
+  if (st == ZEF_OK) st = label_enqueue(ctx, plan);
+  ctx->lb = saved;
+  if (st) return st;
+  if (stats) {
+    st = zef_synchronize(ctx);
+    if (st) return st;
+    e = cudaMemcpy(ctx->h_counters, view.counters, CNT_COUNT_ * sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "read counters");
+    const int64_t *h = ctx->h_counters;
+    int64_t tt = 0;
+    for (auto &c : ctx->comps) tt += c.nt;
+    stats->points = n;
+    stats->nonfinite_points = h[CNT_NONFINITE];
+    stats->pairs_nominal = n * tt;
+    stats->pairs_rescued = h[CNT_PAIRS_RESCUE];
+    stats->pairs_evaluated = h[CNT_PAIRS_EVAL] + h[CNT_PAIRS_RESCUE];
+    stats->uncertain_pairs = h[CNT_UNC];
+    stats->work_items = h[CNT_ITEMS];
+    stats->tiles = h[CNT_TILES];
+    stats->block_threads = plan.shape.threads;
+    stats->points_per_thread = plan.shape.ppt;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+    stats->ms_total = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    stats->ms_label = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]);
+    stats->ms_rescue = ms;
+  }
+  return ZEF_OK;
+}

@@ -99,6 +99,10 @@ _lib.zef_compartment_priority.restype = ctypes.c_int
 _lib.zef_label_points.argtypes = [_P, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                   ctypes.POINTER(LabelStats)]
 _lib.zef_label_points.restype = ctypes.c_int
+_lib.zef_label_points_noalloc.argtypes = [_P, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
+                                          ctypes.POINTER(LabelStats)]
+_lib.zef_label_points_noalloc.restype = ctypes.c_int
+NOALLOC_MAX_POINTS = 65536
 _lib.zef_refine_and_relabel.argtypes = [_P, ctypes.POINTER(Mesh), _I32, ctypes.POINTER(LabelOpts),
                                         ctypes.POINTER(LevelStats)]
 _lib.zef_refine_and_relabel.restype = ctypes.c_int
