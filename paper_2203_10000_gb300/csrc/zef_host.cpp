@@ -444,6 +444,8 @@ zef_status zef_synchronize(zef_ctx *ctx) {
     CK(cudaMemset(ctx->d_status, 0, 2 * sizeof(uint32_t)), "clear status");
     if (st[0] & ST_TIMEOUT)
       return fail(ctx, ZEF_ERR_TIMEOUT, "a bounded device wait expired (site " + std::to_string(st[1]) + ")");
+    if (st[0] & ST_INVALID)
+      return fail(ctx, ZEF_ERR_INVALID_ARG, "a tet references a node index outside [0, num_nodes)");
     if (st[0] & ST_CAPACITY)
       return fail(ctx, ZEF_ERR_CAPACITY, "refinement exceeded the mesh capacities");
   }

@@ -39,6 +39,7 @@ struct __align__(16) DevComp {
 enum : uint32_t {
   ST_TIMEOUT = 1u,
   ST_CAPACITY = 2u,
+  ST_INVALID = 4u,
 };
 
 constexpr int kGroup = 16;        // Kahan group: entries summed plainly before compensation
@@ -97,6 +98,8 @@ enum Counter {
   CNT_LEVEL_NEW,
   CNT_NODES,
   CNT_TETS,
+  CNT_ABORT,          // refinement stopped (capacity)
+  CNT_OWN_LEN,        // 6 x flagged tets of the level
   CNT_COUNT_ = 24
 };
 
@@ -170,6 +173,9 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap);
 zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan);
 zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off);
 zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns);
+zef_status scan_exclusive(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, int64_t len_mul,
+                          int64_t len_cap, int64_t *total_out, uint32_t *bsums);
+int grid_blocks(zef_ctx *ctx, int64_t work, int threads);
 LaunchShape choose_shape(zef_ctx *ctx, const zef_label_opts &o, int64_t n, bool *need_tune);
 zef_status autotune(zef_ctx *ctx, const LabelPlan &plan, LaunchShape *best);
 void fill_default_opts(zef_label_opts *o);

@@ -589,7 +589,6 @@ __global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
       box[3 + k] = INT32_MIN;
     }
     cnt[CNT_TILES] = (n + tile - 1) / tile;
-    cnt[CNT_TILES + 1] = 0;
     (void)ncomp;
   }
 }
@@ -887,6 +886,23 @@ zef_status scan_inplace(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, in
 }  // namespace
 
 // ------------------------------------------------------------------ host API of this file
+// Exclusive in-place scan of uint32 data (length *len_ptr * len_mul, or
+// len_cap when len_ptr is null) using `bsums` (>= len_cap / 2048 + 1 words)
+// for the block sums; the total goes to *total_out when non-null.
+zef_status scan_exclusive(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, int64_t len_mul,
+                          int64_t len_cap, int64_t *total_out, uint32_t *bsums) {
+  const int64_t nb = std::max<int64_t>(1, (len_cap + kScanB - 1) / kScanB);
+  const int64_t len_c = len_ptr ? 0 : len_cap;
+  k_scan_blocks<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(data, len_ptr, len_c, len_mul, bsums);
+  k_scan_sums<<<1, 1024, 0, ctx->stream>>>(bsums, len_ptr, len_c, len_mul, total_out);
+  k_scan_add<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(data, len_ptr, len_c, len_mul, bsums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scan launch");
+  return ZEF_OK;
+}
+
+int grid_blocks(zef_ctx *ctx, int64_t work, int threads) { return grid_for(ctx, work, threads); }
+
 bool shape_valid(int threads, int ppt) {
   return (threads == 128 || threads == 256) && (ppt == 2 || ppt == 4 || ppt == 8);
 }

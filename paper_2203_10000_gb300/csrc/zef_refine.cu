@@ -1,10 +1,493 @@
-// Refinement kernels (placeholder until the refine path lands).
+// Refinement and recursive re-labeling (Sec. 2.1.2 and Sec. 2.1.3 item 2).
+//
+// One level, entirely on the device with device-resident counts:
+//   k_rf_flag      tets whose four node labels are not all equal (the tissue
+//                  boundary of the labeled mesh) -> flag
+//   scan           rank of every flagged tet, count F
+//   k_rf_check     capacity checks (tets M + 7F, hash table)
+//   k_rf_insert    the six edges of every flagged tet into an open-addressing
+//                  table keyed by the sorted node pair; atomicMin keeps the
+//                  smallest (rank, local edge) code, i.e. the first appearance
+//   k_rf_owner/scan  new node numbers in order of first appearance, count K
+//   k_rf_nodes     the K edge midpoints, rounded once to float32
+//   label pipeline only the K new nodes are labeled (zef_label.cu)
+//   k_rf_children  1 -> 8 split: the slot of the flagged tet receives child 0,
+//                  children 1..7 are appended; the octahedron is cut along its
+//                  shortest diagonal (float32 squared lengths, ties to the
+//                  lower diagonal index)
+//   k_rf_advance   per-level statistics, N += K, M += 7F
+// The `levels` iterations are captured once into a CUDA graph and launched as
+// one unit; no host round trip happens between levels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "zef_internal.h"
 
+#define CK(call, what)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
 namespace zef {
+
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kLevelStats = 8;
+
+// local node numbering of a flagged tet: 0..3 corners, 4 = m01, 5 = m02,
+// 6 = m03, 7 = m12, 8 = m13, 9 = m23
+__constant__ int c_edge[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+__constant__ int c_child[3][8][4] = {
+    // diagonal m01-m23
+    {{0, 4, 5, 6}, {4, 1, 7, 8}, {5, 7, 2, 9}, {6, 8, 9, 3},
+     {4, 9, 5, 6}, {4, 9, 6, 8}, {4, 9, 8, 7}, {4, 9, 7, 5}},
+    // diagonal m02-m13
+    {{0, 4, 5, 6}, {4, 1, 7, 8}, {5, 7, 2, 9}, {6, 8, 9, 3},
+     {5, 8, 6, 4}, {5, 8, 9, 6}, {5, 8, 7, 9}, {5, 8, 4, 7}},
+    // diagonal m03-m12
+    {{0, 4, 5, 6}, {4, 1, 7, 8}, {5, 7, 2, 9}, {6, 8, 9, 3},
+     {6, 7, 4, 5}, {6, 7, 5, 9}, {6, 7, 9, 8}, {6, 7, 8, 4}},
+};
+__constant__ int c_diag[3][2] = {{4, 9}, {5, 8}, {6, 7}};
+
+struct RF {
+  float *nodes;
+  int32_t *tets;
+  int32_t *labels;
+  int64_t *cnt;
+  uint32_t *flags;   // [tet_cap], scanned in place
+  uint32_t *owned;   // [6 fmax], scanned in place
+  unsigned long long *hkeys;
+  uint32_t *hvals;
+  int32_t *hids;
+  unsigned long long hmask;
+  int64_t node_cap, tet_cap, fmax;
+  uint32_t *status;
+  int64_t *lstats;
+};
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long edge_key(int32_t a, int32_t b) {
+  const uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
+  return ((unsigned long long)lo << 32) | hi;
+}
+
+__device__ __forceinline__ bool is_flagged(const RF &r, int64_t t, int64_t M, uint32_t *rank) {
+  const uint32_t s = r.flags[t];
+  const uint32_t nx = (t + 1 < M) ? r.flags[t + 1] : (uint32_t)r.cnt[CNT_LEVEL_FLAGGED];
+  *rank = s;
+  return nx != s;
+}
+
+// slot of a key known to be in the table (bounded probe)
+__device__ __forceinline__ unsigned long long find_slot(const RF &r, unsigned long long key) {
+  unsigned long long h = mix64(key) & r.hmask;
+  for (unsigned long long it = 0; it <= r.hmask; ++it) {
+    if (r.hkeys[h] == key) return h;
+    h = (h + 1) & r.hmask;
+  }
+  return 0;  // unreachable when the key was inserted
+}
+
+__global__ void k_rf_init(int64_t *cnt, int64_t n, int64_t m) {
+  if (threadIdx.x == 0) {
+    cnt[CNT_NODES] = n;
+    cnt[CNT_TETS] = m;
+    cnt[CNT_ABORT] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rf_flag(RF r) {
+  if (r.cnt[CNT_ABORT]) return;
+  const int64_t M = r.cnt[CNT_TETS];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+    const int4 q = reinterpret_cast<const int4 *>(r.tets)[t];
+    const int64_t N = r.cnt[CNT_NODES];
+    if (q.x < 0 || q.y < 0 || q.z < 0 || q.w < 0 || q.x >= N || q.y >= N || q.z >= N || q.w >= N) {
+      // a node index outside [0, num_nodes): stop the refinement, report it
+      r.flags[t] = 0u;
+      atomicOr(r.status, ST_INVALID);
+      atomicExch((unsigned long long *)(r.cnt + CNT_ABORT), 1ull);
+      continue;
+    }
+    const int32_t l0 = r.labels[q.x], l1 = r.labels[q.y], l2 = r.labels[q.z], l3 = r.labels[q.w];
+    r.flags[t] = (l0 != l1 || l0 != l2 || l0 != l3) ? 1u : 0u;
+  }
+}
+
+__global__ void k_rf_check(RF r) {
+  if (threadIdx.x != 0) return;
+  const int64_t F = r.cnt[CNT_LEVEL_FLAGGED], M = r.cnt[CNT_TETS];
+  if (!r.cnt[CNT_ABORT] && (F > r.fmax || M + 7 * F > r.tet_cap)) {
+    r.cnt[CNT_ABORT] = 1;
+    atomicOr(r.status, ST_CAPACITY);
+  }
+  r.cnt[CNT_OWN_LEN] = r.cnt[CNT_ABORT] ? 0 : 6 * F;
+}
+
+__global__ void __launch_bounds__(256) k_rf_insert(RF r) {
+  if (r.cnt[CNT_ABORT]) return;
+  const int64_t M = r.cnt[CNT_TETS];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t rank;
+    if (!is_flagged(r, t, M, &rank)) continue;
+    const int32_t *v = r.tets + 4 * t;
+    for (int e = 0; e < 6; ++e) {
+      const unsigned long long key = edge_key(v[c_edge[e][0]], v[c_edge[e][1]]);
+      const uint32_t code = rank * 6u + (uint32_t)e;
+      unsigned long long h = mix64(key) & r.hmask;
+      for (unsigned long long it = 0; it <= r.hmask; ++it) {
+        const unsigned long long prev = atomicCAS(r.hkeys + h, kEmpty, key);
+        if (prev == kEmpty || prev == key) {
+          atomicMin(r.hvals + h, code);
+          break;
+        }
+        h = (h + 1) & r.hmask;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_rf_owner(RF r) {
+  if (r.cnt[CNT_ABORT]) return;
+  const int64_t M = r.cnt[CNT_TETS];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t rank;
+    if (!is_flagged(r, t, M, &rank)) continue;
+    const int32_t *v = r.tets + 4 * t;
+    for (int e = 0; e < 6; ++e) {
+      const unsigned long long key = edge_key(v[c_edge[e][0]], v[c_edge[e][1]]);
+      const uint32_t code = rank * 6u + (uint32_t)e;
+      r.owned[code] = (r.hvals[find_slot(r, key)] == code) ? 1u : 0u;
+    }
+  }
+}
+
+// after the owner scan: node capacity, and the counts of the label pipeline
+__global__ void k_rf_check2(RF r) {
+  if (threadIdx.x != 0) return;
+  const int64_t K = r.cnt[CNT_LEVEL_NEW], N = r.cnt[CNT_NODES];
+  if (!r.cnt[CNT_ABORT] && N + K > r.node_cap) {
+    r.cnt[CNT_ABORT] = 1;
+    atomicOr(r.status, ST_CAPACITY);
+  }
+  r.cnt[CNT_N] = r.cnt[CNT_ABORT] ? 0 : K;
+  r.cnt[CNT_OFF] = N;
+}
+
+__global__ void __launch_bounds__(256) k_rf_nodes(RF r) {
+  if (r.cnt[CNT_ABORT]) return;
+  const int64_t M = r.cnt[CNT_TETS], N = r.cnt[CNT_NODES];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t rank;
+    if (!is_flagged(r, t, M, &rank)) continue;
+    const int32_t *v = r.tets + 4 * t;
+    for (int e = 0; e < 6; ++e) {
+      const int32_t a = v[c_edge[e][0]], b = v[c_edge[e][1]];
+      const unsigned long long key = edge_key(a, b);
+      const uint32_t code = rank * 6u + (uint32_t)e;
+      const unsigned long long slot = find_slot(r, key);
+      if (r.hvals[slot] != code) continue;
+      const int64_t id = N + r.owned[code];
+      r.hids[slot] = (int32_t)id;
+      const int32_t lo = min(a, b), hi = max(a, b);
+      for (int k = 0; k < 3; ++k)
+        r.nodes[3 * id + k] = __fmul_rn(__fadd_rn(r.nodes[3 * (int64_t)lo + k], r.nodes[3 * (int64_t)hi + k]), 0.5f);
+    }
+  }
+}
+
+__device__ __forceinline__ float len2_rn(const float *p, const float *q) {
+  const float dx = __fsub_rn(p[0], q[0]), dy = __fsub_rn(p[1], q[1]), dz = __fsub_rn(p[2], q[2]);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+__global__ void __launch_bounds__(256) k_rf_children(RF r) {
+  if (r.cnt[CNT_ABORT]) return;
+  const int64_t M = r.cnt[CNT_TETS];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M; t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t rank;
+    if (!is_flagged(r, t, M, &rank)) continue;
+    int32_t loc[10];
+    for (int k = 0; k < 4; ++k) loc[k] = r.tets[4 * t + k];
+    for (int e = 0; e < 6; ++e)
+      loc[4 + e] = r.hids[find_slot(r, edge_key(loc[c_edge[e][0]], loc[c_edge[e][1]]))];
+    float l[3];
+    for (int d = 0; d < 3; ++d)
+      l[d] = len2_rn(r.nodes + 3 * (int64_t)loc[c_diag[d][0]], r.nodes + 3 * (int64_t)loc[c_diag[d][1]]);
+    int diag = 0;
+    if (l[1] < l[diag]) diag = 1;
+    if (l[2] < l[diag]) diag = 2;
+    for (int c = 0; c < 8; ++c) {
+      const int64_t dst = c == 0 ? t : M + 7 * (int64_t)rank + (c - 1);
+      const int4 q = make_int4(loc[c_child[diag][c][0]], loc[c_child[diag][c][1]], loc[c_child[diag][c][2]],
+                               loc[c_child[diag][c][3]]);
+      reinterpret_cast<int4 *>(r.tets)[dst] = q;
+    }
+  }
+}
+
+__global__ void k_rf_advance(RF r, int level) {
+  if (threadIdx.x != 0) return;
+  int64_t *s = r.lstats + (int64_t)level * kLevelStats;
+  if (r.cnt[CNT_ABORT]) {
+    s[0] = s[1] = s[4] = s[5] = 0;
+    s[2] = r.cnt[CNT_NODES];
+    s[3] = r.cnt[CNT_TETS];
+    s[6] = 1;
+    return;
+  }
+  const int64_t F = r.cnt[CNT_LEVEL_FLAGGED], K = r.cnt[CNT_LEVEL_NEW];
+  r.cnt[CNT_NODES] += K;
+  r.cnt[CNT_TETS] += 7 * F;
+  s[0] = F;
+  s[1] = K;
+  s[2] = r.cnt[CNT_NODES];
+  s[3] = r.cnt[CNT_TETS];
+  s[4] = r.cnt[CNT_PAIRS_EVAL] + r.cnt[CNT_PAIRS_RESCUE];
+  s[5] = r.cnt[CNT_UNC];
+  s[6] = 0;
+}
+
+bool device_ptr(const void *p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice && a.device == device) || a.type == cudaMemoryTypeManaged;
+}
+
+zef_status grow(zef_ctx *ctx, int idx, size_t bytes) {
+  if (ctx->rf_buf[idx] && ctx->rf_cap[idx] >= bytes) return ZEF_OK;
+  if (ctx->rf_buf[idx]) cudaFree(ctx->rf_buf[idx]);
+  ctx->rf_buf[idx] = nullptr;
+  ctx->rf_cap[idx] = 0;
+  if (ctx->rf_exec) {
+    cudaGraphExecDestroy(ctx->rf_exec);
+    ctx->rf_exec = nullptr;
+  }
+  CK(cudaMalloc(&ctx->rf_buf[idx], std::max<size_t>(bytes, 256)), "cudaMalloc(refine)");
+  ctx->rf_cap[idx] = bytes;
+  return ZEF_OK;
+}
+
+uint64_t fbits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, sizeof(u));
+  return u;
+}
+
+uint64_t hash_mix(uint64_t h, uint64_t v) {
+  h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+}  // namespace
+
 zef_status refine_run(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_label_opts &opts,
                       zef_level_stats *per_level) {
-  (void)mesh; (void)levels; (void)opts; (void)per_level;
-  return fail(ctx, ZEF_ERR_INVALID_ARG, "refinement not built yet");
+  const int64_t N0 = mesh->num_nodes, M0 = mesh->num_tets;
+  const int64_t ncap = mesh->node_capacity, tcap = mesh->tet_capacity;
+  const bool dn = device_ptr(mesh->nodes, ctx->device), dt = device_ptr(mesh->tets, ctx->device),
+             dl = device_ptr(mesh->node_labels, ctx->device);
+  if (!(dn == dt && dt == dl)) return fail(ctx, ZEF_ERR_INVALID_ARG, "mesh arrays must all be host or all device");
+  const bool host = !dn;
+  if (per_level) std::memset(per_level, 0, sizeof(zef_level_stats) * std::max(levels, 0));
+
+  // buffers
+  float *nodes = mesh->nodes;
+  int32_t *tets = mesh->tets, *labels = mesh->node_labels;
+  zef_status st;
+  if (host) {
+    if ((st = grow(ctx, 5, (size_t)ncap * 3 * sizeof(float)))) return st;
+    if ((st = grow(ctx, 6, (size_t)tcap * 4 * sizeof(int32_t)))) return st;
+    if ((st = grow(ctx, 7, (size_t)ncap * sizeof(int32_t)))) return st;
+    nodes = (float *)ctx->rf_buf[5];
+    tets = (int32_t *)ctx->rf_buf[6];
+    labels = (int32_t *)ctx->rf_buf[7];
+    CK(cudaMemcpyAsync(nodes, mesh->nodes, (size_t)N0 * 3 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream),
+       "copy nodes");
+    CK(cudaMemcpyAsync(tets, mesh->tets, (size_t)M0 * 4 * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream),
+       "copy tets");
+    if (mesh->labels_valid)
+      CK(cudaMemcpyAsync(labels, mesh->node_labels, (size_t)N0 * sizeof(int32_t), cudaMemcpyHostToDevice,
+                         ctx->stream),
+         "copy labels");
+  } else if ((reinterpret_cast<uintptr_t>(tets) & 15) != 0) {
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "device tets must be 16-byte aligned");
+  }
+  const int64_t fmax = std::max<int64_t>(0, (tcap - M0) / 7);
+  int64_t hcap = 1024;
+  while (hcap < 12 * fmax) hcap <<= 1;
+  const int64_t bs_len = std::max<int64_t>(tcap, 6 * fmax) / 2048 + 2;
+  if ((st = grow(ctx, 0, (size_t)std::max<int64_t>(tcap, 1) * sizeof(uint32_t)))) return st;      // flags
+  if ((st = grow(ctx, 1, (size_t)std::max<int64_t>(6 * fmax, 1) * sizeof(uint32_t)))) return st;  // owned
+  if ((st = grow(ctx, 2, (size_t)hcap * (sizeof(unsigned long long) + 2 * sizeof(uint32_t))))) return st;
+  if ((st = grow(ctx, 3, (size_t)bs_len * sizeof(uint32_t)))) return st;
+  if ((st = grow(ctx, 4, (size_t)std::max(levels, 1) * kLevelStats * sizeof(int64_t)))) return st;
+  const int64_t new_cap = std::max<int64_t>(1, std::min<int64_t>(6 * fmax, ncap - N0));
+  if ((st = label_reserve(ctx, std::max<int64_t>(new_cap, mesh->labels_valid ? 1 : N0)))) return st;
+  LabelBuffers &b = ctx->lb;
+
+  LaunchShape shape{256, 4};
+  if (opts.precision == ZEF_FP64_PLAIN) shape = LaunchShape{128, 2};
+  else if (opts.block_threads) shape = LaunchShape{opts.block_threads, opts.points_per_thread};
+
+  // initial labeling of every node (not graph-captured: host-known count)
+  if (!mesh->labels_valid && N0 > 0) {
+    LabelPlan p0;
+    p0.pts = nodes;
+    p0.labels = labels;
+    p0.omega = nullptr;
+    p0.omega_ld = 0;
+    p0.n_cap = N0;
+    p0.d_n = b.counters + CNT_N;
+    p0.d_off = b.counters + CNT_OFF;
+    p0.opts = opts;
+    p0.shape = shape;
+    p0.timed = false;
+    if ((st = label_set_count(ctx, N0, 0))) return st;
+    if ((st = label_enqueue(ctx, p0))) return st;
+  }
+
+  RF r;
+  r.nodes = nodes;
+  r.tets = tets;
+  r.labels = labels;
+  r.cnt = b.counters;
+  r.flags = (uint32_t *)ctx->rf_buf[0];
+  r.owned = (uint32_t *)ctx->rf_buf[1];
+  r.hkeys = (unsigned long long *)ctx->rf_buf[2];
+  r.hvals = (uint32_t *)(r.hkeys + hcap);
+  r.hids = (int32_t *)(r.hvals + hcap);
+  r.hmask = (unsigned long long)(hcap - 1);
+  r.node_cap = ncap;
+  r.tet_cap = tcap;
+  r.fmax = fmax;
+  r.status = ctx->d_status;
+  r.lstats = (int64_t *)ctx->rf_buf[4];
+  uint32_t *bsums = (uint32_t *)ctx->rf_buf[3];
+
+  k_rf_init<<<1, 32, 0, ctx->stream>>>(b.counters, N0, M0);
+  CK(cudaGetLastError(), "k_rf_init");
+
+  if (levels > 0) {
+    uint64_t key = 0x5eed;
+    for (uint64_t v : {(uint64_t)(uintptr_t)nodes, (uint64_t)(uintptr_t)tets, (uint64_t)(uintptr_t)labels,
+                       (uint64_t)ncap, (uint64_t)tcap, (uint64_t)fmax, (uint64_t)levels,
+                       (uint64_t)(uintptr_t)b.spts, (uint64_t)(uintptr_t)b.flags, (uint64_t)(uintptr_t)b.hist,
+                       (uint64_t)(uintptr_t)b.counters, (uint64_t)b.cap_points, (uint64_t)shape.threads,
+                       (uint64_t)shape.ppt, (uint64_t)opts.precision, fbits(opts.margin),
+                       fbits(opts.winding_tol), (uint64_t)(uintptr_t)ctx->d_entries})
+      key = hash_mix(key, v);
+    if (!ctx->rf_exec || ctx->rf_key != key) {
+      if (ctx->rf_exec) {
+        cudaGraphExecDestroy(ctx->rf_exec);
+        ctx->rf_exec = nullptr;
+      }
+      // capture on a private stream (the caller's may be the legacy default
+      // stream, which cannot be captured)
+      cudaStream_t cap;
+      CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreate(capture)");
+      cudaStream_t user = ctx->stream;
+      ctx->stream = cap;
+      cudaGraph_t graph = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      st = ZEF_OK;
+      if (ce == cudaSuccess) {
+        const int g_t = grid_blocks(ctx, tcap, 256);
+        for (int lv = 0; lv < levels && st == ZEF_OK; ++lv) {
+          k_rf_flag<<<g_t, 256, 0, cap>>>(r);
+          st = scan_exclusive(ctx, r.flags, b.counters + CNT_TETS, 1, tcap, b.counters + CNT_LEVEL_FLAGGED, bsums);
+          if (st) break;
+          k_rf_check<<<1, 32, 0, cap>>>(r);
+          cudaMemsetAsync(r.hkeys, 0xff, (size_t)hcap * sizeof(unsigned long long), cap);
+          cudaMemsetAsync(r.hvals, 0xff, (size_t)hcap * sizeof(uint32_t), cap);
+          k_rf_insert<<<g_t, 256, 0, cap>>>(r);
+          k_rf_owner<<<g_t, 256, 0, cap>>>(r);
+          st = scan_exclusive(ctx, r.owned, b.counters + CNT_OWN_LEN, 1, std::max<int64_t>(6 * fmax, 1),
+                              b.counters + CNT_LEVEL_NEW, bsums);
+          if (st) break;
+          k_rf_check2<<<1, 32, 0, cap>>>(r);
+          k_rf_nodes<<<g_t, 256, 0, cap>>>(r);
+          LabelPlan p;
+          p.pts = nodes;
+          p.labels = labels;
+          p.omega = nullptr;
+          p.omega_ld = 0;
+          p.n_cap = new_cap;
+          p.d_n = b.counters + CNT_N;
+          p.d_off = b.counters + CNT_OFF;
+          p.opts = opts;
+          p.shape = shape;
+          p.timed = false;
+          st = label_enqueue(ctx, p);
+          if (st) break;
+          k_rf_children<<<g_t, 256, 0, cap>>>(r);
+          k_rf_advance<<<1, 32, 0, cap>>>(r, lv);
+        }
+        cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+        if (st == ZEF_OK && ee != cudaSuccess) st = cuda_fail(ctx, ee, "cudaStreamEndCapture");
+      } else {
+        st = cuda_fail(ctx, ce, "cudaStreamBeginCapture");
+      }
+      ctx->stream = user;
+      cudaStreamDestroy(cap);
+      if (st == ZEF_OK) {
+        cudaError_t ie = cudaGraphInstantiate(&ctx->rf_exec, graph, 0);
+        if (ie != cudaSuccess) st = cuda_fail(ctx, ie, "cudaGraphInstantiate");
+        else ctx->rf_key = key;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      if (st) return st;
+    }
+    CK(cudaGraphLaunch(ctx->rf_exec, ctx->stream), "cudaGraphLaunch");
+  }
+  // results
+  std::vector<int64_t> ls((size_t)std::max(levels, 1) * kLevelStats, 0);
+  int64_t cnt[CNT_COUNT_];
+  CK(cudaMemcpyAsync(ctx->h_counters, b.counters, CNT_COUNT_ * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream),
+     "read counters");
+  if (levels > 0)
+    CK(cudaMemcpyAsync(ls.data(), r.lstats, ls.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream),
+       "read level stats");
+  st = zef_synchronize(ctx);
+  std::memcpy(cnt, ctx->h_counters, sizeof(cnt));
+  const int64_t N1 = cnt[CNT_NODES], M1 = cnt[CNT_TETS];
+  if (host) {
+    CK(cudaMemcpy(mesh->nodes, nodes, (size_t)N1 * 3 * sizeof(float), cudaMemcpyDeviceToHost), "copy nodes back");
+    CK(cudaMemcpy(mesh->tets, tets, (size_t)M1 * 4 * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy tets back");
+    CK(cudaMemcpy(mesh->node_labels, labels, (size_t)N1 * sizeof(int32_t), cudaMemcpyDeviceToHost),
+       "copy labels back");
+  }
+  mesh->num_nodes = N1;
+  mesh->num_tets = M1;
+  mesh->labels_valid = 1;
+  if (per_level)
+    for (int lv = 0; lv < levels; ++lv) {
+      const int64_t *s = &ls[(size_t)lv * kLevelStats];
+      per_level[lv].flagged_tets = s[0];
+      per_level[lv].new_nodes = s[1];
+      per_level[lv].nodes = s[2];
+      per_level[lv].tets = s[3];
+      per_level[lv].pairs_evaluated = s[4];
+      per_level[lv].uncertain_pairs = s[5];
+    }
+  return st;
 }
+
 }  // namespace zef
