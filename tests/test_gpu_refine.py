@@ -76,10 +76,10 @@ def test_refine_sphere_exact(zef, device):
 
 
 def test_refine_head_coarse_exact(zef):
-    """config-3 surfaces (11 compartments) on an 8 mm lattice, 2 levels."""
+    """config-3 surfaces (11 compartments) on a 10 mm lattice, 2 levels."""
     from oracle import refine
     w = zs.config3()
-    nodes, tets = zs.lattice_5tet(25, 8.0, (-100.0, -100.0, -100.0))
+    nodes, tets = zs.lattice_5tet(20, 10.0, (-100.0, -100.0, -100.0))
     ctx = make_ctx(zef, w.surfaces, w.priority)
     n1, t1, l1, per = gpu_refine(zef, ctx, nodes, tets, 2, 400_000, 2_000_000)
     on, ot, ol, oper = refine.refine_and_relabel(nodes, tets, w.surfaces, w.priority, 2)
