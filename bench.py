@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shape", default="", help="threads,ppt override")
+    ap.add_argument("--kernel", type=int, default=0, help="FP32 kernel form (0 grouped, 1 per triangle)")
     return ap.parse_args()
 
 
@@ -199,10 +200,10 @@ def run_ours(args):
     pts_h = np.ascontiguousarray(w.points)
     pts = torch.from_numpy(pts_h).to(dev)
     labels = torch.empty(N, dtype=torch.int32, device=dev)
-    opts = zef.make_opts()
+    opts = zef.make_opts(kernel=args.kernel)
     if args.shape:
         t, p = (int(x) for x in args.shape.split(","))
-        opts = zef.make_opts(block_threads=t, points_per_thread=p)
+        opts = zef.make_opts(block_threads=t, points_per_thread=p, kernel=args.kernel)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     flush.fill_(0)            # load the fill kernel before the timed region
     stream = torch.cuda.current_stream(dev)
@@ -248,7 +249,13 @@ def run_ours(args):
         ms = float(t.item())
     ms_step = ms / args.steps
     pairs = st["pairs_evaluated"]
-    value = pairs * ws / (ms_step * 1e-3)
+    # headline: every point x triangle pair of the workload is decided each
+    # step (pairs outside a closed surface's bounding box exactly, by
+    # culling), so the rate is N x sum(T) / step time -- the same basis as
+    # nodes x triangles / labeling time and as the oracle, which culls
+    # nothing.  The evaluated-pair rate is reported beside it.
+    nominal = st["pairs_nominal"]
+    value = nominal * ws / (ms_step * 1e-3)
 
     # roofline of the FP32 kernel (events around it on the context stream)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -271,8 +278,9 @@ def run_ours(args):
                        "compartments": len(w.surfaces),
                        "l2": "flushed between steps (256 MB device write inside the timed region)",
                        "shape": [st["block_threads"], st["points_per_thread"]]},
-            "pairs_evaluated_per_step": pairs, "pairs_nominal_per_step": st["pairs_nominal"],
-            "nominal_pairs_per_s": st["pairs_nominal"] * ws / (ms_step * 1e-3),
+            "value_basis": "nominal pairs: points x total triangles per step / step time",
+            "pairs_evaluated_per_step": pairs, "pairs_nominal_per_step": nominal,
+            "evaluated_pairs_per_s": pairs * ws / (ms_step * 1e-3),
             "points_per_s": N * ws / (ms_step * 1e-3),
             "uncertain_pairs_per_step": st["uncertain_pairs"], "rescued_pairs_per_step": st["pairs_rescued"],
             "ms_label_kernel": ms_lab, "ms_rescue": float(np.mean(ms_rescue)),
@@ -311,7 +319,7 @@ def run_ours(args):
             ctx.label_points(pts_h, labels=lab_h, opts=opts, stats=False)
         barrier()
         te = (time.perf_counter() - t0) / ke
-        line["e2e"] = {"value": pairs * ws / te, "unit": "pairs/s", "h2d_bytes_per_step": int(N * 12),
+        line["e2e"] = {"value": nominal * ws / te, "unit": "pairs/s", "h2d_bytes_per_step": int(N * 12),
                        "d2h_bytes_per_step": int(N * 4), "ms_per_step": te * 1e3,
                        "labels_equal_device_run": bool(np.array_equal(lab_h, labels.cpu().numpy()))}
 

@@ -92,7 +92,11 @@ typedef struct zef_label_opts {
        autotuned choice.  Valid: threads 128 or 256, points 2, 4 or 8. */
     int32_t block_threads;
     int32_t points_per_thread;
-    int32_t reserved[3];
+    /* Form of the FP32 kernel: 0 = one atan2 per group of four triangles,
+       taken of the product of their (D + iN) factors with 2 pi wraps counted
+       exactly (default); 1 = one atan2 per triangle. */
+    int32_t kernel;
+    int32_t reserved[2];
 } zef_label_opts;
 
 typedef struct zef_label_stats {

@@ -214,7 +214,7 @@ void zef_destroy(zef_ctx *ctx) {
   LabelBuffers &b = ctx->lb;
   fr(b.spts); fr(b.perm); fr(b.keys); fr(b.in_mask); fr(b.unc_mask); fr(b.tile_box);
   fr(b.hist); fr(b.flags); fr(b.block_sums); fr(b.items); fr(b.unc_list); fr(b.counters);
-  fr(b.labels_tmp); fr(b.pts_tmp); fr(b.omega_tmp);
+  fr(b.labels_tmp); fr(b.pts_tmp); fr(b.omega_tmp); fr(b.tune_pts);
   for (auto &p : ctx->rf_buf) fr(p);
   if (ctx->rf_exec) cudaGraphExecDestroy(ctx->rf_exec);
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -353,8 +353,17 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
   std::vector<Entry> ent;
   ent.reserve(nt + nt / 4 + 32);
   int64_t nstrips = 0;
-  const float ninf = -std::numeric_limits<float>::infinity();
   auto vtx = [&](int32_t v) { return &V[3 * (int64_t)v]; };
+  // A non-triangle entry (weight 0) has n = 0, hence N = 0 exactly, and its
+  // window always repeats a vertex, so D = 2 r_u (r_u r_w + R_u . R_w) >= 0:
+  // the factor (D, N) is a positive real and adds no angle.  kappa = 0 makes
+  // the conditioning test catch an FP32 D <= 0 there.
+  auto push_prime = [&](const float *p) {
+    Entry e;
+    e.v = make_float4(p[0], p[1], p[2], 0.f);
+    e.n = make_float4(0.f, 0.f, 0.f, 0.f);
+    ent.push_back(e);
+  };
   for (int64_t t = 0; t < nt; ++t) {
     if (used[t]) continue;
     int best_r = 0;
@@ -367,12 +376,22 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
     std::vector<int64_t> tseq;
     sp.walk<true>(t, best_r, used, &seq, &tseq);
     ++nstrips;
-    for (size_t k = 0; k < seq.size(); ++k) {
+    // priming: the first strip starts from the window (s0, s0); a later strip
+    // follows the window (y, z) of the previous one with z, x0, x0, x1, so
+    // the windows are (y,z,z), (z,z,x0), (z,x0,x0), (x0,x0,x1)
+    if (!ent.empty()) {
+      const float4 z = ent.back().v;
+      const float zp[3] = {z.x, z.y, z.z};
+      push_prime(zp);
+      push_prime(vtx(seq[0]));
+    }
+    push_prime(vtx(seq[0]));
+    push_prime(vtx(seq[1]));
+    for (size_t k = 2; k < seq.size(); ++k) {
       Entry e;
       const float *p = vtx(seq[k]);
       e.v = make_float4(p[0], p[1], p[2], 0.f);
-      e.n = make_float4(0.f, 0.f, 0.f, ninf);
-      if (k >= 2) {
+      {
         const int32_t *f = &T[3 * tseq[k - 2]];
         const float *a = vtx(f[0]), *b = vtx(f[1]), *c = vtx(f[2]);
         double e1[3], e2[3];
@@ -391,10 +410,9 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
     }
   }
   while (ent.size() % kGroup) {
-    Entry e = ent.back();
-    e.v.w = 0.f;
-    e.n = make_float4(0.f, 0.f, 0.f, ninf);
-    ent.push_back(e);
+    const float4 z = ent.back().v;
+    const float zp[3] = {z.x, z.y, z.z};
+    push_prime(zp);
   }
   ch.nstrips = nstrips;
   ch.entry_off = (int64_t)ctx->h_entries.size();
@@ -464,7 +482,8 @@ zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *
   zef_label_opts o;
   if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
   fill_default_opts(&o);
-  if (o.precision < 0 || o.precision > 2) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision");
+  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -568,7 +587,8 @@ zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, 
   zef_label_opts o;
   if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
   fill_default_opts(&o);
-  if (o.precision < 0 || o.precision > 2) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision");
+  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
   DeviceGuard g(ctx->device);
@@ -620,14 +640,32 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
     CK(cudaMalloc(&ctx->d_row_ids, ZEF_MAX_COMPARTMENTS * sizeof(int32_t)), "cudaMalloc(rows)");
     CK(cudaMalloc(&ctx->d_lpt, ZEF_MAX_COMPARTMENTS * sizeof(int32_t)), "cudaMalloc(lpt)");
   }
+  // power-of-two scale: the largest |coordinate| of the surfaces -> [32, 64)
+  float m = 0.f;
+  for (const CompHost &h : ctx->comps)
+    for (int k = 0; k < 3; ++k) m = std::max(m, std::max(std::fabs(h.lo[k]), std::fabs(h.hi[k])));
+  int ex = 0;
+  std::frexp(m, &ex);  // m = f 2^ex, f in [0.5, 1)
+  const float s = (m > 0.f) ? std::ldexp(1.f, 6 - ex) : 1.f;
+  const float s2 = s * s;
+  ctx->scale = s;
+  std::vector<Entry> es(ctx->h_entries);
+  for (Entry &e : es) {
+    e.v.x *= s; e.v.y *= s; e.v.z *= s;
+    e.n.x *= s2; e.n.y *= s2; e.n.z *= s2; e.n.w *= s2;
+  }
+  std::vector<float4> ts(ctx->h_tris);
+  for (float4 &t : ts) {
+    t.x *= s; t.y *= s; t.z *= s;
+  }
   std::vector<DevComp> dc(C);
   std::vector<int32_t> rows(C), lpt(C);
   for (int i = 0; i < C; ++i) {
     const CompHost &h = ctx->comps[i];
     DevComp &d = dc[i];
     for (int k = 0; k < 3; ++k) {
-      d.lo[k] = h.lo[k];
-      d.hi[k] = h.hi[k];
+      d.lo[k] = h.lo[k] * s;
+      d.hi[k] = h.hi[k] * s;
     }
     d.entry_off = (int32_t)h.entry_off;
     d.entry_cnt = (int32_t)h.entry_cnt;
@@ -642,10 +680,8 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
   std::iota(lpt.begin(), lpt.end(), 0);
   std::stable_sort(lpt.begin(), lpt.end(),
                    [&](int a, int b) { return ctx->comps[a].nt > ctx->comps[b].nt; });
-  CK(cudaMemcpy(ctx->d_entries, ctx->h_entries.data(), ne * sizeof(Entry), cudaMemcpyHostToDevice),
-     "upload entries");
-  CK(cudaMemcpy(ctx->d_tris, ctx->h_tris.data(), ntv * sizeof(float4), cudaMemcpyHostToDevice),
-     "upload tris");
+  CK(cudaMemcpy(ctx->d_entries, es.data(), ne * sizeof(Entry), cudaMemcpyHostToDevice), "upload entries");
+  CK(cudaMemcpy(ctx->d_tris, ts.data(), ntv * sizeof(float4), cudaMemcpyHostToDevice), "upload tris");
   CK(cudaMemcpy(ctx->d_comps, dc.data(), C * sizeof(DevComp), cudaMemcpyHostToDevice), "upload comps");
   CK(cudaMemcpy(ctx->d_row_ids, rows.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice), "upload rows");
   CK(cudaMemcpy(ctx->d_lpt, lpt.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice), "upload lpt");

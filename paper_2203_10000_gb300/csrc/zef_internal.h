@@ -78,6 +78,7 @@ struct LabelBuffers {
   float *pts_tmp = nullptr;     // staging for host inputs
   float *omega_tmp = nullptr;
   int64_t cap_omega = 0;
+  float *tune_pts = nullptr;    // autotuner sample (2^20 points)
 };
 
 enum Counter {
@@ -106,6 +107,7 @@ enum Counter {
 struct LaunchShape {
   int threads;
   int ppt;
+  int variant = 0;  // zef_label_opts.kernel
 };
 
 }  // namespace zef
@@ -123,6 +125,10 @@ struct zef_ctx {
   std::vector<float4> h_tris;         // 3 per triangle (w unused)
 
   bool dirty = true;
+  // power of two applied to every coordinate on the device so that the
+  // registered surfaces fit in [-64, 64]^3 (exact; solid angles are scale
+  // invariant); keeps products of four (D, N) factors far from overflow
+  float scale = 1.f;
   zef::Entry *d_entries = nullptr;
   float4 *d_tris = nullptr;
   zef::DevComp *d_comps = nullptr;

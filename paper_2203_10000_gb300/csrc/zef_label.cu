@@ -59,7 +59,7 @@ constexpr float kPi = 3.14159265358979323846f;
 constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kFourPi = 12.5663706143591729539f;
-constexpr float kInvFourPi = 0.0795774715459476678844f;
+constexpr float kInvTwoPi = 0.159154943091895335769f;
 
 // atan(x) = x (1 + s P(s)), s = x^2, 0 <= x <= 1: minimax fit of the relative
 // error with the constant term held at 1 (max relative error 1.25e-7),
@@ -175,6 +175,7 @@ struct PState {
   float ra, rb, sab;       // |R_a|, |R_b|, r_a r_b + R_a . R_b
   float grp, sum, comp;    // group sum, Kahan sum and compensation (half angles)
   float bad;               // min over triangles of max(|N|, D) - kappa |n| r_c
+  uint32_t kp, kn;         // +2 pi / -2 pi wraps of the grouped complex products
 };
 
 __device__ __forceinline__ void window_init(PState &s, float4 v0) {
@@ -205,6 +206,38 @@ __device__ __forceinline__ void vos_step(PState &s, const float4 V, const float4
   s.rb = rc;
 }
 
+// Geometry of one strip step: (N, D) of the window (a, b, c) and the
+// conditioning minimum; the angle is left to the caller.
+__device__ __forceinline__ void geom_step(PState &s, const float4 V, const float4 Nn, float &N, float &D) {
+  const float cx = V.x - s.px, cy = V.y - s.py, cz = V.z - s.pz;
+  const float qc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  const float rc = qc * rsqrtf(qc);
+  const float dac = fmaf(s.ax, cx, fmaf(s.ay, cy, s.az * cz));
+  const float dbc = fmaf(s.bx, cx, fmaf(s.by, cy, s.bz * cz));
+  N = fmaf(Nn.x, cx, fmaf(Nn.y, cy, Nn.z * cz));
+  D = fmaf(s.sab, rc, fmaf(dac, s.rb, dbc * s.ra));
+  s.bad = fminf(s.bad, fmaf(-Nn.w, rc, fmaxf(fabsf(N), D)));
+  s.sab = fmaf(s.rb, rc, dbc);
+  s.ax = s.bx; s.ay = s.by; s.az = s.bz;
+  s.bx = cx; s.by = cy; s.bz = cz;
+  s.ra = s.rb;
+  s.rb = rc;
+}
+
+// (cr, ci) = (ar + i ai)(br + i bi); the principal argument of the product
+// loses 2 pi when both factors lie in the upper half plane (sign bits of ai
+// and bi clear) and the product falls in the lower one, and gains 2 pi in the
+// mirrored case: kp / kn count those wraps (IEEE signed zeros keep +-0 and
+// +-pi consistent with atan2).
+__device__ __forceinline__ void cmul_wrap(float ar, float ai, float br, float bi, float &cr, float &ci,
+                                          uint32_t &kp, uint32_t &kn) {
+  cr = fmaf(ar, br, -(ai * bi));
+  ci = fmaf(ar, bi, ai * br);
+  const uint32_t x = __float_as_uint(ai), y = __float_as_uint(bi), z = __float_as_uint(ci);
+  kp += (~x & ~y & z) >> 31;
+  kn += (x & y & ~z) >> 31;
+}
+
 __device__ __forceinline__ void kahan_flush(PState &s) {
   const float y = s.grp - s.comp;
   const float t = s.sum + y;
@@ -232,9 +265,11 @@ struct LabelArgs {
   int fp32_only;
 };
 
-// Classification of one (point, compartment) pair after the FP32 sum.
+// Classification of one (point, compartment) pair after the FP32 sum:
+// Omega / 2 = half + 2 pi K (K the net count of 2 pi wraps).
 __device__ __forceinline__ void classify_store(const LabelArgs &a, const DevComp &c, int64_t i, float px,
-                                               float py, float pz, float omega, float bad) {
+                                               float py, float pz, float half, int K, float bad) {
+  float omega = 2.f * fmaf(kTwoPi, (float)K, half);
   const bool fin = finite3(px, py, pz);
   const bool outside_box = px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] ||
                            pz > c.hi[2];
@@ -244,9 +279,10 @@ __device__ __forceinline__ void classify_store(const LabelArgs &a, const DevComp
   } else if (outside_box) {
     omega = 0.f;
   } else {
-    const float k = rintf(omega * kInvFourPi);
-    const float dist = fabsf(fmaf(-kFourPi, k, omega));
-    const bool unc = !(bad >= 0.f) || !(dist <= a.winding_tol) || !(fabsf(omega - kTwoPi) >= a.margin);
+    // distance of Omega to 4 pi Z, from the small half angle (K drops out)
+    const float k = rintf(half * kInvTwoPi);
+    const float dist = 2.f * fabsf(fmaf(-kTwoPi, k, half));
+    const bool unc = !(bad > 0.f) || !(dist <= a.winding_tol) || !(fabsf(omega - kTwoPi) >= a.margin);
     if (unc && !a.fp32_only) {
       atomicOr(a.unc_mask + i, bit);
     } else if (omega > kTwoPi) {
@@ -257,7 +293,10 @@ __device__ __forceinline__ void classify_store(const LabelArgs &a, const DevComp
 }
 
 // ------------------------------------------------------------------ FP32 persistent kernel
-template <int NT, int P>
+// V = 0: one atan2 per group of four strip steps, on the product of their
+//        (D + i N) factors with wrap counting (the default);
+// V = 1: one atan2 per triangle.
+template <int NT, int P, int V>
 __global__ void __launch_bounds__(NT) k_label32(LabelArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Entry *sbuf = reinterpret_cast<Entry *>(smem_raw);
@@ -302,6 +341,7 @@ __global__ void __launch_bounds__(NT) k_label32(LabelArgs a) {
       st[q].pz = p.z;
       st[q].grp = st[q].sum = st[q].comp = 0.f;
       st[q].bad = __int_as_float(0x7f800000);
+      st[q].kp = st[q].kn = 0u;
     }
     bool timed_out = false;
     for (int ch = 0; ch < nchunks; ++ch) {
@@ -320,12 +360,33 @@ __global__ void __launch_bounds__(NT) k_label32(LabelArgs a) {
         for (int q = 0; q < P; ++q) window_init(st[q], v0);
       }
       for (int g = 0; g < cnt; g += kGroup) {
-#pragma unroll 4
-        for (int j = 0; j < kGroup; ++j) {
-          const float4 V = E[g + j].v;
-          const float4 Nn = E[g + j].n;
+        if constexpr (V == 0) {
+#pragma unroll 1
+          for (int j = 0; j < kGroup; j += 4) {
+            const Entry *e = E + g + j;
+            const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
+            const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
 #pragma unroll
-          for (int q = 0; q < P; ++q) vos_step(st[q], V, Nn);
+            for (int q = 0; q < P; ++q) {
+              float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+              geom_step(st[q], v0, n0, N0, D0);
+              geom_step(st[q], v1, n1, N1, D1);
+              cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
+              geom_step(st[q], v2, n2, N0, D0);
+              geom_step(st[q], v3, n3, N1, D1);
+              cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
+              cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
+              st[q].grp += half_angle(I, R);
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int j = 0; j < kGroup; ++j) {
+            const float4 Vv = E[g + j].v;
+            const float4 Nn = E[g + j].n;
+#pragma unroll
+            for (int q = 0; q < P; ++q) vos_step(st[q], Vv, Nn);
+          }
         }
 #pragma unroll
         for (int q = 0; q < P; ++q) kahan_flush(st[q]);
@@ -348,8 +409,8 @@ __global__ void __launch_bounds__(NT) k_label32(LabelArgs a) {
     for (int q = 0; q < P; ++q) {
       const int64_t i = base + q * NT + tid;
       if (i < n) {
-        const float om = 2.f * (st[q].sum - st[q].comp);
-        classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, om, st[q].bad);
+        classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, st[q].sum - st[q].comp,
+                       (int)st[q].kp - (int)st[q].kn, st[q].bad);
       }
     }
     if (tid == 0) {
@@ -653,13 +714,29 @@ __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, ui
   }
 }
 
+// Points in bucket order, multiplied by the context's power-of-two scale
+// (exact).  A non-finite input point becomes NaN; a finite one that the scale
+// would push past the float range is clamped (it is far outside every
+// surface either way).
+__device__ __forceinline__ float scaled_coord(float x, float s) {
+  return fminf(fmaxf(x * s, -3.0e38f), 3.0e38f);
+}
+
 __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt, const uint32_t *keys,
-                                                uint32_t *cursor, float4 *spts, int32_t *perm) {
+                                                uint32_t *cursor, float4 *spts, int32_t *perm, float scale) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float *p = pts + 3 * (off + i);
     const uint32_t pos = atomicAdd(cursor + keys[i], 1u);
-    spts[pos] = make_float4(p[0], p[1], p[2], 0.f);
+    const float x = p[0], y = p[1], z = p[2];
+    float4 q;
+    if (finite3(x, y, z)) {
+      q = make_float4(scaled_coord(x, scale), scaled_coord(y, scale), scaled_coord(z, scale), 0.f);
+    } else {
+      const float nan = __int_as_float(0x7fc00000);
+      q = make_float4(nan, nan, nan, 0.f);
+    }
+    spts[pos] = q;
     perm[pos] = (int32_t)i;
   }
 }
@@ -826,10 +903,10 @@ __global__ void __launch_bounds__(kScanT) k_scan_add(uint32_t *data, const int64
 }
 
 // ------------------------------------------------------------------ launch helpers
-template <int NT, int P>
+template <int NT, int P, int V>
 zef_status launch_label32(zef_ctx *ctx, const LabelArgs &a) {
   const size_t smem = 2 * kChunk * sizeof(Entry);
-  auto kern = k_label32<NT, P>;
+  auto kern = k_label32<NT, P, V>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem);
@@ -854,15 +931,20 @@ zef_status launch_label64(zef_ctx *ctx, const LabelArgs &a) {
   return ZEF_OK;
 }
 
-zef_status dispatch_label32(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
+template <int V>
+zef_status dispatch_variant(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
   if (s.threads == 256) {
-    if (s.ppt == 2) return launch_label32<256, 2>(ctx, a);
-    if (s.ppt == 4) return launch_label32<256, 4>(ctx, a);
-    return launch_label32<256, 8>(ctx, a);
+    if (s.ppt == 2) return launch_label32<256, 2, V>(ctx, a);
+    if (s.ppt == 4) return launch_label32<256, 4, V>(ctx, a);
+    return launch_label32<256, 8, V>(ctx, a);
   }
-  if (s.ppt == 2) return launch_label32<128, 2>(ctx, a);
-  if (s.ppt == 4) return launch_label32<128, 4>(ctx, a);
-  return launch_label32<128, 8>(ctx, a);
+  if (s.ppt == 2) return launch_label32<128, 2, V>(ctx, a);
+  if (s.ppt == 4) return launch_label32<128, 4, V>(ctx, a);
+  return launch_label32<128, 8, V>(ctx, a);
+}
+
+zef_status dispatch_label32(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
+  return s.variant == 1 ? dispatch_variant<1>(ctx, a, s) : dispatch_variant<0>(ctx, a, s);
 }
 
 int grid_for(zef_ctx *ctx, int64_t work, int threads) {
@@ -912,19 +994,102 @@ void fill_default_opts(zef_label_opts *o) {
   if (!(o->winding_tol > 0.f)) o->winding_tol = 4e-6f;
 }
 
+// ------------------------------------------------------------------ autotuner
+// The launch shape trades per-pair efficiency (points per thread, warps per
+// SM) against culling (smaller tiles of Morton-ordered points overlap fewer
+// compartment boxes), so the best shape depends on the geometry.  The tuner
+// times every candidate on a strided sample of the call's own points (at most
+// 2^20, so the one-time cost stays a fraction of a full call) and caches the
+// winner under a key of (point-count octave, compartments, total triangles,
+// precision, kernel form).
+namespace {
+
+constexpr LaunchShape kCandidates[] = {{256, 4}, {256, 2}, {128, 4}, {128, 2}};
+constexpr int64_t kTunePoints = 1 << 20;
+
+uint64_t tune_key(zef_ctx *ctx, const zef_label_opts &o, int64_t n) {
+  int oct = 0;
+  while ((int64_t(1) << (oct + 1)) <= n) ++oct;
+  int64_t tt = 0;
+  for (const CompHost &c : ctx->comps) tt += c.nt;
+  uint64_t k = (uint64_t)oct;
+  k = k * 131 + ctx->comps.size();
+  k = k * 1000003 + (uint64_t)tt;
+  k = k * 7 + (uint64_t)o.precision;
+  k = k * 3 + (uint64_t)o.kernel;
+  return k;
+}
+
+__global__ void __launch_bounds__(256) k_gather_stride(const float *pts, int64_t stride, int64_t m, float *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const float *p = pts + 3 * i * stride;
+    out[3 * i] = p[0];
+    out[3 * i + 1] = p[1];
+    out[3 * i + 2] = p[2];
+  }
+}
+
+}  // namespace
+
 LaunchShape choose_shape(zef_ctx *ctx, const zef_label_opts &o, int64_t n, bool *need_tune) {
   *need_tune = false;
   if (o.precision == ZEF_FP64_PLAIN) return LaunchShape{128, 2};
-  if (o.block_threads && o.points_per_thread) return LaunchShape{o.block_threads, o.points_per_thread};
-  (void)ctx;
-  (void)n;
-  return LaunchShape{256, 4};
+  if (o.block_threads && o.points_per_thread)
+    return LaunchShape{o.block_threads, o.points_per_thread, o.kernel};
+  const uint64_t key = tune_key(ctx, o, n);
+  for (const auto &kv : ctx->tune_cache)
+    if (kv.first == key) return kv.second;
+  *need_tune = n >= 4096;  // small calls: not worth timing
+  return LaunchShape{256, 4, o.kernel};
 }
 
+// plan.pts must be device memory with plan.n_cap points at offset 0.
 zef_status autotune(zef_ctx *ctx, const LabelPlan &plan, LaunchShape *best) {
-  (void)ctx;
-  (void)plan;
-  *best = LaunchShape{256, 4};
+  LabelBuffers &b = ctx->lb;
+  const int64_t n = plan.n_cap;
+  const int64_t stride = (n + kTunePoints - 1) / kTunePoints;
+  const int64_t m = (n + stride - 1) / stride;
+  if (!b.tune_pts) {
+    cudaError_t ea = cudaMalloc(&b.tune_pts, (size_t)kTunePoints * 3 * sizeof(float));
+    if (ea != cudaSuccess) return cuda_fail(ctx, ea, "cudaMalloc(tune sample)");
+  }
+  k_gather_stride<<<grid_for(ctx, m, 256), 256, 0, ctx->stream>>>(plan.pts, stride, m, b.tune_pts);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_gather_stride launch");
+  float best_ms = 3.0e38f;
+  LaunchShape pick{256, 4, plan.opts.kernel};
+  for (const LaunchShape &c0 : kCandidates) {
+    LaunchShape c = c0;
+    c.variant = plan.opts.kernel;
+    LabelPlan p = plan;
+    p.pts = b.tune_pts;
+    p.labels = b.labels_tmp;
+    p.omega = nullptr;
+    p.omega_ld = 0;
+    p.n_cap = m;
+    p.shape = c;
+    p.timed = false;
+    float ms_min = 3.0e38f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run also loads the kernel
+      zef_status st = label_set_count(ctx, m, 0);
+      if (st) return st;
+      cudaEventRecord(ctx->ev[0], ctx->stream);
+      st = label_enqueue(ctx, p);
+      if (st) return st;
+      cudaEventRecord(ctx->ev[5], ctx->stream);
+      e = cudaEventSynchronize(ctx->ev[5]);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
+      if (rep > 0) ms_min = std::min(ms_min, ms);
+    }
+    if (ms_min < best_ms) {
+      best_ms = ms_min;
+      pick = c;
+    }
+  }
+  ctx->tune_cache.emplace_back(tune_key(ctx, plan.opts, n), pick);
+  *best = pick;
   return ZEF_OK;
 }
 
@@ -1004,7 +1169,7 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   k_keys<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist);
   zef_status st = scan_inplace(ctx, b.hist, nullptr, 1, kBuckets, nullptr);
   if (st) return st;
-  k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm);
+  k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm, ctx->scale);
   const int64_t tiles_cap = (ncap + tile - 1) / tile;
   k_tile_box<<<grid_for(ctx, tiles_cap * 256, 256), 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
   k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,

@@ -48,7 +48,8 @@ EXPORTED = ["zef_create", "zef_destroy", "zef_last_error", "zef_add_compartment"
 class LabelOpts(ctypes.Structure):
     _fields_ = [("margin", ctypes.c_float), ("winding_tol", ctypes.c_float),
                 ("precision", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("points_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("points_per_thread", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class LabelStats(ctypes.Structure):
@@ -152,8 +153,9 @@ def _contig(x, dtype_np, dtype_name):
 
 
 def make_opts(margin=0.0, winding_tol=0.0, precision=ZEF_FP32_RESCUE, block_threads=0,
-              points_per_thread=0) -> LabelOpts:
+              points_per_thread=0, kernel=0) -> LabelOpts:
     o = LabelOpts()
+    o.kernel = kernel
     o.margin = margin
     o.winding_tol = winding_tol
     o.precision = precision

@@ -108,6 +108,41 @@ def test_launch_shapes_ragged_tail(zef, oracle_mod, shape):
     assert np.array_equal(om, om2) and np.array_equal(lab, lab2)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_kernel_forms_match_oracle(zef, oracle_mod, kernel):
+    """Grouped complex products (0) and one atan2 per triangle (1)."""
+    w = zs.config0()
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab, om, st = gpu_label(ctx, w.points, opts=zef.make_opts(kernel=kernel))
+    olab, oom = oracle_mod.label_points(w.points, w.surfaces, w.priority)
+    assert_parity(lab, om, olab, oom)
+    surfs = [_sphere(87.0, 12, 3), _sphere(92.0, 12, 2), _sphere(100.0, 12, 1)]
+    pts = np.random.default_rng(21).uniform(-110, 110, size=(30000, 3)).astype(np.float32)
+    ctx = make_ctx(zef, surfs, [3, 2, 1])
+    lab, om, st = gpu_label(ctx, pts, opts=zef.make_opts(kernel=kernel))
+    olab, oom = oracle_mod.label_points(pts, surfs, [3, 2, 1])
+    assert_parity(lab, om, olab, oom)
+
+
+def test_autotuned_shape_matches_fixed_shape(zef, oracle_mod):
+    """With no shape given the library times its candidate shapes on a
+    sample of the call's points and caches the winner; the per-point
+    arithmetic does not depend on the shape, so Omega is bit-identical."""
+    w = zs.config1(npts_limit=0)
+    g = zs.lattice_centroids(40, 5.0, (-100.0, -100.0, -100.0))   # 320,000 centroids
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab_a, om_a, st_a = gpu_label(ctx, g)
+    lab_b, om_b, st_b = gpu_label(ctx, g)          # second call: cached choice
+    assert (st_a["block_threads"], st_a["points_per_thread"]) in {(256, 4), (256, 2), (128, 4), (128, 2)}
+    assert (st_b["block_threads"], st_b["points_per_thread"]) == (st_a["block_threads"],
+                                                                  st_a["points_per_thread"])
+    lab_f, om_f, _ = gpu_label(ctx, g, opts=zef.make_opts(block_threads=256, points_per_thread=4))
+    assert np.array_equal(lab_a, lab_f) and np.array_equal(om_a, om_f)
+    idx = zs.sample_rows(g, 3000, seed=6)
+    olab, oom = oracle_mod.label_points(g[idx], w.surfaces, w.priority)
+    assert_parity(lab_a[idx], om_a[:, idx], olab, oom)
+
+
 def test_empty_and_tiny_inputs(zef, oracle_mod):
     w = zs.config0()
     ctx = make_ctx(zef, w.surfaces, w.priority)

@@ -128,7 +128,10 @@ def _check_strips(ent, verts, tris):
     idx = [key[tuple(map(float, e[:3]))] for e in ent]
     for k in range(2, len(ent)):
         if ent[k, 3] == 0.0:
-            assert ent[k, 7] == -np.inf and np.all(ent[k, 4:7] == 0)
+            # a non-triangle window repeats a vertex (so D >= 0 and N = 0
+            # exactly: an identity factor), with zero normal and kappa
+            assert ent[k, 7] == 0.0 and np.all(ent[k, 4:7] == 0)
+            assert len({idx[k - 2], idx[k - 1], idx[k]}) < 3, k
             continue
         assert ent[k, 3] == 1.0
         a, b, c = idx[k - 2], idx[k - 1], idx[k]
