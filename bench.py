@@ -243,10 +243,8 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_2203_10000_gb300.shard import max_over_ranks
+        ms = max_over_ranks(ms, device=dev)
     ms_step = ms / args.steps
     pairs = st["pairs_evaluated"]
     # headline: every point x triangle pair of the workload is decided each
@@ -266,8 +264,16 @@ def run_ours(args):
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
+        # DRAM bytes of one launch from an ncu capture; used only while the
+        # kernel source and the launch shape are the ones that were captured
         try:
-            traffic = json.load(open(tpath)).get(f"config{args.config}")
+            import hashlib
+            rec = json.load(open(tpath)).get(f"config{args.config}")
+            src = os.path.join(ROOT, "paper_2203_10000_gb300", "csrc", "zef_label.cu")
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            shape = f"k_label32<{st['block_threads']},{st['points_per_thread']},{args.kernel}>"
+            if rec and rec["source_sha256_prefix"] == sha and rec["kernel"] == shape:
+                traffic = rec["bytes_per_launch"]
         except Exception:
             traffic = None
 

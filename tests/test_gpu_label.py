@@ -80,7 +80,8 @@ def test_config0_parity(zef, oracle_mod):
     off_surface(oom)
     assert_parity(lab, om, olab, oom)
     assert st["pairs_evaluated"] <= st["pairs_nominal"]
-    assert st["work_items"] >= 1 and st["tiles"] == (len(w.points) + 1023) // 1024
+    tile = st["block_threads"] * st["points_per_thread"]
+    assert st["work_items"] >= 1 and st["tiles"] == (len(w.points) + tile - 1) // tile
 
 
 def test_config0_host_pointers_match_device(zef):
