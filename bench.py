@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-refine", action="store_true", help="skip the refine-and-relabel measurement")
     ap.add_argument("--shape", default="", help="threads,ppt override")
     ap.add_argument("--kernel", type=int, default=0, help="FP32 kernel form (0 grouped, 1 per triangle)")
     return ap.parse_args()
@@ -179,6 +180,42 @@ def run_reference(args):
                                        f"{w.total_tris} triangles each (no culling)"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def refine_measure(zef, torch, dev):
+    """Refine-and-relabel workload: the three-layer head plus 8 deep
+    compartments on a 4 mm lattice (51^3 nodes), 3 levels as one CUDA graph.
+    The second call reuses the captured graph; its device time is reported
+    with the per-level counts."""
+    import zef_synth as zs
+    w = zs.config3()
+    ctx = zef.Context(dev.index)
+    for s in w.surfaces:
+        ctx.add_compartment(s.id, s.verts, s.tris)
+    ctx.set_priority(w.priority)
+    ncap, tcap = 6_000_000, 16_000_000
+    nodes = torch.zeros((ncap, 3), dtype=torch.float32, device=dev)
+    tets = torch.zeros((tcap, 4), dtype=torch.int32, device=dev)
+    labels = torch.zeros(ncap, dtype=torch.int32, device=dev)
+    n0, m0 = w.nodes.shape[0], w.tets.shape[0]
+    src_n = torch.from_numpy(w.nodes).to(dev)
+    src_t = torch.from_numpy(w.tets).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = None
+    for rep in range(2):
+        nodes[:n0].copy_(src_n)
+        tets[:m0].copy_(src_t)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n1, m1, per = ctx.refine_and_relabel(nodes, tets, labels, n0, m0, 3)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out = {"workload": w.name, "initial_nodes": n0, "initial_tets": m0, "levels": per,
+               "ms_total_incl_initial_labeling": e0.elapsed_time(e1), "final_nodes": n1, "final_tets": m1}
+    ctx.close()
+    return out
 
 
 def run_ours(args):
@@ -328,6 +365,9 @@ def run_ours(args):
         line["e2e"] = {"value": nominal * ws / te, "unit": "pairs/s", "h2d_bytes_per_step": int(N * 12),
                        "d2h_bytes_per_step": int(N * 4), "ms_per_step": te * 1e3,
                        "labels_equal_device_run": bool(np.array_equal(lab_h, labels.cpu().numpy()))}
+
+    if rank == 0 and not args.no_refine:
+        line["refine"] = refine_measure(zef, torch, dev)
 
     if rank == 0 and not args.no_cpu:
         sample = args.cpu_sample or auto_sample(w, 12.0)

@@ -89,7 +89,7 @@ typedef struct zef_label_opts {
     /* zef_precision */
     int32_t precision;
     /* Threads per block and points per thread of the FP32 kernel; 0 = the
-       autotuned choice.  Valid: threads 128 or 256, points 2, 4 or 8. */
+       autotuned choice.  Valid: threads 128 or 256, points 2 or 4. */
     int32_t block_threads;
     int32_t points_per_thread;
     /* Form of the FP32 kernel: 0 = one atan2 per group of four triangles,

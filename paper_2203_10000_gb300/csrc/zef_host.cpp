@@ -485,7 +485,7 @@ zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
-    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (n == 0) return ZEF_OK;
   DeviceGuard g(ctx->device);
@@ -590,7 +590,7 @@ zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, 
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
-    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   DeviceGuard g(ctx->device);
   zef_status st = ensure_uploaded(ctx);
   if (st) return st;

@@ -58,7 +58,6 @@ namespace {
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr float kTwoPi = 6.28318530717958647692f;
-constexpr float kFourPi = 12.5663706143591729539f;
 constexpr float kInvTwoPi = 0.159154943091895335769f;
 
 // atan(x) = x (1 + s P(s)), s = x^2, 0 <= x <= 1: minimax fit of the relative
@@ -253,6 +252,7 @@ struct LabelArgs {
   const float4 *spts;
   const int32_t *perm;
   const int2 *items;
+  const float *tile_box;
   unsigned long long *in_mask;
   unsigned long long *unc_mask;
   float *omega;
@@ -267,9 +267,17 @@ struct LabelArgs {
 
 // Classification of one (point, compartment) pair after the FP32 sum:
 // Omega / 2 = half + 2 pi K (K the net count of 2 pi wraps).
-__device__ __forceinline__ void classify_store(const LabelArgs &a, const DevComp &c, int64_t i, float px,
+// True when the box b (lo x, y, z, hi x, y, z) misses the compartment's box.
+__device__ __forceinline__ bool box_misses(const float *b, const DevComp *cp) {
+  return b[3] < __ldg(&cp->lo[0]) || b[0] > __ldg(&cp->hi[0]) || b[4] < __ldg(&cp->lo[1]) ||
+         b[1] > __ldg(&cp->hi[1]) || b[5] < __ldg(&cp->lo[2]) || b[2] > __ldg(&cp->hi[2]);
+}
+
+// Returns true when the point is certainly inside the compartment.
+__device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp &c, int64_t i, float px,
                                                float py, float pz, float half, int K, float bad) {
   float omega = 2.f * fmaf(kTwoPi, (float)K, half);
+  bool inside = false;
   const bool fin = finite3(px, py, pz);
   const bool outside_box = px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] ||
                            pz > c.hi[2];
@@ -287,115 +295,201 @@ __device__ __forceinline__ void classify_store(const LabelArgs &a, const DevComp
       atomicOr(a.unc_mask + i, bit);
     } else if (omega > kTwoPi) {
       atomicOr(a.in_mask + i, bit);
+      inside = true;
     }
   }
   if (a.omega) a.omega[(int64_t)c.row * a.omega_ld + a.perm[i]] = omega;
+  return inside;
 }
 
 // ------------------------------------------------------------------ FP32 persistent kernel
+// One work item = one tile of TILE consecutive Morton-ordered points.  The
+// block walks, in priority order, the compartments whose bounding boxes meet
+// the tile's box.  Without Omega output a point that is certainly inside a
+// compartment needs no lower-priority one (Sec. 2.1: the first compartment of
+// the hierarchy wins), so a warp whose points are all decided, or whose
+// points' box misses the compartment's box, skips the arithmetic, and the
+// block leaves the tile once every point is decided.
 // V = 0: one atan2 per group of four strip steps, on the product of their
 //        (D + i N) factors with wrap counting (the default);
 // V = 1: one atan2 per triangle.
+// Register budget: 2 points per thread -> 85 registers (6 blocks of 128 or
+// 3 of 256 per SM), 4 points -> 128 registers.
+template <int NT, int P>
+constexpr int label32_min_blocks() {
+  return (P == 2 ? 6 : 4) * 128 / NT;
+}
+
 template <int NT, int P, int V>
-__global__ void __launch_bounds__(NT) k_label32(LabelArgs a) {
+__global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(LabelArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Entry *sbuf = reinterpret_cast<Entry *>(smem_raw);
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int64_t s_item;
-  const int tid = threadIdx.x;
+  __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
+  __shared__ float s_tbox[6];
+  __shared__ float s_wbox[NT / 32][6];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int TILE = NT * P;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_barrier_init();
   }
+  for (int c = tid; c < a.ncomp; c += NT) s_rowcomp[a.comps[c].row] = c;
   __syncthreads();
   uint32_t ph0 = 0, ph1 = 0;
-  const int64_t n = a.counters[CNT_N];
+  const int n = (int)a.counters[CNT_N];  // < 2^31 (checked on the host)
   const int64_t nitems = a.counters[CNT_ITEMS];
+  const bool early = a.omega == nullptr;
   for (;;) {
     if (tid == 0) s_item = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_WORK), 1ull);
     __syncthreads();
     const int64_t item = s_item;
     if (item >= nitems) break;
-    const int2 w = a.items[item];
-    const DevComp c = a.comps[w.y];
-    const int64_t base = (int64_t)w.x * TILE;
-    const Entry *gsrc = a.entries + c.entry_off;
-    const int nchunks = (c.entry_cnt + kChunk - 1) / kChunk;
-    if (tid == 0) {
-      int cnt0 = min(kChunk, c.entry_cnt);
-      tma_load_1d(sbuf, gsrc, cnt0 * (uint32_t)sizeof(Entry), &bar[0]);
-      if (nchunks > 1) {
-        int cnt1 = min(kChunk, c.entry_cnt - kChunk);
-        tma_load_1d(sbuf + kChunk, gsrc + kChunk, cnt1 * (uint32_t)sizeof(Entry), &bar[1]);
-      }
-    }
+    const int tile = a.items[item].x;
+    const int base = tile * TILE;
     PState st[P];
+    uint32_t done = 0;  // bit q: point q is invalid, non-finite or certainly inside an earlier compartment
+    {
+      float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      int64_t i = base + q * NT + tid;
-      float4 p = a.spts[i < n ? i : base];
-      st[q].px = p.x;
-      st[q].py = p.y;
-      st[q].pz = p.z;
-      st[q].grp = st[q].sum = st[q].comp = 0.f;
-      st[q].bad = __int_as_float(0x7f800000);
-      st[q].kp = st[q].kn = 0u;
+      for (int q = 0; q < P; ++q) {
+        const int i = base + q * NT + tid;
+        const bool valid = i < n;
+        const float4 p = a.spts[valid ? i : base];
+        st[q].px = p.x;
+        st[q].py = p.y;
+        st[q].pz = p.z;
+        const bool fin = finite3(p.x, p.y, p.z);
+        if (!valid || !fin) done |= 1u << q;
+        if (valid && fin) {
+          wlo[0] = fminf(wlo[0], p.x); wlo[1] = fminf(wlo[1], p.y); wlo[2] = fminf(wlo[2], p.z);
+          whi[0] = fmaxf(whi[0], p.x); whi[1] = fmaxf(whi[1], p.y); whi[2] = fmaxf(whi[2], p.z);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
+          wlo[k] = fminf(wlo[k], __shfl_xor_sync(0xffffffffu, wlo[k], o));
+          whi[k] = fmaxf(whi[k], __shfl_xor_sync(0xffffffffu, whi[k], o));
+        }
+      if (lane == 0)
+        for (int k = 0; k < 3; ++k) {
+          s_wbox[wid][k] = wlo[k];
+          s_wbox[wid][3 + k] = whi[k];
+        }
+      if (tid < 6) s_tbox[tid] = a.tile_box[(int64_t)tile * 6 + tid];
+      __syncthreads();
     }
+    const uint32_t all_done = (1u << P) - 1u;
     bool timed_out = false;
-    for (int ch = 0; ch < nchunks; ++ch) {
-      const int b = ch & 1;
-      bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
-      if (__syncthreads_or(!ok)) {
-        timed_out = true;
-        break;
+    for (int r = 0; r < a.ncomp; ++r) {
+      // the compartment record is re-read where needed (read-only, cached)
+      // rather than held in registers across the hot loop
+      const DevComp *cp = a.comps + s_rowcomp[r];
+      if (box_misses(s_tbox, cp)) continue;  // winding number 0 for every point of the tile
+      const bool mine_done = done == all_done;
+      if (early && __syncthreads_and(mine_done)) break;
+      const bool wskip = box_misses(s_wbox[wid], cp) || (early && __all_sync(0xffffffffu, mine_done));
+      if (__syncthreads_and(wskip)) continue;
+      const int entry_cnt = __ldg(&cp->entry_cnt);
+      const Entry *gsrc = a.entries + __ldg(&cp->entry_off);
+      const int nchunks = (entry_cnt + kChunk - 1) / kChunk;
+      if (tid == 0) {
+        const int cnt0 = min(kChunk, entry_cnt);
+        tma_load_1d(sbuf, gsrc, cnt0 * (uint32_t)sizeof(Entry), &bar[0]);
+        if (nchunks > 1) {
+          const int cnt1 = min(kChunk, entry_cnt - kChunk);
+          tma_load_1d(sbuf + kChunk, gsrc + kChunk, cnt1 * (uint32_t)sizeof(Entry), &bar[1]);
+        }
       }
-      if (b) ph1 ^= 1; else ph0 ^= 1;
-      const Entry *E = sbuf + b * kChunk;
-      const int cnt = min(kChunk, c.entry_cnt - ch * kChunk);
-      if (ch == 0) {
-        const float4 v0 = E[0].v;
 #pragma unroll
-        for (int q = 0; q < P; ++q) window_init(st[q], v0);
+      for (int q = 0; q < P; ++q) {
+        st[q].grp = st[q].sum = st[q].comp = 0.f;
+        st[q].bad = __int_as_float(0x7f800000);
+        st[q].kp = st[q].kn = 0u;
       }
-      for (int g = 0; g < cnt; g += kGroup) {
-        if constexpr (V == 0) {
-#pragma unroll 1
-          for (int j = 0; j < kGroup; j += 4) {
-            const Entry *e = E + g + j;
-            const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
-            const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const int b = ch & 1;
+        const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
+        if (__syncthreads_or(!ok)) {
+          timed_out = true;
+          break;
+        }
+        if (b) ph1 ^= 1; else ph0 ^= 1;
+        if (!wskip) {
+          const Entry *E = sbuf + b * kChunk;
+          const int cnt = min(kChunk, entry_cnt - ch * kChunk);
+          if (ch == 0) {
+            const float4 v0 = E[0].v;
 #pragma unroll
-            for (int q = 0; q < P; ++q) {
-              float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
-              geom_step(st[q], v0, n0, N0, D0);
-              geom_step(st[q], v1, n1, N1, D1);
-              cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
-              geom_step(st[q], v2, n2, N0, D0);
-              geom_step(st[q], v3, n3, N1, D1);
-              cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
-              cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
-              st[q].grp += half_angle(I, R);
-            }
+            for (int q = 0; q < P; ++q) window_init(st[q], v0);
           }
-        } else {
-#pragma unroll 4
-          for (int j = 0; j < kGroup; ++j) {
-            const float4 Vv = E[g + j].v;
-            const float4 Nn = E[g + j].n;
+          for (int g = 0; g < cnt; g += kGroup) {
+            if constexpr (V == 0) {
+#pragma unroll 1
+              for (int j = 0; j < kGroup; j += 4) {
+                const Entry *e = E + g + j;
+                const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
+                const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
 #pragma unroll
-            for (int q = 0; q < P; ++q) vos_step(st[q], Vv, Nn);
+                for (int q = 0; q < P; ++q) {
+                  float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+                  geom_step(st[q], v0, n0, N0, D0);
+                  geom_step(st[q], v1, n1, N1, D1);
+                  cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
+                  geom_step(st[q], v2, n2, N0, D0);
+                  geom_step(st[q], v3, n3, N1, D1);
+                  cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
+                  cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
+                  st[q].grp += half_angle(I, R);
+                }
+              }
+            } else {
+#pragma unroll 4
+              for (int j = 0; j < kGroup; ++j) {
+                const float4 Vv = E[g + j].v;
+                const float4 Nn = E[g + j].n;
+#pragma unroll
+                for (int q = 0; q < P; ++q) vos_step(st[q], Vv, Nn);
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) kahan_flush(st[q]);
           }
         }
-#pragma unroll
-        for (int q = 0; q < P; ++q) kahan_flush(st[q]);
+        __syncthreads();
+        if (tid == 0 && ch + 2 < nchunks) {
+          const int cnt2 = min(kChunk, entry_cnt - (ch + 2) * kChunk);
+          tma_load_1d(sbuf + b * kChunk, gsrc + (int64_t)(ch + 2) * kChunk, cnt2 * (uint32_t)sizeof(Entry),
+                      &bar[b]);
+        }
       }
-      __syncthreads();
-      if (tid == 0 && ch + 2 < nchunks) {
-        int cnt2 = min(kChunk, c.entry_cnt - (ch + 2) * kChunk);
-        tma_load_1d(sbuf + b * kChunk, gsrc + (int64_t)(ch + 2) * kChunk, cnt2 * (uint32_t)sizeof(Entry),
-                    &bar[b]);
+      if (timed_out) break;
+      const DevComp c = *cp;
+      if (!wskip) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int i = base + q * NT + tid;
+          if (i < n) {
+            const bool inside = classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, st[q].sum - st[q].comp,
+                                               (int)st[q].kp - (int)st[q].kn, st[q].bad);
+            if (inside) done |= 1u << q;
+          }
+        }
+      }
+      if (!wskip && lane == 0) {
+        // valid points of this warp x triangles
+        int wcount = 0;
+        const int wbase = base + (tid & ~31);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int first = wbase + q * NT;
+          wcount += max(0, min(32, n - first));
+        }
+        atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL),
+                  (unsigned long long)((int64_t)wcount * c.tri_cnt));
       }
     }
     if (timed_out) {
@@ -404,18 +498,6 @@ __global__ void __launch_bounds__(NT) k_label32(LabelArgs a) {
       mbar_wait(&bar[0], ph0);
       mbar_wait(&bar[1], ph1);
       return;
-    }
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int64_t i = base + q * NT + tid;
-      if (i < n) {
-        classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, st[q].sum - st[q].comp,
-                       (int)st[q].kp - (int)st[q].kn, st[q].bad);
-      }
-    }
-    if (tid == 0) {
-      const int64_t valid = min((int64_t)TILE, n - base);
-      atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), (unsigned long long)(valid * c.tri_cnt));
     }
   }
 }
@@ -808,6 +890,45 @@ __global__ void __launch_bounds__(256) k_emit(int64_t *cnt, const uint32_t *scan
   }
 }
 
+// Work list of the FP32 kernel: every tile whose box meets at least one
+// compartment box, largest estimated work (sum of the met compartments'
+// triangle counts) first, bucketed on a log scale (4096 buckets).
+constexpr int kWorkBuckets = 4096;
+constexpr uint32_t kNoWork = 0xffffffffu;
+
+__global__ void __launch_bounds__(256) k_tile_work(int64_t *cnt, const float *tile_box, const DevComp *comps,
+                                                  int ncomp, uint32_t *tile_key, uint32_t *hist) {
+  const int64_t ntiles = cnt[CNT_TILES];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+    const float *b = tile_box + t * 6;
+    float est = 0.f;
+    for (int c = 0; c < ncomp; ++c) {
+      const DevComp &d = comps[c];
+      const bool ov = !(b[3] < d.lo[0] || b[0] > d.hi[0] || b[4] < d.lo[1] || b[1] > d.hi[1] || b[5] < d.lo[2] ||
+                        b[2] > d.hi[2]);
+      if (ov) est += (float)d.tri_cnt;
+    }
+    uint32_t key = kNoWork;
+    if (est > 0.f) {
+      const int lg = (int)(__log2f(est) * 128.f);
+      key = (uint32_t)(kWorkBuckets - 1 - min(kWorkBuckets - 1, max(0, lg)));
+      atomicAdd(hist + key, 1u);
+    }
+    tile_key[t] = key;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tile_scatter(int64_t *cnt, const uint32_t *tile_key, uint32_t *cursor,
+                                                     int2 *items) {
+  const int64_t ntiles = cnt[CNT_TILES];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t key = tile_key[t];
+    if (key == kNoWork) continue;
+    const uint32_t pos = atomicAdd(cursor + key, 1u);
+    items[pos] = make_int2((int)t, (int)key);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_resolve(LabelArgs a, const float *pts, int32_t *labels,
                                                 const int32_t *row_ids) {
   const int64_t n = a.counters[CNT_N], off = a.counters[CNT_OFF];
@@ -933,14 +1054,8 @@ zef_status launch_label64(zef_ctx *ctx, const LabelArgs &a) {
 
 template <int V>
 zef_status dispatch_variant(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
-  if (s.threads == 256) {
-    if (s.ppt == 2) return launch_label32<256, 2, V>(ctx, a);
-    if (s.ppt == 4) return launch_label32<256, 4, V>(ctx, a);
-    return launch_label32<256, 8, V>(ctx, a);
-  }
-  if (s.ppt == 2) return launch_label32<128, 2, V>(ctx, a);
-  if (s.ppt == 4) return launch_label32<128, 4, V>(ctx, a);
-  return launch_label32<128, 8, V>(ctx, a);
+  if (s.threads == 256) return s.ppt == 2 ? launch_label32<256, 2, V>(ctx, a) : launch_label32<256, 4, V>(ctx, a);
+  return s.ppt == 2 ? launch_label32<128, 2, V>(ctx, a) : launch_label32<128, 4, V>(ctx, a);
 }
 
 zef_status dispatch_label32(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
@@ -986,7 +1101,7 @@ zef_status scan_exclusive(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, 
 int grid_blocks(zef_ctx *ctx, int64_t work, int threads) { return grid_for(ctx, work, threads); }
 
 bool shape_valid(int threads, int ppt) {
-  return (threads == 128 || threads == 256) && (ppt == 2 || ppt == 4 || ppt == 8);
+  return (threads == 128 || threads == 256) && (ppt == 2 || ppt == 4);
 }
 
 void fill_default_opts(zef_label_opts *o) {
@@ -1172,11 +1287,22 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm, ctx->scale);
   const int64_t tiles_cap = (ncap + tile - 1) / tile;
   k_tile_box<<<grid_for(ctx, tiles_cap * 256, 256), 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
-  k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,
-                                                             b.flags);
-  st = scan_inplace(ctx, b.flags, b.counters + CNT_TILES, C, tiles_cap * C, b.counters + CNT_ITEMS);
-  if (st) return st;
-  k_emit<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.flags, ctx->d_lpt, C, b.items);
+  if (plan.opts.precision == ZEF_FP64_PLAIN) {
+    // (tile, compartment) items for the plain FP64 kernel
+    k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,
+                                                               b.flags);
+    st = scan_inplace(ctx, b.flags, b.counters + CNT_TILES, C, tiles_cap * C, b.counters + CNT_ITEMS);
+    if (st) return st;
+    k_emit<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.flags, ctx->d_lpt, C, b.items);
+  } else {
+    // tile items, largest estimated work first
+    cudaMemsetAsync(b.hist, 0, (size_t)kWorkBuckets * sizeof(uint32_t), s);
+    k_tile_work<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, C, b.flags,
+                                                              b.hist);
+    st = scan_inplace(ctx, b.hist, nullptr, 1, kWorkBuckets, b.counters + CNT_ITEMS);
+    if (st) return st;
+    k_tile_scatter<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.flags, b.hist, b.items);
+  }
 
   LabelArgs a;
   a.entries = ctx->d_entries;
@@ -1185,6 +1311,7 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.spts = b.spts;
   a.perm = b.perm;
   a.items = b.items;
+  a.tile_box = b.tile_box;
   a.in_mask = b.in_mask;
   a.unc_mask = b.unc_mask;
   a.omega = plan.omega;

@@ -95,7 +95,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
-    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4/8)");
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (n == 0) return ZEF_OK;
 

@@ -94,7 +94,7 @@ def test_config0_host_pointers_match_device(zef):
     assert np.array_equal(om_h, om_d)
 
 
-@pytest.mark.parametrize("shape", [(256, 4), (256, 2), (256, 8), (128, 2), (128, 4), (128, 8)])
+@pytest.mark.parametrize("shape", [(256, 4), (256, 2), (128, 2), (128, 4)])
 def test_launch_shapes_ragged_tail(zef, oracle_mod, shape):
     w = zs.config0()
     pts = w.points[: len(w.points) - 37]            # several tiles plus a ragged tail
