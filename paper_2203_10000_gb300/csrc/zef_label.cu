@@ -303,106 +303,102 @@ __device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp
 }
 
 // ------------------------------------------------------------------ FP32 persistent kernel
-// One work item = one tile of TILE consecutive Morton-ordered points.  The
-// block walks, in priority order, the compartments whose bounding boxes meet
-// the tile's box.  Without Omega output a point that is certainly inside a
-// compartment needs no lower-priority one (Sec. 2.1: the first compartment of
-// the hierarchy wins), so a warp whose points are all decided, or whose
-// points' box misses the compartment's box, skips the arithmetic, and the
-// block leaves the tile once every point is decided.
+// Every warp is an independent persistent worker: it takes a tile of 32 x P
+// consecutive Morton-ordered points from the work list, walks the
+// compartments whose boxes meet the tile's box in priority order, and streams
+// each compartment's strip entries through its own double buffer in shared
+// memory (1-D bulk TMA copies issued by lane 0, one mbarrier per buffer).
+// There is no block-wide barrier on the hot path, so a warp that finishes a
+// tile early moves straight on to the next one.  Without Omega output a point
+// that is certainly inside a compartment needs no lower-priority one (Sec. 2.1:
+// the first compartment of the hierarchy wins), and the warp leaves the tile
+// once all its points are decided.
 // V = 0: one atan2 per group of four strip steps, on the product of their
 //        (D + i N) factors with wrap counting (the default);
 // V = 1: one atan2 per triangle.
-// Register budget: 2 points per thread -> 85 registers (6 blocks of 128 or
-// 3 of 256 per SM), 4 points -> 128 registers.
+constexpr int kWChunk = 128;  // strip entries per warp buffer (4 KB)
+
+// Register budget: 128 registers (16 warps per SM) with two points per
+// thread, which measured fastest; unconstrained with four.
 template <int NT, int P>
 constexpr int label32_min_blocks() {
-  return (P == 2 ? 6 : 4) * 128 / NT;
+  return P == 2 ? 512 / NT : 1;
 }
 
 template <int NT, int P, int V>
 __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(LabelArgs a) {
+  constexpr int NW = NT / 32;
+  constexpr int TILE = 32 * P;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Entry *sbuf = reinterpret_cast<Entry *>(smem_raw);
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int64_t s_item;
+  __shared__ __align__(8) uint64_t bars[NW][2];
   __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
-  __shared__ float s_tbox[6];
-  __shared__ float s_wbox[NT / 32][6];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int TILE = NT * P;
-  if (tid == 0) {
+  __shared__ float s_wbox[NW][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Entry *wbuf = reinterpret_cast<Entry *>(smem_raw) + wid * 2 * kWChunk;
+  uint64_t *bar = bars[wid];
+  if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_barrier_init();
   }
-  for (int c = tid; c < a.ncomp; c += NT) s_rowcomp[a.comps[c].row] = c;
+  for (int c = threadIdx.x; c < a.ncomp; c += NT) s_rowcomp[a.comps[c].row] = c;
   __syncthreads();
   uint32_t ph0 = 0, ph1 = 0;
   const int n = (int)a.counters[CNT_N];  // < 2^31 (checked on the host)
   const int64_t nitems = a.counters[CNT_ITEMS];
   const bool early = a.omega == nullptr;
+  constexpr uint32_t all_done = (1u << P) - 1u;
   for (;;) {
-    if (tid == 0) s_item = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_WORK), 1ull);
-    __syncthreads();
-    const int64_t item = s_item;
+    int64_t item = 0;
+    if (lane == 0) item = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_WORK), 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= nitems) break;
     const int tile = a.items[item].x;
     const int base = tile * TILE;
     PState st[P];
     uint32_t done = 0;  // bit q: point q is invalid, non-finite or certainly inside an earlier compartment
-    {
-      float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float wb[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const int i = base + q * NT + tid;
-        const bool valid = i < n;
-        const float4 p = a.spts[valid ? i : base];
-        st[q].px = p.x;
-        st[q].py = p.y;
-        st[q].pz = p.z;
-        const bool fin = finite3(p.x, p.y, p.z);
-        if (!valid || !fin) done |= 1u << q;
-        if (valid && fin) {
-          wlo[0] = fminf(wlo[0], p.x); wlo[1] = fminf(wlo[1], p.y); wlo[2] = fminf(wlo[2], p.z);
-          whi[0] = fmaxf(whi[0], p.x); whi[1] = fmaxf(whi[1], p.y); whi[2] = fmaxf(whi[2], p.z);
-        }
+    for (int q = 0; q < P; ++q) {
+      const int i = base + q * 32 + lane;
+      const bool valid = i < n;
+      const float4 p = a.spts[valid ? i : base];
+      st[q].px = p.x;
+      st[q].py = p.y;
+      st[q].pz = p.z;
+      const bool fin = finite3(p.x, p.y, p.z);
+      if (!valid || !fin) {
+        done |= 1u << q;
+      } else {
+        wb[0] = fminf(wb[0], p.x); wb[1] = fminf(wb[1], p.y); wb[2] = fminf(wb[2], p.z);
+        wb[3] = fmaxf(wb[3], p.x); wb[4] = fmaxf(wb[4], p.y); wb[5] = fmaxf(wb[5], p.z);
       }
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        for (int o = 16; o > 0; o >>= 1) {
-          wlo[k] = fminf(wlo[k], __shfl_xor_sync(0xffffffffu, wlo[k], o));
-          whi[k] = fmaxf(whi[k], __shfl_xor_sync(0xffffffffu, whi[k], o));
-        }
-      if (lane == 0)
-        for (int k = 0; k < 3; ++k) {
-          s_wbox[wid][k] = wlo[k];
-          s_wbox[wid][3 + k] = whi[k];
-        }
-      if (tid < 6) s_tbox[tid] = a.tile_box[(int64_t)tile * 6 + tid];
-      __syncthreads();
     }
-    const uint32_t all_done = (1u << P) - 1u;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      for (int o = 16; o > 0; o >>= 1) {
+        wb[k] = fminf(wb[k], __shfl_xor_sync(0xffffffffu, wb[k], o));
+        wb[3 + k] = fmaxf(wb[3 + k], __shfl_xor_sync(0xffffffffu, wb[3 + k], o));
+      }
+    // the tile's box lives in shared memory while the compartments are walked
+    if (lane == 0)
+      for (int k = 0; k < 6; ++k) s_wbox[wid][k] = wb[k];
+    __syncwarp();
     bool timed_out = false;
     for (int r = 0; r < a.ncomp; ++r) {
       // the compartment record is re-read where needed (read-only, cached)
       // rather than held in registers across the hot loop
       const DevComp *cp = a.comps + s_rowcomp[r];
-      if (box_misses(s_tbox, cp)) continue;  // winding number 0 for every point of the tile
-      const bool mine_done = done == all_done;
-      if (early && __syncthreads_and(mine_done)) break;
-      const bool wskip = box_misses(s_wbox[wid], cp) || (early && __all_sync(0xffffffffu, mine_done));
-      if (__syncthreads_and(wskip)) continue;
+      if (box_misses(s_wbox[wid], cp)) continue;  // winding number 0 for every point of the tile
+      if (early && __all_sync(0xffffffffu, done == all_done)) break;
       const int entry_cnt = __ldg(&cp->entry_cnt);
       const Entry *gsrc = a.entries + __ldg(&cp->entry_off);
-      const int nchunks = (entry_cnt + kChunk - 1) / kChunk;
-      if (tid == 0) {
-        const int cnt0 = min(kChunk, entry_cnt);
-        tma_load_1d(sbuf, gsrc, cnt0 * (uint32_t)sizeof(Entry), &bar[0]);
-        if (nchunks > 1) {
-          const int cnt1 = min(kChunk, entry_cnt - kChunk);
-          tma_load_1d(sbuf + kChunk, gsrc + kChunk, cnt1 * (uint32_t)sizeof(Entry), &bar[1]);
-        }
+      const int nchunks = (entry_cnt + kWChunk - 1) / kWChunk;
+      if (lane == 0) {
+        tma_load_1d(wbuf, gsrc, min(kWChunk, entry_cnt) * (uint32_t)sizeof(Entry), &bar[0]);
+        if (nchunks > 1)
+          tma_load_1d(wbuf + kWChunk, gsrc + kWChunk, min(kWChunk, entry_cnt - kWChunk) * (uint32_t)sizeof(Entry),
+                      &bar[1]);
       }
 #pragma unroll
       for (int q = 0; q < P; ++q) {
@@ -413,88 +409,73 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       for (int ch = 0; ch < nchunks; ++ch) {
         const int b = ch & 1;
         const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
-        if (__syncthreads_or(!ok)) {
+        if (__any_sync(0xffffffffu, !ok)) {
           timed_out = true;
           break;
         }
         if (b) ph1 ^= 1; else ph0 ^= 1;
-        if (!wskip) {
-          const Entry *E = sbuf + b * kChunk;
-          const int cnt = min(kChunk, entry_cnt - ch * kChunk);
-          if (ch == 0) {
-            const float4 v0 = E[0].v;
+        const Entry *E = wbuf + b * kWChunk;
+        const int cnt = min(kWChunk, entry_cnt - ch * kWChunk);
+        if (ch == 0) {
+          const float4 v0 = E[0].v;
 #pragma unroll
-            for (int q = 0; q < P; ++q) window_init(st[q], v0);
-          }
-          for (int g = 0; g < cnt; g += kGroup) {
-            if constexpr (V == 0) {
+          for (int q = 0; q < P; ++q) window_init(st[q], v0);
+        }
+        for (int g = 0; g < cnt; g += kGroup) {
+          if constexpr (V == 0) {
 #pragma unroll 1
-              for (int j = 0; j < kGroup; j += 4) {
-                const Entry *e = E + g + j;
-                const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
-                const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
+            for (int j = 0; j < kGroup; j += 4) {
+              const Entry *e = E + g + j;
+              const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
+              const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
 #pragma unroll
-                for (int q = 0; q < P; ++q) {
-                  float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
-                  geom_step(st[q], v0, n0, N0, D0);
-                  geom_step(st[q], v1, n1, N1, D1);
-                  cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
-                  geom_step(st[q], v2, n2, N0, D0);
-                  geom_step(st[q], v3, n3, N1, D1);
-                  cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
-                  cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
-                  st[q].grp += half_angle(I, R);
-                }
-              }
-            } else {
-#pragma unroll 4
-              for (int j = 0; j < kGroup; ++j) {
-                const float4 Vv = E[g + j].v;
-                const float4 Nn = E[g + j].n;
-#pragma unroll
-                for (int q = 0; q < P; ++q) vos_step(st[q], Vv, Nn);
+              for (int q = 0; q < P; ++q) {
+                float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+                geom_step(st[q], v0, n0, N0, D0);
+                geom_step(st[q], v1, n1, N1, D1);
+                cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
+                geom_step(st[q], v2, n2, N0, D0);
+                geom_step(st[q], v3, n3, N1, D1);
+                cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
+                cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
+                st[q].grp += half_angle(I, R);
               }
             }
+          } else {
+#pragma unroll 4
+            for (int j = 0; j < kGroup; ++j) {
+              const float4 Vv = E[g + j].v;
+              const float4 Nn = E[g + j].n;
 #pragma unroll
-            for (int q = 0; q < P; ++q) kahan_flush(st[q]);
+              for (int q = 0; q < P; ++q) vos_step(st[q], Vv, Nn);
+            }
           }
+#pragma unroll
+          for (int q = 0; q < P; ++q) kahan_flush(st[q]);
         }
-        __syncthreads();
-        if (tid == 0 && ch + 2 < nchunks) {
-          const int cnt2 = min(kChunk, entry_cnt - (ch + 2) * kChunk);
-          tma_load_1d(sbuf + b * kChunk, gsrc + (int64_t)(ch + 2) * kChunk, cnt2 * (uint32_t)sizeof(Entry),
-                      &bar[b]);
-        }
+        __syncwarp();  // every lane is done with buffer b before it is refilled
+        if (lane == 0 && ch + 2 < nchunks)
+          tma_load_1d(wbuf + b * kWChunk, gsrc + (int64_t)(ch + 2) * kWChunk,
+                      min(kWChunk, entry_cnt - (ch + 2) * kWChunk) * (uint32_t)sizeof(Entry), &bar[b]);
       }
       if (timed_out) break;
       const DevComp c = *cp;
-      if (!wskip) {
 #pragma unroll
-        for (int q = 0; q < P; ++q) {
-          const int i = base + q * NT + tid;
-          if (i < n) {
-            const bool inside = classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, st[q].sum - st[q].comp,
-                                               (int)st[q].kp - (int)st[q].kn, st[q].bad);
-            if (inside) done |= 1u << q;
-          }
+      for (int q = 0; q < P; ++q) {
+        const int i = base + q * 32 + lane;
+        if (i < n) {
+          const bool inside = classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, st[q].sum - st[q].comp,
+                                             (int)st[q].kp - (int)st[q].kn, st[q].bad);
+          if (inside) done |= 1u << q;
         }
       }
-      if (!wskip && lane == 0) {
-        // valid points of this warp x triangles
-        int wcount = 0;
-        const int wbase = base + (tid & ~31);
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-          const int first = wbase + q * NT;
-          wcount += max(0, min(32, n - first));
-        }
+      if (lane == 0)
         atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL),
-                  (unsigned long long)((int64_t)wcount * c.tri_cnt));
-      }
+                  (unsigned long long)((int64_t)max(0, min(TILE, n - base)) * c.tri_cnt));
     }
     if (timed_out) {
-      if (tid == 0) record_timeout(a.status, 1);
-      // let copies still in flight land before the block exits (bounded)
+      if (lane == 0) record_timeout(a.status, 1);
+      // let copies still in flight land before the warp exits (bounded)
       mbar_wait(&bar[0], ph0);
       mbar_wait(&bar[1], ph1);
       return;
@@ -1026,7 +1007,7 @@ __global__ void __launch_bounds__(kScanT) k_scan_add(uint32_t *data, const int64
 // ------------------------------------------------------------------ launch helpers
 template <int NT, int P, int V>
 zef_status launch_label32(zef_ctx *ctx, const LabelArgs &a) {
-  const size_t smem = 2 * kChunk * sizeof(Entry);
+  const size_t smem = (size_t)(NT / 32) * 2 * kWChunk * sizeof(Entry);
   auto kern = k_label32<NT, P, V>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
@@ -1211,7 +1192,7 @@ zef_status autotune(zef_ctx *ctx, const LabelPlan &plan, LaunchShape *best) {
 zef_status label_reserve(zef_ctx *ctx, int64_t n_cap) {
   LabelBuffers &b = ctx->lb;
   const int C = (int)ctx->comps.size();
-  const int64_t min_tile = 128 * 2;
+  const int64_t min_tile = 32 * 2;  // smallest tile of any launch shape
   const int64_t tiles = (n_cap + min_tile - 1) / min_tile;
   zef_status st;
   if (b.cap_points < n_cap) {
@@ -1271,7 +1252,9 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap) {
 zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   LabelBuffers &b = ctx->lb;
   const int C = (int)ctx->comps.size();
-  const int tile = plan.shape.threads * plan.shape.ppt;
+  // FP32: tiles of one warp (32 x P points); plain FP64: tiles of one block
+  const int tile = plan.opts.precision == ZEF_FP64_PLAIN ? plan.shape.threads * plan.shape.ppt
+                                                         : 32 * plan.shape.ppt;
   cudaStream_t s = ctx->stream;
   if (plan.timed) cudaEventRecord(ctx->ev[0], s);
   k_reset<<<1, 32, 0, s>>>(b.counters, tile, C);

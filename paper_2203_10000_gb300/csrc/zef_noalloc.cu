@@ -25,7 +25,7 @@ namespace {
 using namespace zef;
 
 constexpr int64_t kMaxPoints = ZEF_NOALLOC_MAX_POINTS;
-constexpr int64_t kMinTile = 128 * 2;                        // smallest tile of any shape
+constexpr int64_t kMinTile = 32 * 2;                         // smallest tile of any shape
 constexpr int64_t kMaxTiles = (kMaxPoints + kMinTile - 1) / kMinTile;
 constexpr int64_t kMaxFlags = kMaxTiles * ZEF_MAX_COMPARTMENTS;
 constexpr int64_t kScanBlock = 2048;                         // elements per scan block
