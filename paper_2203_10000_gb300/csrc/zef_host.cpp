@@ -24,6 +24,20 @@ zef_status fail(zef_ctx *ctx, zef_status st, const std::string &msg) {
   return st;
 }
 
+// kDop directions of a Fibonacci sphere: z_k = 1 - (2k + 1) / K, azimuth k
+// times the golden angle; rounded to float (the device tests use the same
+// float values).
+void dop_directions(float (*dirs)[3]) {
+  const double golden = 3.14159265358979323846 * (3.0 - std::sqrt(5.0));
+  for (int k = 0; k < kDop; ++k) {
+    const double z = 1.0 - (2.0 * k + 1.0) / kDop;
+    const double r = std::sqrt(std::max(0.0, 1.0 - z * z));
+    dirs[k][0] = (float)(r * std::cos(golden * k));
+    dirs[k][1] = (float)(r * std::sin(golden * k));
+    dirs[k][2] = (float)z;
+  }
+}
+
 zef_status cuda_fail(zef_ctx *ctx, cudaError_t e, const char *what) {
   std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
   zef_status st = (e == cudaErrorMemoryAllocation) ? ZEF_ERR_OOM : ZEF_ERR_CUDA;
@@ -181,6 +195,7 @@ zef_status zef_create(zef_ctx **out, int device, void *cuda_stream) {
     if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaMemset(status)"); break; }
     e = cudaMallocHost(&ctx->h_counters, CNT_COUNT_ * sizeof(int64_t));
     if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaMallocHost"); break; }
+    if ((st = upload_dop_directions(ctx)) != ZEF_OK) break;
     for (auto &ev : ctx->ev) {
       e = cudaEventCreate(&ev);
       if (e != cudaSuccess) { st = cuda_fail(ctx, e, "cudaEventCreate"); break; }
@@ -210,6 +225,7 @@ void zef_destroy(zef_ctx *ctx) {
   fr(ctx->d_comps);
   fr(ctx->d_row_ids);
   fr(ctx->d_lpt);
+  fr(ctx->d_dop);
   fr(ctx->d_status);
   LabelBuffers &b = ctx->lb;
   fr(b.spts); fr(b.perm); fr(b.keys); fr(b.in_mask); fr(b.unc_mask); fr(b.tile_box);
@@ -338,11 +354,21 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
     ch.lo[k] = std::numeric_limits<float>::infinity();
     ch.hi[k] = -std::numeric_limits<float>::infinity();
   }
-  for (int64_t i = 0; i < 3 * nt; ++i) {
-    const float *p = &V[3 * T[i]];
+  std::vector<uint8_t> referenced(nv, 0);
+  for (int64_t i = 0; i < 3 * nt; ++i) referenced[T[i]] = 1;
+  float dirs[kDop][3];
+  dop_directions(dirs);
+  for (int k = 0; k < kDop; ++k) ch.dop[k] = -std::numeric_limits<double>::infinity();
+  for (int64_t v = 0; v < nv; ++v) {
+    if (!referenced[v]) continue;
+    const float *p = &V[3 * v];
     for (int k = 0; k < 3; ++k) {
       ch.lo[k] = std::min(ch.lo[k], p[k]);
       ch.hi[k] = std::max(ch.hi[k], p[k]);
+    }
+    for (int k = 0; k < kDop; ++k) {
+      const double t = (double)dirs[k][0] * p[0] + (double)dirs[k][1] * p[1] + (double)dirs[k][2] * p[2];
+      ch.dop[k] = std::max(ch.dop[k], t);
     }
   }
 
@@ -639,6 +665,7 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
     CK(cudaMalloc(&ctx->d_comps, ZEF_MAX_COMPARTMENTS * sizeof(DevComp)), "cudaMalloc(comps)");
     CK(cudaMalloc(&ctx->d_row_ids, ZEF_MAX_COMPARTMENTS * sizeof(int32_t)), "cudaMalloc(rows)");
     CK(cudaMalloc(&ctx->d_lpt, ZEF_MAX_COMPARTMENTS * sizeof(int32_t)), "cudaMalloc(lpt)");
+    CK(cudaMalloc(&ctx->d_dop, ZEF_MAX_COMPARTMENTS * kDop * sizeof(float)), "cudaMalloc(dop)");
   }
   // power-of-two scale: the largest |coordinate| of the surfaces -> [32, 64)
   float m = 0.f;
@@ -677,9 +704,21 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
       if (ctx->priority[r] == h.id) d.row = r;
     rows[d.row] = h.id;
   }
+  // hull bounds in scaled coordinates: h s (exact power-of-two scaling) plus a
+  // margin that covers the float evaluation of d . p for |p| <= 1000 (scaled
+  // units; every surface lies within 64), rounded up to float
+  std::vector<float> dop((size_t)C * kDop);
+  for (int i = 0; i < C; ++i)
+    for (int k = 0; k < kDop; ++k) {
+      const double thr = ctx->comps[i].dop[k] * s + 6.4e-4;
+      float f = (float)thr;
+      if ((double)f < thr) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+      dop[(size_t)i * kDop + k] = f;
+    }
   std::iota(lpt.begin(), lpt.end(), 0);
   std::stable_sort(lpt.begin(), lpt.end(),
                    [&](int a, int b) { return ctx->comps[a].nt > ctx->comps[b].nt; });
+  CK(cudaMemcpy(ctx->d_dop, dop.data(), dop.size() * sizeof(float), cudaMemcpyHostToDevice), "upload dop");
   CK(cudaMemcpy(ctx->d_entries, es.data(), ne * sizeof(Entry), cudaMemcpyHostToDevice), "upload entries");
   CK(cudaMemcpy(ctx->d_tris, ts.data(), ntv * sizeof(float4), cudaMemcpyHostToDevice), "upload tris");
   CK(cudaMemcpy(ctx->d_comps, dc.data(), C * sizeof(DevComp), cudaMemcpyHostToDevice), "upload comps");

@@ -17,7 +17,8 @@ namespace zef {
 //       triangle of the surface, 0 for the two entries that prime a strip;
 //   n = (nx, ny, nz, kappa): that triangle's doubled-area normal with the
 //       surface's orientation, and kappa = KAPPA * |n| for the conditioning
-//       test; n = 0 and kappa = -inf on priming entries.
+//       test; n = 0 and kappa = 0 on the other entries, whose windows repeat
+//       a vertex (so N = 0, D >= 0: an identity factor).
 struct __align__(16) Entry {
   float4 v;
   float4 n;
@@ -49,11 +50,20 @@ constexpr float kKappa = 1.0f / 8192.0f;  // conditioning threshold of a pair
 constexpr int kMortonBits = 7;    // bits per axis of the binning key
 constexpr int kBuckets = 1 << (3 * kMortonBits);
 
+// Convex-hull bound of a compartment: kDop fixed unit directions d_k (a
+// Fibonacci sphere); h_k >= max over the surface's vertices of d_k . v, with
+// a conservative rounding margin.  A point p with d_k . p > h_k for some k lies
+// outside the convex hull of the closed surface, where its winding number --
+// hence Omega -- is exactly 0.
+constexpr int kDop = 96;
+void dop_directions(float (*dirs)[3]);  // fills kDop unit vectors (host)
+
 struct CompHost {
   int32_t id;
   int64_t nv, nt;
   float lo[3], hi[3];
   int64_t entry_off, entry_cnt, tri_off, nstrips;
+  double dop[kDop];  // max over the vertices of d_k . v (unscaled coordinates)
 };
 
 // Grow-only device buffers of the labeling pipeline.
@@ -134,6 +144,7 @@ struct zef_ctx {
   zef::DevComp *d_comps = nullptr;
   int32_t *d_row_ids = nullptr;       // priority row -> id
   int32_t *d_lpt = nullptr;           // LPT rank -> comp index
+  float *d_dop = nullptr;             // [C][kDop] hull support bounds (scaled coordinates)
   int64_t d_entries_cap = 0, d_tris_cap = 0;
 
   uint32_t *d_status = nullptr;       // [2]
@@ -179,6 +190,7 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap);
 zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan);
 zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off);
 zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns);
+zef_status upload_dop_directions(zef_ctx *ctx);
 zef_status scan_exclusive(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, int64_t len_mul,
                           int64_t len_cap, int64_t *total_out, uint32_t *bsums);
 int grid_blocks(zef_ctx *ctx, int64_t work, int threads);

@@ -71,6 +71,9 @@ constexpr float kA5 = -0.06060978191365727f;
 constexpr float kA6 = 0.025035448658018142f;
 constexpr float kA7 = -0.004909851860197689f;
 
+// directions of the convex-hull bound (uploaded once per device)
+__constant__ float c_dop[kDop][3];
+
 constexpr int kScanT = 256;
 constexpr int kScanV = 8;
 constexpr int kScanB = kScanT * kScanV;
@@ -253,6 +256,7 @@ struct LabelArgs {
   const int32_t *perm;
   const int2 *items;
   const float *tile_box;
+  const float *dop;  // [C][kDop] hull bounds
   unsigned long long *in_mask;
   unsigned long long *unc_mask;
   float *omega;
@@ -273,14 +277,36 @@ __device__ __forceinline__ bool box_misses(const float *b, const DevComp *cp) {
          b[1] > __ldg(&cp->hi[1]) || b[5] < __ldg(&cp->lo[2]) || b[2] > __ldg(&cp->hi[2]);
 }
 
+// Convex-hull bound (kDop half-spaces d_k . x <= thr_k, thr from the host with
+// a conservative margin).  A box lies outside when its smallest d_k . x,
+// taken at the corner (d_k >= 0 ? lo : hi), exceeds one bound; the winding
+// number of every point in it is then 0.
+__device__ __forceinline__ bool dop_box_misses(const float *b, const float *thr) {
+#pragma unroll 4
+  for (int k = 0; k < kDop; ++k) {
+    const float dx = c_dop[k][0], dy = c_dop[k][1], dz = c_dop[k][2];
+    const float t = fmaf(dx, dx >= 0.f ? b[0] : b[3], fmaf(dy, dy >= 0.f ? b[1] : b[4], dz * (dz >= 0.f ? b[2] : b[5])));
+    if (t > __ldg(thr + k)) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool dop_point_outside(float x, float y, float z, const float *thr) {
+#pragma unroll 4
+  for (int k = 0; k < kDop; ++k)
+    if (fmaf(c_dop[k][0], x, fmaf(c_dop[k][1], y, c_dop[k][2] * z)) > __ldg(thr + k)) return true;
+  return false;
+}
+
 // Returns true when the point is certainly inside the compartment.
-__device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp &c, int64_t i, float px,
-                                               float py, float pz, float half, int K, float bad) {
+__device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp &c, const float *thr, int64_t i,
+                                               float px, float py, float pz, float half, int K, float bad) {
   float omega = 2.f * fmaf(kTwoPi, (float)K, half);
   bool inside = false;
   const bool fin = finite3(px, py, pz);
+  // outside the box or the hull bound: winding number 0, Omega exactly 0
   const bool outside_box = px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] ||
-                           pz > c.hi[2];
+                           pz > c.hi[2] || dop_point_outside(px, py, pz, thr);
   const unsigned long long bit = 1ull << c.row;
   if (!fin) {
     omega = __int_as_float(0x7fc00000);
@@ -389,7 +415,9 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       // the compartment record is re-read where needed (read-only, cached)
       // rather than held in registers across the hot loop
       const DevComp *cp = a.comps + s_rowcomp[r];
-      if (box_misses(s_wbox[wid], cp)) continue;  // winding number 0 for every point of the tile
+      const float *thr = a.dop + (int64_t)s_rowcomp[r] * kDop;
+      // winding number 0 for every point of the tile
+      if (box_misses(s_wbox[wid], cp) || dop_box_misses(s_wbox[wid], thr)) continue;
       if (early && __all_sync(0xffffffffu, done == all_done)) break;
       const int entry_cnt = __ldg(&cp->entry_cnt);
       const Entry *gsrc = a.entries + __ldg(&cp->entry_off);
@@ -464,8 +492,9 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       for (int q = 0; q < P; ++q) {
         const int i = base + q * 32 + lane;
         if (i < n) {
-          const bool inside = classify_store(a, c, i, st[q].px, st[q].py, st[q].pz, st[q].sum - st[q].comp,
-                                             (int)st[q].kp - (int)st[q].kn, st[q].bad);
+          const bool inside = classify_store(a, c, a.dop + (int64_t)s_rowcomp[r] * kDop, i, st[q].px, st[q].py,
+                                             st[q].pz, st[q].sum - st[q].comp, (int)st[q].kp - (int)st[q].kn,
+                                             st[q].bad);
           if (inside) done |= 1u << q;
         }
       }
@@ -584,7 +613,8 @@ __global__ void __launch_bounds__(NT) k_label64(LabelArgs a) {
         const float fx = (float)px[q], fy = (float)py[q], fz = (float)pz[q];
         const bool fin = finite3(fx, fy, fz);
         const bool outside_box = fx < c.lo[0] || fx > c.hi[0] || fy < c.lo[1] || fy > c.hi[1] ||
-                                 fz < c.lo[2] || fz > c.hi[2];
+                                 fz < c.lo[2] || fz > c.hi[2] ||
+                                 dop_point_outside(fx, fy, fz, a.dop + (int64_t)w.y * kDop);
         float omf = (float)om;
         if (!fin) {
           omf = __int_as_float(0x7fc00000);
@@ -842,7 +872,7 @@ __global__ void __launch_bounds__(256) k_tile_box(const float4 *spts, int64_t *c
 }
 
 __global__ void __launch_bounds__(256) k_flags(int64_t *cnt, const float *tile_box, const DevComp *comps,
-                                              const int32_t *lpt, int ncomp, uint32_t *flags) {
+                                              const int32_t *lpt, int ncomp, const float *dop, uint32_t *flags) {
   const int64_t ntiles = cnt[CNT_TILES];
   const int64_t len = ntiles * ncomp;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < len; j += (int64_t)gridDim.x * blockDim.x) {
@@ -851,7 +881,8 @@ __global__ void __launch_bounds__(256) k_flags(int64_t *cnt, const float *tile_b
     const DevComp &c = comps[lpt[r]];
     const float *b = tile_box + t * 6;
     const bool ov = !(b[3] < c.lo[0] || b[0] > c.hi[0] || b[4] < c.lo[1] || b[1] > c.hi[1] || b[5] < c.lo[2] ||
-                      b[2] > c.hi[2]);
+                      b[2] > c.hi[2]) &&
+                    !dop_box_misses(b, dop + (int64_t)lpt[r] * kDop);
     flags[j] = ov ? 1u : 0u;
   }
 }
@@ -878,7 +909,7 @@ constexpr int kWorkBuckets = 4096;
 constexpr uint32_t kNoWork = 0xffffffffu;
 
 __global__ void __launch_bounds__(256) k_tile_work(int64_t *cnt, const float *tile_box, const DevComp *comps,
-                                                  int ncomp, uint32_t *tile_key, uint32_t *hist) {
+                                                  int ncomp, const float *dop, uint32_t *tile_key, uint32_t *hist) {
   const int64_t ntiles = cnt[CNT_TILES];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
     const float *b = tile_box + t * 6;
@@ -886,7 +917,8 @@ __global__ void __launch_bounds__(256) k_tile_work(int64_t *cnt, const float *ti
     for (int c = 0; c < ncomp; ++c) {
       const DevComp &d = comps[c];
       const bool ov = !(b[3] < d.lo[0] || b[0] > d.hi[0] || b[4] < d.lo[1] || b[1] > d.hi[1] || b[5] < d.lo[2] ||
-                        b[2] > d.hi[2]);
+                        b[2] > d.hi[2]) &&
+                      !dop_box_misses(b, dop + (int64_t)c * kDop);
       if (ov) est += (float)d.tri_cnt;
     }
     uint32_t key = kNoWork;
@@ -1273,15 +1305,15 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
     // (tile, compartment) items for the plain FP64 kernel
     k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,
-                                                               b.flags);
+                                                               ctx->d_dop, b.flags);
     st = scan_inplace(ctx, b.flags, b.counters + CNT_TILES, C, tiles_cap * C, b.counters + CNT_ITEMS);
     if (st) return st;
     k_emit<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.flags, ctx->d_lpt, C, b.items);
   } else {
     // tile items, largest estimated work first
     cudaMemsetAsync(b.hist, 0, (size_t)kWorkBuckets * sizeof(uint32_t), s);
-    k_tile_work<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, C, b.flags,
-                                                              b.hist);
+    k_tile_work<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, C, ctx->d_dop,
+                                                              b.flags, b.hist);
     st = scan_inplace(ctx, b.hist, nullptr, 1, kWorkBuckets, b.counters + CNT_ITEMS);
     if (st) return st;
     k_tile_scatter<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.flags, b.hist, b.items);
@@ -1295,6 +1327,7 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.perm = b.perm;
   a.items = b.items;
   a.tile_box = b.tile_box;
+  a.dop = ctx->d_dop;
   a.in_mask = b.in_mask;
   a.unc_mask = b.unc_mask;
   a.omega = plan.omega;
@@ -1339,6 +1372,20 @@ zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off) {
   k_prepare<<<1, 32, 0, ctx->stream>>>(ctx->lb.counters, n, off);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_prepare launch");
+  return ZEF_OK;
+}
+
+}  // namespace zef
+
+namespace zef {
+
+// Convex-hull bound directions into this device's constant memory (once per
+// context, at creation; the device is current).
+zef_status upload_dop_directions(zef_ctx *ctx) {
+  float dirs[kDop][3];
+  dop_directions(dirs);
+  cudaError_t e = cudaMemcpyToSymbol(c_dop, dirs, sizeof(dirs));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "upload hull directions");
   return ZEF_OK;
 }
 
