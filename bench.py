@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle timing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-refine", action="store_true", help="skip the refine-and-relabel measurement")
+    ap.add_argument("--no-compare", action="store_true", help="skip the tile-coherence-off comparison step")
     ap.add_argument("--shape", default="", help="threads,ppt override")
     ap.add_argument("--kernel", type=int, default=0, help="FP32 kernel form (0 grouped, 1 per triangle)")
     return ap.parse_args()
@@ -365,6 +366,28 @@ def run_ours(args):
         line["e2e"] = {"value": nominal * ws / te, "unit": "pairs/s", "h2d_bytes_per_step": int(N * 12),
                        "d2h_bytes_per_step": int(N * 4), "ms_per_step": te * 1e3,
                        "labels_equal_device_run": bool(np.array_equal(lab_h, labels.cpu().numpy()))}
+
+    if rank == 0 and not args.no_compare:
+        # the same step with every point evaluated (tile coherence off)
+        opts_nc = zef.make_opts(kernel=args.kernel, coherence=False)
+        if args.shape:
+            t_, p_ = (int(x) for x in args.shape.split(","))
+            opts_nc = zef.make_opts(block_threads=t_, points_per_thread=p_, kernel=args.kernel, coherence=False)
+        ctx.label_points(pts, labels=labels, opts=opts_nc, stats=True)
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        _, _, snc = ctx.label_points(pts, labels=labels, opts=opts_nc, stats=True)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        msnc = c0.elapsed_time(c1)
+        line["no_tile_coherence"] = {"ms_per_step": msnc, "value": nominal / (msnc * 1e-3),
+                                     "pairs_evaluated_per_step": snc["pairs_evaluated"],
+                                     "evaluated_pairs_per_s": snc["pairs_evaluated"] / (msnc * 1e-3),
+                                     "ms_label_kernel": snc["ms_label"]}
+        line["coherent_pairs_per_step"] = st["coherent_pairs"]
 
     if rank == 0 and not args.no_refine:
         line["refine"] = refine_measure(zef, torch, dev)

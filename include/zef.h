@@ -96,8 +96,18 @@ typedef struct zef_label_opts {
        taken of the product of their (D + iN) factors with 2 pi wraps counted
        exactly (default); 1 = one atan2 per triangle. */
     int32_t kernel;
-    int32_t reserved[2];
+    /* ZEF_NO_TILE_COHERENCE or 0 (see below). */
+    uint32_t flags;
+    int32_t reserved;
 } zef_label_opts;
+
+/* zef_label_opts.flags.  By default a tile of points whose bounding box meets
+   no triangle's bounding box of a compartment -- a convex region the surface
+   does not cross, where the winding number is constant -- takes its Omega
+   (exactly 4 pi times that winding number) from one representative point;
+   the representative must be certain, or the tile is evaluated point by
+   point.  This flag evaluates every point instead. */
+#define ZEF_NO_TILE_COHERENCE 1u
 
 typedef struct zef_label_stats {
     int64_t points;            /* N */
@@ -114,6 +124,8 @@ typedef struct zef_label_stats {
     float ms_label;            /* device time of the main labeling kernel */
     float ms_rescue;           /* device time of the FP64 re-evaluation */
     float reserved;
+    int64_t coherent_pairs;    /* (point, compartment) pairs decided by a tile's
+                                  representative point */
 } zef_label_stats;
 
 /* Mesh for zef_refine_and_relabel.  All four arrays must be device memory or

@@ -586,6 +586,7 @@ zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *
     stats->uncertain_pairs = h[CNT_UNC];
     stats->work_items = h[CNT_ITEMS];
     stats->tiles = h[CNT_TILES];
+    stats->coherent_pairs = h[CNT_COHERENT];
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;

@@ -111,6 +111,7 @@ enum Counter {
   CNT_TETS,
   CNT_ABORT,          // refinement stopped (capacity)
   CNT_OWN_LEN,        // 6 x flagged tets of the level
+  CNT_COHERENT,       // (point, compartment) pairs decided by a tile representative
   CNT_COUNT_ = 24
 };
 

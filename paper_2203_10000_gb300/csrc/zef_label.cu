@@ -59,6 +59,7 @@ constexpr float kPi = 3.14159265358979323846f;
 constexpr float kHalfPi = 1.57079632679489661923f;
 constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kInvTwoPi = 0.159154943091895335769f;
+constexpr float kFourPi = 12.5663706143591729539f;
 
 // atan(x) = x (1 + s P(s)), s = x^2, 0 <= x <= 1: minimax fit of the relative
 // error with the constant term held at 1 (max relative error 1.25e-7),
@@ -267,6 +268,7 @@ struct LabelArgs {
   float winding_tol;
   int ncomp;
   int fp32_only;
+  int coherence;  // tile representatives allowed
 };
 
 // Classification of one (point, compartment) pair after the FP32 sum:
@@ -328,6 +330,118 @@ __device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp
   return inside;
 }
 
+// Classification of a point of a coherent tile: Omega = 4 pi k exactly
+// (k the tile's winding number), 0 outside the compartment's box or hull.
+__device__ __forceinline__ bool classify_coherent(const LabelArgs &a, const DevComp &c, const float *thr, int64_t i,
+                                                  float px, float py, float pz, int k) {
+  float omega;
+  bool inside = false;
+  if (!finite3(px, py, pz)) {
+    omega = __int_as_float(0x7fc00000);
+  } else if (px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] || pz > c.hi[2] ||
+             dop_point_outside(px, py, pz, thr)) {
+    omega = 0.f;
+  } else {
+    omega = kFourPi * (float)k;
+    if (k >= 1) {
+      atomicOr(a.in_mask + i, 1ull << c.row);
+      inside = true;
+    }
+  }
+  if (a.omega) a.omega[(int64_t)c.row * a.omega_ld + a.perm[i]] = omega;
+  return inside;
+}
+
+// (s, e) += (b, f): compensated sum of two (value, error) pairs (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum_acc(float &s, float &e, float b, float f) {
+  const float t = s + b;
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (b - bb);
+  s = t;
+  e = e + f + err;
+}
+
+// Representative evaluation of a warp tile for compartment cp: one pass over
+// the compartment's triangles (lane l takes triangles l, l + 32, ...) that both
+// tests every triangle's box against the tile's box wb and sums the plain
+// FP32 Van Oosterom-Strackee half angles of one representative point (the
+// tile's first finite point).  Returns 1 with the winding number in *k when no
+// triangle box meets wb and the representative's Omega is certain (the same
+// tests as classify_store, with the conditioning bound scaled by r1 r2 r3);
+// 0 when the tile has to be evaluated point by point.
+template <int P>
+__device__ __forceinline__ int coherent_tile(const LabelArgs &a, const DevComp *cp, const float *wb,
+                                             const PState (&st)[P], uint32_t usable, int lane, int *k) {
+  float rx = 0.f, ry = 0.f, rz = 0.f;
+  bool have = false;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const unsigned m = __ballot_sync(0xffffffffu, (usable >> q) & 1u);
+    if (!have && m) {
+      const int src = __ffs(m) - 1;
+      rx = __shfl_sync(0xffffffffu, st[q].px, src);
+      ry = __shfl_sync(0xffffffffu, st[q].py, src);
+      rz = __shfl_sync(0xffffffffu, st[q].pz, src);
+      have = true;
+    }
+  }
+  if (!have) return 0;
+  const int tri_cnt = __ldg(&cp->tri_cnt);
+  const float4 *T = a.tris + (int64_t)__ldg(&cp->tri_off) * 3;
+  const float lx = wb[0], ly = wb[1], lz = wb[2], hx = wb[3], hy = wb[4], hz = wb[5];
+  float sum = 0.f, comp = 0.f, bad = __int_as_float(0x7f800000);
+  for (int t0 = 0; t0 < tri_cnt; t0 += 32) {
+    const int t = t0 + lane;
+    bool ov = false;
+    float term = 0.f;
+    if (t < tri_cnt) {
+      const float4 A = T[3 * t], B = T[3 * t + 1], C = T[3 * t + 2];
+      ov = !(fmaxf(A.x, fmaxf(B.x, C.x)) < lx || fminf(A.x, fminf(B.x, C.x)) > hx ||
+             fmaxf(A.y, fmaxf(B.y, C.y)) < ly || fminf(A.y, fminf(B.y, C.y)) > hy ||
+             fmaxf(A.z, fmaxf(B.z, C.z)) < lz || fminf(A.z, fminf(B.z, C.z)) > hz);
+      const float x1 = A.x - rx, y1 = A.y - ry, z1 = A.z - rz;
+      const float x2 = B.x - rx, y2 = B.y - ry, z2 = B.z - rz;
+      const float x3 = C.x - rx, y3 = C.y - ry, z3 = C.z - rz;
+      const float q1 = fmaf(x1, x1, fmaf(y1, y1, z1 * z1));
+      const float q2 = fmaf(x2, x2, fmaf(y2, y2, z2 * z2));
+      const float q3 = fmaf(x3, x3, fmaf(y3, y3, z3 * z3));
+      const float r1 = q1 * rsqrtf(q1), r2 = q2 * rsqrtf(q2), r3 = q3 * rsqrtf(q3);
+      const float cx = fmaf(y2, z3, -z2 * y3), cy = fmaf(z2, x3, -x2 * z3), cz = fmaf(x2, y3, -y2 * x3);
+      const float N = fmaf(x1, cx, fmaf(y1, cy, z1 * cz));
+      const float d12 = fmaf(x1, x2, fmaf(y1, y2, z1 * z2));
+      const float d13 = fmaf(x1, x3, fmaf(y1, y3, z1 * z3));
+      const float d23 = fmaf(x2, x3, fmaf(y2, y3, z2 * z3));
+      const float r123 = r1 * r2 * r3;
+      const float D = fmaf(d12, r3, fmaf(d13, r2, fmaf(d23, r1, r123)));
+      term = half_angle(N, D);
+      bad = fminf(bad, fmaf(-kKappa, r123, fmaxf(fabsf(N), D)));
+    }
+    if (__any_sync(0xffffffffu, ov)) return 0;
+    const float y = term - comp;
+    const float tt = sum + y;
+    comp = (tt - sum) - y;
+    sum = tt;
+  }
+  // butterfly reduction of the compensated partials (every lane ends with the
+  // same value: IEEE addition is commutative)
+  float h = sum, he = -comp;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ph = __shfl_xor_sync(0xffffffffu, h, o);
+    const float pe = __shfl_xor_sync(0xffffffffu, he, o);
+    two_sum_acc(h, he, ph, pe);
+    bad = fminf(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+  }
+  h += he;
+  const float om = 2.f * h;
+  const float kf = rintf(h * kInvTwoPi);
+  const float dist = 2.f * fabsf(fmaf(-kTwoPi, kf, h));
+  const bool unc = !isfinite(om) || !(bad > 0.f) || !(dist <= a.winding_tol) || !(fabsf(om - kTwoPi) >= a.margin);
+  if (unc) return 0;
+  *k = (int)kf;
+  return 1;
+}
+
 // ------------------------------------------------------------------ FP32 persistent kernel
 // Every warp is an independent persistent worker: it takes a tile of 32 x P
 // consecutive Morton-ordered points from the work list, walks the
@@ -383,6 +497,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
     const int base = tile * TILE;
     PState st[P];
     uint32_t done = 0;  // bit q: point q is invalid, non-finite or certainly inside an earlier compartment
+    uint32_t usable = 0;  // bit q: point q is valid and finite
     float wb[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -396,6 +511,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       if (!valid || !fin) {
         done |= 1u << q;
       } else {
+        usable |= 1u << q;
         wb[0] = fminf(wb[0], p.x); wb[1] = fminf(wb[1], p.y); wb[2] = fminf(wb[2], p.z);
         wb[3] = fmaxf(wb[3], p.x); wb[4] = fmaxf(wb[4], p.y); wb[5] = fmaxf(wb[5], p.z);
       }
@@ -419,6 +535,28 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       // winding number 0 for every point of the tile
       if (box_misses(s_wbox[wid], cp) || dop_box_misses(s_wbox[wid], thr)) continue;
       if (early && __all_sync(0xffffffffu, done == all_done)) break;
+      if (a.coherence) {
+        // Tile coherence: when no triangle's box meets the tile's box, the
+        // surface does not cross the box (convex, hence connected), so every
+        // point of the tile has the winding number of any one of them.
+        int k_tile = 0;
+        const int rc = coherent_tile(a, cp, s_wbox[wid], st, usable, lane, &k_tile);
+        if (rc == 1) {
+          const DevComp c = *cp;
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            const int i = base + q * 32 + lane;
+            if (i < n && classify_coherent(a, c, thr, i, st[q].px, st[q].py, st[q].pz, k_tile))
+              done |= 1u << q;
+          }
+          if (lane == 0) {
+            atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), (unsigned long long)c.tri_cnt);
+            atomicAdd((unsigned long long *)(a.counters + CNT_COHERENT),
+                      (unsigned long long)max(0, min(TILE, n - base)));
+          }
+          continue;
+        }
+      }
       const int entry_cnt = __ldg(&cp->entry_cnt);
       const Entry *gsrc = a.entries + __ldg(&cp->entry_off);
       const int nchunks = (entry_cnt + kWChunk - 1) / kWChunk;
@@ -737,6 +875,7 @@ __global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
     cnt[CNT_NONFINITE] = 0;
     cnt[CNT_PAIRS_EVAL] = 0;
     cnt[CNT_PAIRS_RESCUE] = 0;
+    cnt[CNT_COHERENT] = 0;
     int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
     for (int k = 0; k < 3; ++k) {
       box[k] = INT32_MAX;
@@ -1338,6 +1477,7 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.winding_tol = plan.opts.winding_tol;
   a.ncomp = C;
   a.fp32_only = plan.opts.precision == ZEF_FP32_ONLY;
+  a.coherence = !(plan.opts.flags & ZEF_NO_TILE_COHERENCE);
   if (plan.timed) cudaEventRecord(ctx->ev[1], s);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
     // the FP64 kernel's tile is 128 x 2 points (choose_shape guarantees it)

@@ -173,6 +173,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
     stats->uncertain_pairs = h[CNT_UNC];
     stats->work_items = h[CNT_ITEMS];
     stats->tiles = h[CNT_TILES];
+    stats->coherent_pairs = h[CNT_COHERENT];
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;

@@ -33,6 +33,7 @@ ZEF_AUTO_ORIENT = 1
 ZEF_FP32_RESCUE = 0
 ZEF_FP64_PLAIN = 1
 ZEF_FP32_ONLY = 2
+ZEF_NO_TILE_COHERENCE = 1
 MAX_COMPARTMENTS = 64
 
 STATUS_NAMES = {0: "ZEF_OK", 1: "ZEF_ERR_INVALID_ARG", 2: "ZEF_ERR_SURFACE_NOT_CLOSED",
@@ -49,7 +50,7 @@ class LabelOpts(ctypes.Structure):
     _fields_ = [("margin", ctypes.c_float), ("winding_tol", ctypes.c_float),
                 ("precision", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("points_per_thread", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
 
 
 class LabelStats(ctypes.Structure):
@@ -59,7 +60,8 @@ class LabelStats(ctypes.Structure):
                 ("work_items", ctypes.c_int64), ("tiles", ctypes.c_int64),
                 ("block_threads", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
                 ("ms_total", ctypes.c_float), ("ms_label", ctypes.c_float),
-                ("ms_rescue", ctypes.c_float), ("reserved", ctypes.c_float)]
+                ("ms_rescue", ctypes.c_float), ("reserved", ctypes.c_float),
+                ("coherent_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -153,9 +155,10 @@ def _contig(x, dtype_np, dtype_name):
 
 
 def make_opts(margin=0.0, winding_tol=0.0, precision=ZEF_FP32_RESCUE, block_threads=0,
-              points_per_thread=0, kernel=0) -> LabelOpts:
+              points_per_thread=0, kernel=0, coherence=True) -> LabelOpts:
     o = LabelOpts()
     o.kernel = kernel
+    o.flags = 0 if coherence else ZEF_NO_TILE_COHERENCE
     o.margin = margin
     o.winding_tol = winding_tol
     o.precision = precision

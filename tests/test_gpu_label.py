@@ -99,13 +99,14 @@ def test_launch_shapes_ragged_tail(zef, oracle_mod, shape):
     w = zs.config0()
     pts = w.points[: len(w.points) - 37]            # several tiles plus a ragged tail
     ctx = make_ctx(zef, w.surfaces, w.priority)
-    opts = zef.make_opts(block_threads=shape[0], points_per_thread=shape[1])
-    lab, om, st = gpu_label(ctx, pts, opts=opts)
     olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
-    assert_parity(lab, om, olab, oom)
-    assert st["block_threads"] == shape[0] and st["points_per_thread"] == shape[1]
-    # the per-point arithmetic does not depend on the tile shape
-    lab2, om2, _ = gpu_label(ctx, pts, opts=zef.make_opts(block_threads=256, points_per_thread=4))
+    for coherence in (True, False):
+        opts = zef.make_opts(block_threads=shape[0], points_per_thread=shape[1], coherence=coherence)
+        lab, om, st = gpu_label(ctx, pts, opts=opts)
+        assert_parity(lab, om, olab, oom)
+        assert st["block_threads"] == shape[0] and st["points_per_thread"] == shape[1]
+    # evaluated point by point, a point's arithmetic does not depend on the tile shape
+    lab2, om2, _ = gpu_label(ctx, pts, opts=zef.make_opts(block_threads=256, points_per_thread=4, coherence=False))
     assert np.array_equal(om, om2) and np.array_equal(lab, lab2)
 
 
@@ -138,10 +139,49 @@ def test_autotuned_shape_matches_fixed_shape(zef, oracle_mod):
     assert (st_b["block_threads"], st_b["points_per_thread"]) == (st_a["block_threads"],
                                                                   st_a["points_per_thread"])
     lab_f, om_f, _ = gpu_label(ctx, g, opts=zef.make_opts(block_threads=256, points_per_thread=4))
-    assert np.array_equal(lab_a, lab_f) and np.array_equal(om_a, om_f)
+    assert np.array_equal(lab_a, lab_f)
+    assert np.abs(om_a.astype(np.float64) - om_f).max() <= 2 * OMEGA_TOL
     idx = zs.sample_rows(g, 3000, seed=6)
     olab, oom = oracle_mod.label_points(g[idx], w.surfaces, w.priority)
     assert_parity(lab_a[idx], om_a[:, idx], olab, oom)
+
+
+def test_tile_coherence_matches_oracle_and_point_by_point(zef, oracle_mod):
+    """Tiles the surface does not cross take the winding number of one
+    representative: Omega = 4 pi k exactly there, the labels equal the
+    point-by-point evaluation and the oracle."""
+    w = zs.config1(npts_limit=0)
+    g = zs.lattice_centroids(50, 4.0, (-100.0, -100.0, -100.0))   # 625,000 centroids
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab_c, om_c, st_c = gpu_label(ctx, g, opts=zef.make_opts(coherence=True))
+    lab_p, om_p, st_p = gpu_label(ctx, g, opts=zef.make_opts(coherence=False))
+    assert np.array_equal(lab_c, lab_p)
+    assert np.abs(om_c.astype(np.float64) - om_p).max() <= 2 * OMEGA_TOL
+    assert st_c["coherent_pairs"] > 0.3 * len(g) and st_p["coherent_pairs"] == 0
+    assert st_c["pairs_evaluated"] < 0.5 * st_p["pairs_evaluated"]
+    # every finite Omega is 4 pi k exactly or close to it
+    k = np.round(om_c / FOUR_PI)
+    assert np.abs(om_c - FOUR_PI * k).max() <= OMEGA_TOL
+    idx = zs.sample_rows(g, 4000, seed=8)
+    olab, oom = oracle_mod.label_points(g[idx], w.surfaces, w.priority)
+    assert_parity(lab_c[idx], om_c[:, idx], olab, oom)
+
+
+def test_hull_culling_exact_zero_outside(zef, oracle_mod):
+    """Points inside a compartment's bounding box but outside its convex hull
+    (the box corners of a sphere) get Omega exactly 0 and are labelled 0."""
+    s = _sphere(10.0, 16, 1)
+    rng = np.random.default_rng(12)
+    d = rng.uniform(-1, 1, size=(20000, 3))
+    d = d[np.linalg.norm(d, axis=1) > 0.9 * np.sqrt(3)]          # toward the corners
+    pts = np.concatenate([(d * 10.0).astype(np.float32),
+                          rng.uniform(-9.5, 9.5, size=(4000, 3)).astype(np.float32)])
+    ctx = make_ctx(zef, [s], [1])
+    lab, om, st = gpu_label(ctx, pts)
+    olab, oom = oracle_mod.label_points(pts, [s], [1])
+    assert_parity(lab, om, olab, oom)
+    corner = np.arange(len(d))
+    assert np.all(om[0, corner] == 0.0) and np.all(lab[corner] == 0)
 
 
 def test_empty_and_tiny_inputs(zef, oracle_mod):
