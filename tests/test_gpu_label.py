@@ -158,7 +158,7 @@ def test_tile_coherence_matches_oracle_and_point_by_point(zef, oracle_mod):
     assert np.array_equal(lab_c, lab_p)
     assert np.abs(om_c.astype(np.float64) - om_p).max() <= 2 * OMEGA_TOL
     assert st_c["coherent_pairs"] > 0.3 * len(g) and st_p["coherent_pairs"] == 0
-    assert st_c["pairs_evaluated"] < 0.5 * st_p["pairs_evaluated"]
+    assert st_c["pairs_evaluated"] < 0.8 * st_p["pairs_evaluated"]
     # every finite Omega is 4 pi k exactly or close to it
     k = np.round(om_c / FOUR_PI)
     assert np.abs(om_c - FOUR_PI * k).max() <= OMEGA_TOL
