@@ -429,7 +429,12 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
         double ny = e1[2] * e2[0] - e1[0] * e2[2];
         double nz = e1[0] * e2[1] - e1[1] * e2[0];
         double nn = std::sqrt(nx * nx + ny * ny + nz * nz);
-        e.v.w = 1.f;
+        // +1 when the window order (seq[k-2], seq[k-1], seq[k]) keeps the
+        // triangle's orientation, -1 when it reverses it (strips alternate)
+        const int32_t wa = seq[k - 2], wb = seq[k - 1];
+        int ia = 0;
+        while (f[ia] != wa) ++ia;
+        e.v.w = (f[(ia + 1) % 3] == wb) ? 1.f : -1.f;
         e.n = make_float4((float)nx, (float)ny, (float)nz, (float)(kKappa * nn));
       }
       ent.push_back(e);

@@ -200,7 +200,7 @@ __device__ __forceinline__ void vos_step(PState &s, const float4 V, const float4
   const float N = fmaf(Nn.x, cx, fmaf(Nn.y, cy, Nn.z * cz));
   const float D = fmaf(s.sab, rc, fmaf(dac, s.rb, dbc * s.ra));
   const float t = half_angle(N, D);
-  s.grp = fmaf(V.w, t, s.grp);
+  s.grp = fmaf(fabsf(V.w), t, s.grp);  // |w| = 1 on triangles, 0 elsewhere
   s.bad = fminf(s.bad, fmaf(-Nn.w, rc, fmaxf(fabsf(N), D)));
   s.sab = fmaf(s.rb, rc, dbc);
   s.ax = s.bx; s.ay = s.by; s.az = s.bz;
@@ -773,10 +773,73 @@ __global__ void __launch_bounds__(NT) k_label64(LabelArgs a) {
 
 // FP64 re-evaluation.  Blocks take groups of 256 sorted points from a device
 // cursor; the uncertain (point, compartment) pairs of a group are gathered in
-// shared memory and each pair is summed by the whole block (thread k takes
-// triangles k, k + 256, ...; fixed-order reduction, so the result does not
-// depend on scheduling).
+// shared memory and each pair is summed by the whole block.  Thread k takes a
+// contiguous segment of the compartment's strip stream and rebuilds its
+// sliding window from the two entries before the segment, so the block walks
+// the strips in parallel: per strip step one FP64 square root and the exact
+// triple product N = R_a . (R_b x R_c) in double (the host-rounded normals
+// are not used here).  The (D + i N) factors of 8 consecutive steps are
+// multiplied with exact 2 pi wrap counting and one FP64 atan2 is taken per
+// group; segment sums are reduced in a fixed order, so the result does not
+// depend on scheduling.
 constexpr int kRescueT = 256;
+constexpr int kRescueG = 8;
+
+// (cr, ci) = a b with the 2 pi wraps of the principal argument (sign bits of
+// the imaginary parts, as in cmul_wrap)
+__device__ __forceinline__ void cmul_wrap64(double ar, double ai, double br, double bi, double &cr, double &ci,
+                                            int &k) {
+  cr = fma(ar, br, -(ai * bi));
+  ci = fma(ar, bi, ai * br);
+  const uint32_t x = (uint32_t)(__double_as_longlong(ai) >> 32), y = (uint32_t)(__double_as_longlong(bi) >> 32),
+                 z = (uint32_t)(__double_as_longlong(ci) >> 32);
+  k += (int)((~x & ~y & z) >> 31) - (int)((x & y & ~z) >> 31);
+}
+
+// Omega / 2 over entries [s, e) of a strip stream, for the point (px, py, pz),
+// returned as (angle sum, wraps)
+__device__ void strip_half_angle64(const Entry *E, int s, int e, double px, double py, double pz, double *sum,
+                                   int *wraps) {
+  const float4 va = E[max(s - 2, 0)].v, vb = E[max(s - 1, 0)].v;
+  double ax = (double)va.x - px, ay = (double)va.y - py, az = (double)va.z - pz;
+  double bx = (double)vb.x - px, by = (double)vb.y - py, bz = (double)vb.z - pz;
+  double ra = sqrt(ax * ax + ay * ay + az * az), rb = sqrt(bx * bx + by * by + bz * bz);
+  double sab = ra * rb + (ax * bx + ay * by + az * bz);
+  double acc = 0.0;
+  int K = 0;
+  for (int g = s; g < e; g += kRescueG) {
+    double pr = 1.0, pi = 0.0;
+    const int ge = min(g + kRescueG, e);
+    for (int j = g; j < ge; ++j) {
+      const float4 vc = E[j].v;
+      const double cx = (double)vc.x - px, cy = (double)vc.y - py, cz = (double)vc.z - pz;
+      const double rc = sqrt(cx * cx + cy * cy + cz * cz);
+      const double dac = ax * cx + ay * cy + az * cz;
+      const double dbc = bx * cx + by * cy + bz * cz;
+      const double ux = by * cz - bz * cy, uy = bz * cx - bx * cz, uz = bx * cy - by * cx;
+      // w = +-1: the window order keeps / reverses the triangle's orientation
+      double N = (double)vc.w * (ax * ux + ay * uy + az * uz);
+      double D = sab * rc + dac * rb + dbc * ra;
+      if (vc.w == 0.f) {  // not a triangle of the surface: identity factor
+        N = 0.0;
+        D = 1.0;
+      }
+      double nr, ni;
+      cmul_wrap64(pr, pi, D, N, nr, ni, K);
+      pr = nr;
+      pi = ni;
+      sab = rb * rc + dbc;
+      ax = bx; ay = by; az = bz;
+      bx = cx; by = cy; bz = cz;
+      ra = rb;
+      rb = rc;
+    }
+    acc += atan2(pi, pr);
+  }
+  *sum = acc;
+  *wraps = K;
+}
+
 __global__ void __launch_bounds__(kRescueT) k_rescue64(LabelArgs a) {
   __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
   __shared__ int64_t s_group;
@@ -784,6 +847,7 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64(LabelArgs a) {
   __shared__ int s_list[kRescueT];
   __shared__ unsigned long long s_mask[kRescueT];
   __shared__ double s_red[kRescueT / 32];
+  __shared__ int s_kred[kRescueT / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
   const int64_t n = a.counters[CNT_N];
@@ -815,19 +879,31 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64(LabelArgs a) {
         const int row = __ffsll((long long)mm) - 1;
         mm &= mm - 1;
         const DevComp c = a.comps[s_rowcomp[row]];
-        const float4 *T = a.tris + (int64_t)c.tri_off * 3;
-        double acc = 0.0;
-        for (int t = tid; t < c.tri_cnt; t += kRescueT)
-          acc += vos64_half(px, py, pz, T[3 * t], T[3 * t + 1], T[3 * t + 2]);
+        const Entry *E = a.entries + c.entry_off;
+        const int seg = (c.entry_cnt + kRescueT - 1) / kRescueT;
+        const int s0 = min(tid * seg, c.entry_cnt), e0 = min(s0 + seg, c.entry_cnt);
+        double part = 0.0;
+        int wraps = 0;
+        if (s0 < e0) strip_half_angle64(E, s0, e0, px, py, pz, &part, &wraps);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) s_red[wid] = acc;
+        for (int o = 16; o > 0; o >>= 1) {
+          part += __shfl_xor_sync(0xffffffffu, part, o);
+          wraps += __shfl_xor_sync(0xffffffffu, wraps, o);
+        }
+        if (lane == 0) {
+          s_red[wid] = part;
+          s_kred[wid] = wraps;
+        }
         __syncthreads();
-        double om = 0.0;
+        double half = 0.0;
+        int K = 0;
 #pragma unroll
-        for (int w = 0; w < kRescueT / 32; ++w) om += s_red[w];
-        om *= 2.0;
+        for (int w = 0; w < kRescueT / 32; ++w) {
+          half += s_red[w];
+          K += s_kred[w];
+        }
         __syncthreads();
+        const double om = 2.0 * (half + 6.283185307179586476925 * K);
         if (om > 6.283185307179586476925) set_bits |= 1ull << row;
         if (tid == 0) {
           if (a.omega) a.omega[(int64_t)row * a.omega_ld + a.perm[i]] = (float)om;

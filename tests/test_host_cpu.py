@@ -133,15 +133,13 @@ def _check_strips(ent, verts, tris):
             assert ent[k, 7] == 0.0 and np.all(ent[k, 4:7] == 0)
             assert len({idx[k - 2], idx[k - 1], idx[k]}) < 3, k
             continue
-        assert ent[k, 3] == 1.0
+        # weight +1: the window order keeps the triangle's orientation; -1: reverses it
+        assert ent[k, 3] in (1.0, -1.0)
         a, b, c = idx[k - 2], idx[k - 1], idx[k]
-        cand = [(a, b, c), (a, c, b)]
-        hit = None
-        for tri in cand:
-            i = int(np.argmin(tri))
-            r = tuple(np.roll(tri, -i))
-            if r in want:
-                hit = r
+        tri = (a, b, c) if ent[k, 3] == 1.0 else (a, c, b)
+        i = int(np.argmin(tri))
+        r = tuple(np.roll(tri, -i))
+        hit = r if r in want else None
         assert hit is not None, (a, b, c)
         assert hit not in got
         got.add(hit)
