@@ -14,16 +14,28 @@ extern "C" {
 
 /* Strip stream of registered compartment `index` (registration order).
    Each entry is 8 floats: the vertex entering the sliding triangle window
-   (x, y, z), a weight (1 when the window is a surface triangle, 0 on the two
-   entries that start a strip and on padding), that triangle's doubled-area
-   normal (x, y, z) with the surface orientation, and kappa * |normal| (-inf
-   when the weight is 0).  Writes min(count, cap) entries to `out` (host,
+   (x, y, z), a weight (+1 when the window (a, b, c) is a surface triangle
+   in its own orientation, -1 when it is the triangle (a, c, b), 0 when the
+   window is not a triangle: the two entries that start the stream, strip
+   restarts and padding, whose windows repeat a vertex), that triangle's
+   doubled-area normal (x, y, z) with the surface orientation, and
+   kappa * |normal| (normal and kappa term are 0 when the weight is 0).  Writes min(count, cap) entries to `out` (host,
    nullable) and the entry count to *count.  Works on host-only contexts. */
 zef_status zef_debug_strip_entries(const zef_ctx *ctx, int32_t index, float *out, int64_t cap,
                                    int64_t *count);
 
 /* Entry and strip counts of compartment `index`. */
 zef_status zef_debug_strip_stats(const zef_ctx *ctx, int32_t index, int64_t *entries, int64_t *strips);
+
+/* The label kernel's FP32 atan2: out[i] = atan2(y[i], x[i]) in (-pi, pi],
+   computed by the same device function the FP32 kernel applies to the
+   Van Oosterom-Strackee pair (N, D) of Sec. 2.1.3 (range reduction to
+   min/max in [0, 1], a minimax polynomial of degree 8 in x^2, octant
+   reflections).  y, x, out: n floats each in device memory of the context's
+   device; synchronizes.  Denormal inputs are flushed to zero.  Errors:
+   ZEF_ERR_INVALID_ARG (null or host arrays, n < 0), ZEF_ERR_NOT_READY on a
+   host-only context. */
+zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);
 
 /* Failure-detection probe: launches one block whose threads wait on a device
    barrier that is never signalled, with the given limit in nanoseconds

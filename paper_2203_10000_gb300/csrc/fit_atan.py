@@ -5,7 +5,7 @@ the constant term is held at 1 so that the relative error vanishes as x -> 0
 (far triangles, whose tiny solid angles dominate the count, then carry no
 systematic bias).  The coefficients minimise the maximum relative error by
 Lawson's iteratively reweighted least squares (a discrete minimax method) on a
-dense grid.  Run: python fit_atan.py [degree]  (the kernel uses degree 7).
+dense grid.  Run: python fit_atan.py [degree]  (the kernel uses degree 8).
 """
 import sys
 

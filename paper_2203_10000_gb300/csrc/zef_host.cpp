@@ -761,6 +761,22 @@ extern "C" zef_status zef_debug_strip_stats(const zef_ctx *ctx, int32_t index, i
   return ZEF_OK;
 }
 
+extern "C" zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out,
+                                           int64_t n) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context");
+  if (n < 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "negative count");
+  if (n == 0) return ZEF_OK;
+  if (!y || !x || !out) return fail(ctx, ZEF_ERR_INVALID_ARG, "null array");
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(y, ctx->device) || !is_device_ptr(x, ctx->device) || !is_device_ptr(out, ctx->device))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "arrays must be device memory of the context's device");
+  zef_status st = launch_debug_half_angle(ctx, y, x, out, n);
+  if (st) return st;
+  return zef_synchronize(ctx);
+}
+
 extern "C" zef_status zef_debug_wait_probe(zef_ctx *ctx, int64_t limit_ns) {
   if (!ctx) return ZEF_ERR_INVALID_ARG;
   ctx->err.clear();

@@ -191,6 +191,7 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap);
 zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan);
 zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off);
 zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns);
+zef_status launch_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);
 zef_status upload_dop_directions(zef_ctx *ctx);
 zef_status scan_exclusive(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, int64_t len_mul,
                           int64_t len_cap, int64_t *total_out, uint32_t *bsums);

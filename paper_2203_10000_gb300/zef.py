@@ -119,6 +119,8 @@ _lib.zef_debug_strip_entries.argtypes = [_P, _I32, _P, _I64, ctypes.POINTER(_I64
 _lib.zef_debug_strip_entries.restype = ctypes.c_int
 _lib.zef_debug_wait_probe.argtypes = [_P, _I64]
 _lib.zef_debug_wait_probe.restype = ctypes.c_int
+_lib.zef_debug_half_angle.argtypes = [_P, _P, _P, _P, _I64]
+_lib.zef_debug_half_angle.restype = ctypes.c_int
 
 
 def lib():
@@ -244,6 +246,18 @@ class Context:
         """Run the bounded-wait probe; returns the status code (expected
         ZEF_ERR_TIMEOUT) without raising."""
         return int(_lib.zef_debug_wait_probe(self._h, int(limit_ns)))
+
+    def half_angle(self, y, x, out):
+        """The FP32 label kernel's atan2(y, x) applied elementwise to device
+        float32 tensors (diagnostics)."""
+        for t in (y, x, out):
+            if not _is_torch(t) or not t.is_cuda or t.dtype.itemsize != 4 or not t.is_contiguous():
+                raise ValueError("half_angle wants contiguous float32 CUDA tensors")
+        n = y.numel()
+        if x.numel() != n or out.numel() != n:
+            raise ValueError("size mismatch")
+        self._check(_lib.zef_debug_half_angle(self._h, y.data_ptr(), x.data_ptr(), out.data_ptr(), n))
+        return out
 
     def set_priority(self, ids):
         a = np.ascontiguousarray(ids, dtype=np.int32)

@@ -71,6 +71,40 @@ def test_bounded_wait_expires_and_context_survives(zef, oracle_mod):
     assert_parity(lab, om, olab, oom)
 
 
+# ------------------------------------------------------------------ FP32 atan2
+def test_fp32_atan2_within_atan2f_bound(zef):
+    """The label kernel's own atan2 against FP64 atan2, with CUDA's atan2f
+    (torch.atan2 on the device) measured on the same float32 inputs: both
+    within atan2f's documented maximum error of 3 ulp.  Inputs: log-uniform
+    magnitudes over 2^-40..2^40 of both signs, half of them with |y|/|x|
+    near 1 (the octant boundary), plus the axes."""
+    rng = np.random.default_rng(5)
+    n = 1 << 22
+    y = rng.choice([-1.0, 1.0], n) * 2.0 ** rng.uniform(-40, 40, n)
+    x = rng.choice([-1.0, 1.0], n) * 2.0 ** rng.uniform(-40, 40, n)
+    m = n // 2
+    x[:m] = rng.choice([-1.0, 1.0], m) * np.abs(y[:m]) * (1 + rng.uniform(-0.25, 0.25, m))
+    axes_y = [0.0, 0.0, -0.0, -0.0, 1.0, -1.0, 3.0, -3.0, 2.0 ** -40, 1.0]
+    axes_x = [1.0, -1.0, 1.0, -1.0, 0.0, 0.0, 3.0, -3.0, 1.0, 2.0 ** -40]
+    y = np.concatenate([y, axes_y]).astype(np.float32)
+    x = np.concatenate([x, axes_x]).astype(np.float32)
+    ref = np.arctan2(y.astype(np.float64), x.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    ty, tx = torch.from_numpy(y).cuda(), torch.from_numpy(x).cuda()
+    ctx = zef.Context(0)
+    ours = ctx.half_angle(ty, tx, torch.empty_like(ty)).cpu().numpy().astype(np.float64)
+    cuda = torch.atan2(ty, tx).cpu().numpy().astype(np.float64)
+    e_ours = np.abs(ours - ref) / ulp
+    e_cuda = np.abs(cuda - ref) / ulp
+    print(f"max ulp: kernel atan2 {e_ours.max():.3f}, atan2f {e_cuda.max():.3f}")
+    assert e_cuda.max() <= 3.0
+    assert e_ours.max() <= 3.0, (e_ours.max(), y[np.argmax(e_ours)], x[np.argmax(e_ours)])
+    assert np.array_equal(np.signbit(ours[-10:]), np.signbit(ref[-10:]))
+    # a zero pair has no angle: NaN, which the label kernel re-evaluates in FP64
+    z = torch.zeros(4, device="cuda")
+    assert torch.isnan(ctx.half_angle(z, z.clone(), torch.empty_like(z))).all()
+
+
 # ------------------------------------------------------------------ small case
 def test_config0_parity(zef, oracle_mod):
     w = zs.config0()
