@@ -200,10 +200,33 @@ zef_status zef_compartment_priority(zef_ctx *ctx, const int32_t *ids, int32_t n)
              -1 for a point with a non-finite coordinate
      omega   nullable; [C][n] float32 out, row r = the r-th compartment in
              priority order: the solid angle Omega in steradians (0 exactly
-             where the point is outside the compartment's bounding box)
+             where the point is outside the compartment's bounding box or
+             convex-hull bound, 4 pi k exactly for the points of a tile the
+             surface provably does not cross; NaN for non-finite points)
      opts    nullable = defaults;  stats nullable (non-NULL synchronizes) */
 zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
                             float *omega, const zef_label_opts *opts, zef_label_stats *stats);
+
+/* Element labels by the four-nodes rule (Sec. 2.1.3: a tetrahedron whose
+   four nodes all lie inside dS is an element of S) under the priority order
+   of Sec. 2.1: the label of a tet is the first compartment in priority order
+   whose surface encloses all four of its nodes (Omega > 2 pi at each), 0 when
+   none does, -1 when one of its nodes has a non-finite coordinate.  Every
+   (node, compartment) pair is decided (no priority early exit): a node
+   labeled with one compartment may also lie inside a later one.
+     nodes        [n_nodes][3] float32
+     tets         [n_tets][4] int32 node indices, 0 <= index < n_nodes
+     elem_labels  [n_tets] int32 out
+     node_labels  nullable; [n_nodes] int32 out, as zef_label_points' labels
+     opts, stats  as zef_label_points; stats describe the node labeling
+   Host or device arrays (the rules of zef_label_points).  A tet with an index
+   outside [0, n_nodes) gets -1 and the call returns ZEF_ERR_INVALID_ARG (an
+   all-device call without stats does not synchronize: the next
+   zef_synchronize reports it). */
+zef_status zef_label_elements(zef_ctx *ctx, const float *nodes, int64_t n_nodes,
+                              const int32_t *tets, int64_t n_tets, int32_t *elem_labels,
+                              int32_t *node_labels, const zef_label_opts *opts,
+                              zef_label_stats *stats);
 
 /* Largest point count of one zef_label_points_noalloc call. */
 #define ZEF_NOALLOC_MAX_POINTS 65536

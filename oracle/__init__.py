@@ -12,6 +12,9 @@ CPU-baseline leg import this package.  It shares no code with the CUDA path
   intersecting compartments are resolved by the layer hierarchy: the first
   compartment of the priority list that encloses the point wins (Sec. 2.1);
   a point enclosed by none gets 0, the temporary bounding box.
+* ``label_elements`` -- element labels by the four-nodes rule (Sec. 2.1.3: a
+  tetrahedron whose four nodes are inside a compartment surface belongs to
+  that compartment) under the same priority list.
 * ``refine.refine_and_relabel`` -- the refinement/re-labeling recursion
   (Sec. 2.1.2, 2.1.3 item 2).
 """
@@ -141,3 +144,27 @@ def label_points(points, surfaces, priority, threads: int = 0):
         decided |= hit
     labels[~finite] = -1
     return labels, omega
+
+
+def label_elements(nodes, tets, surfaces, priority, threads: int = 0):
+    """Element labels by the four-nodes rule (Sec. 2.1.3) with the priority
+    list of Sec. 2.1: a tet gets the first compartment in priority order whose
+    surface encloses all four of its nodes (Omega > 2 pi at each node), 0 when
+    none does, and -1 when a node has a non-finite coordinate.
+
+    Returns (element labels int32 (M,), node labels int32 (N,))."""
+    node_labels, omega = label_points(nodes, surfaces, priority, threads)
+    t = np.asarray(tets, dtype=np.int64).reshape(-1, 4)
+    if t.size and (t.min() < 0 or t.max() >= node_labels.shape[0]):
+        raise ValueError("tet node index out of range")
+    ins = inside(omega)                      # (C, N); NaN rows compare False
+    prio = [int(i) for i in priority]
+    labels = np.zeros(t.shape[0], dtype=np.int32)
+    decided = np.zeros(t.shape[0], dtype=bool)
+    for row, cid in enumerate(prio):
+        all_four = ins[row][t].all(axis=1)   # every node of the tet inside
+        hit = ~decided & all_four
+        labels[hit] = cid
+        decided |= hit
+    labels[(node_labels[t] < 0).any(axis=1)] = -1
+    return labels, node_labels

@@ -231,6 +231,7 @@ void zef_destroy(zef_ctx *ctx) {
   fr(b.spts); fr(b.perm); fr(b.keys); fr(b.in_mask); fr(b.unc_mask); fr(b.tile_box);
   fr(b.hist); fr(b.flags); fr(b.block_sums); fr(b.items); fr(b.unc_list); fr(b.counters);
   fr(b.labels_tmp); fr(b.pts_tmp); fr(b.omega_tmp); fr(b.tune_pts);
+  fr(ctx->el_node_labels); fr(ctx->el_masks); fr(ctx->el_tets); fr(ctx->el_labels);
   for (auto &p : ctx->rf_buf) fr(p);
   if (ctx->rf_exec) cudaGraphExecDestroy(ctx->rf_exec);
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -505,6 +506,76 @@ zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *
                             const zef_label_opts *opts, zef_label_stats *stats) {
   if (!ctx) return ZEF_ERR_INVALID_ARG;
   ctx->err.clear();
+  return zef::label_points_impl(ctx, pts, n, labels, omega, opts, stats, nullptr, false);
+}
+
+zef_status zef_label_elements(zef_ctx *ctx, const float *nodes, int64_t n_nodes, const int32_t *tets,
+                              int64_t n_tets, int32_t *elem_labels, int32_t *node_labels,
+                              const zef_label_opts *opts, zef_label_stats *stats) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (n_tets < 0 || n_nodes < 0 || (n_tets > 0 && (!tets || !elem_labels)))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad tets/elem_labels arguments");
+  if (n_tets > ((int64_t)1 << 31) - 1) return fail(ctx, ZEF_ERR_INVALID_ARG, "too many tets (max 2^31-1)");
+  if (n_tets > 0 && n_nodes == 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "tets without nodes");
+  if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
+  if (n_nodes > 0 && !nodes) return fail(ctx, ZEF_ERR_INVALID_ARG, "bad nodes argument");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n_nodes == 0) return ZEF_OK;
+  DeviceGuard g(ctx->device);
+  const bool dnl = node_labels && is_device_ptr(node_labels, ctx->device);
+  const bool dtet = n_tets == 0 || is_device_ptr(tets, ctx->device);
+  const bool delem = n_tets == 0 || is_device_ptr(elem_labels, ctx->device);
+  zef_status st = ensure_buffer(ctx, &ctx->el_masks, &ctx->el_cap_masks, n_nodes);
+  if (st) return st;
+  int32_t *d_nl = node_labels;
+  if (!dnl) {
+    st = ensure_buffer(ctx, &ctx->el_node_labels, &ctx->el_cap_nodes, n_nodes);
+    if (st) return st;
+    d_nl = ctx->el_node_labels;
+  }
+  const int32_t *d_tets = tets;
+  if (!dtet) {
+    st = ensure_buffer(ctx, &ctx->el_tets, &ctx->el_cap_tets, 4 * n_tets);
+    if (st) return st;
+    d_tets = ctx->el_tets;
+  }
+  int32_t *d_elem = elem_labels;
+  if (!delem) {
+    st = ensure_buffer(ctx, &ctx->el_labels, &ctx->el_cap_labels, n_tets);
+    if (st) return st;
+    d_elem = ctx->el_labels;
+  }
+  // node labels and inside bits of every (node, compartment) pair
+  st = zef::label_points_impl(ctx, nodes, n_nodes, d_nl, nullptr, opts, stats, ctx->el_masks, true);
+  if (st) return st;
+  if (!dtet)
+    CK(cudaMemcpyAsync(ctx->el_tets, tets, (size_t)n_tets * 4 * sizeof(int32_t), cudaMemcpyHostToDevice,
+                       ctx->stream), "copy tets");
+  st = launch_elem_labels(ctx, d_tets, n_tets, n_nodes, d_nl, ctx->el_masks, d_elem);
+  if (st) return st;
+  if (!delem)
+    CK(cudaMemcpyAsync(elem_labels, d_elem, (size_t)n_tets * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream), "copy element labels");
+  if (node_labels && !dnl)
+    CK(cudaMemcpyAsync(node_labels, d_nl, (size_t)n_nodes * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream), "copy node labels");
+  if (stats || !dtet || !delem || (node_labels && !dnl) || !is_device_ptr(nodes, ctx->device))
+    return zef_synchronize(ctx);
+  return ZEF_OK;
+}
+
+}  // extern "C"
+
+namespace zef {
+
+// zef_label_points; with d_masks (device, nullable) the inside bits of every
+// point are written in the caller's order, and full_masks turns the priority
+// early exit off so that every bit is decided.
+zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels, float *omega,
+                             const zef_label_opts *opts, zef_label_stats *stats, unsigned long long *d_masks,
+                             bool full_masks) {
   if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
   if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
   if (n < 0 || (n > 0 && (!pts || !labels)))
@@ -556,6 +627,8 @@ zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *
   plan.d_n = b.counters + CNT_N;
   plan.d_off = b.counters + CNT_OFF;
   plan.opts = o;
+  plan.masks = d_masks;
+  plan.full_masks = full_masks;
   bool need_tune = false;
   plan.shape = choose_shape(ctx, o, n, &need_tune);
   plan.timed = stats != nullptr;
@@ -605,6 +678,10 @@ zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *
   return ZEF_OK;
 }
 
+}  // namespace zef
+
+extern "C" {
+
 zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_label_opts *opts,
                                   zef_level_stats *per_level) {
   if (!ctx) return ZEF_ERR_INVALID_ARG;
@@ -647,6 +724,8 @@ zef_status ensure_buffer(zef_ctx *ctx, T **p, int64_t *cap, int64_t need) {
   return ZEF_OK;
 }
 template zef_status ensure_buffer<float>(zef_ctx *, float **, int64_t *, int64_t);
+template zef_status ensure_buffer<int32_t>(zef_ctx *, int32_t **, int64_t *, int64_t);
+template zef_status ensure_buffer<unsigned long long>(zef_ctx *, unsigned long long **, int64_t *, int64_t);
 
 zef_status ensure_uploaded(zef_ctx *ctx) {
   if (ctx->device == ZEF_HOST_ONLY) return ZEF_OK;

@@ -157,6 +157,13 @@ struct zef_ctx {
   // autotuner cache: key -> shape
   std::vector<std::pair<uint64_t, zef::LaunchShape>> tune_cache;
 
+  // element-label scratch (zef_label_elements)
+  int32_t *el_node_labels = nullptr;
+  unsigned long long *el_masks = nullptr;
+  int32_t *el_tets = nullptr;
+  int32_t *el_labels = nullptr;
+  int64_t el_cap_nodes = 0, el_cap_masks = 0, el_cap_tets = 0, el_cap_labels = 0;
+
   // refinement scratch
   void *rf_buf[8] = {};
   size_t rf_cap[8] = {};
@@ -170,6 +177,9 @@ namespace zef {
 zef_status fail(zef_ctx *ctx, zef_status st, const std::string &msg);
 zef_status cuda_fail(zef_ctx *ctx, cudaError_t e, const char *what);
 zef_status ensure_uploaded(zef_ctx *ctx);
+zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels, float *omega,
+                             const zef_label_opts *opts, zef_label_stats *stats, unsigned long long *d_masks,
+                             bool full_masks);
 template <class T>
 zef_status ensure_buffer(zef_ctx *ctx, T **p, int64_t *cap, int64_t need);
 
@@ -185,12 +195,16 @@ struct LabelPlan {
   zef_label_opts opts;
   LaunchShape shape;
   bool timed;                // record events around the main kernels
+  unsigned long long *masks = nullptr;  // nullable: per-point inside bits (priority rows), caller's order
+  bool full_masks = false;   // evaluate every compartment (no priority early exit)
 };
 
 zef_status label_reserve(zef_ctx *ctx, int64_t n_cap);
 zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan);
 zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off);
 zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns);
+zef_status launch_elem_labels(zef_ctx *ctx, const int32_t *tets, int64_t n_tets, int64_t n_nodes,
+                              const int32_t *node_labels, const unsigned long long *masks, int32_t *elem);
 zef_status launch_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);
 zef_status upload_dop_directions(zef_ctx *ctx);
 zef_status scan_exclusive(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, int64_t len_mul,

@@ -273,6 +273,8 @@ struct LabelArgs {
   int ncomp;
   int fp32_only;
   int coherence;  // tile representatives allowed
+  int early;      // priority early exit: a point certainly inside needs no later compartment
+  unsigned long long *masks_out;  // nullable: inside bits per point in the caller's order
 };
 
 // Classification of one (point, compartment) pair after the FP32 sum:
@@ -490,7 +492,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
   uint32_t ph0 = 0, ph1 = 0;
   const int n = (int)a.counters[CNT_N];  // < 2^31 (checked on the host)
   const int64_t nitems = a.counters[CNT_ITEMS];
-  const bool early = a.omega == nullptr;
+  const bool early = a.early;
   constexpr uint32_t all_done = (1u << P) - 1u;
   for (;;) {
     int64_t item = 0;
@@ -935,6 +937,34 @@ __global__ void k_wait_probe(uint32_t *status, unsigned long long limit_ns) {
   if (__syncthreads_or(!ok) && threadIdx.x == 0) record_timeout(status, 99);
 }
 
+// Element labels (Sec. 2.1.3, a tet belongs to S when its four nodes are
+// inside dS; priority order of Sec. 2.1): the AND of the four nodes' inside
+// bits (priority rows), first set bit -> id, 0 when none; -1 for a tet with a
+// non-finite node, and for an index outside [0, n_nodes), which also records
+// ST_INVALID.
+__global__ void __launch_bounds__(256) k_elem_labels(const int32_t *tets, int64_t n_tets, int64_t n_nodes,
+                                                     const int32_t *node_labels,
+                                                     const unsigned long long *masks, const int32_t *row_ids,
+                                                     int32_t *elem, uint32_t *status) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long m = ~0ull;
+    bool bad = false, nonfinite = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int32_t v = tets[4 * t + k];
+      if (v < 0 || v >= n_nodes) {
+        bad = true;
+      } else {
+        nonfinite |= node_labels[v] < 0;
+        m &= masks[v];
+      }
+    }
+    if (bad) atomicOr(status, ST_INVALID);
+    elem[t] = (bad || nonfinite) ? -1 : (m ? row_ids[__ffsll((long long)m) - 1] : 0);
+  }
+}
+
 // The FP32 atan2 of the label kernel applied elementwise (diagnostics: its
 // error is measured against FP64 and CUDA's atan2f).
 __global__ void k_debug_half_angle(const float *y, const float *x, float *out, int64_t n) {
@@ -1178,11 +1208,13 @@ __global__ void __launch_bounds__(256) k_resolve(LabelArgs a, const float *pts, 
     if (!finite3(p.x, p.y, p.z)) {
       lab = -1;
       atomicAdd((unsigned long long *)(a.counters + CNT_NONFINITE), 1ull);
+      if (a.masks_out) a.masks_out[off + a.perm[i]] = 0ull;
       if (a.omega)
         for (int r = 0; r < a.ncomp; ++r) a.omega[(int64_t)r * a.omega_ld + a.perm[i]] = __int_as_float(0x7fc00000);
     } else {
       const unsigned long long m = a.in_mask[i];
       lab = m ? row_ids[__ffsll((long long)m) - 1] : 0;
+      if (a.masks_out) a.masks_out[off + a.perm[i]] = m;
     }
     labels[off + a.perm[i]] = lab;
   }
@@ -1566,6 +1598,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.ncomp = C;
   a.fp32_only = plan.opts.precision == ZEF_FP32_ONLY;
   a.coherence = !(plan.opts.flags & ZEF_NO_TILE_COHERENCE);
+  a.early = plan.omega == nullptr && !plan.full_masks;
+  a.masks_out = plan.masks;
   if (plan.timed) cudaEventRecord(ctx->ev[1], s);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
     // the FP64 kernel's tile is 128 x 2 points (choose_shape guarantees it)
@@ -1592,6 +1626,16 @@ zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns) {
   k_wait_probe<<<1, 64, 0, ctx->stream>>>(ctx->d_status, (unsigned long long)limit_ns);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_wait_probe launch");
+  return ZEF_OK;
+}
+
+zef_status launch_elem_labels(zef_ctx *ctx, const int32_t *tets, int64_t n_tets, int64_t n_nodes,
+                              const int32_t *node_labels, const unsigned long long *masks, int32_t *elem) {
+  if (n_tets > 0)
+    k_elem_labels<<<grid_blocks(ctx, n_tets, 256), 256, 0, ctx->stream>>>(tets, n_tets, n_nodes, node_labels, masks,
+                                                                          ctx->d_row_ids, elem, ctx->d_status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_elem_labels launch");
   return ZEF_OK;
 }
 

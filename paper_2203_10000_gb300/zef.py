@@ -102,6 +102,9 @@ _lib.zef_compartment_priority.restype = ctypes.c_int
 _lib.zef_label_points.argtypes = [_P, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                   ctypes.POINTER(LabelStats)]
 _lib.zef_label_points.restype = ctypes.c_int
+_lib.zef_label_elements.argtypes = [_P, _P, _I64, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
+                                    ctypes.POINTER(LabelStats)]
+_lib.zef_label_elements.restype = ctypes.c_int
 _lib.zef_label_points_noalloc.argtypes = [_P, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                           ctypes.POINTER(LabelStats)]
 _lib.zef_label_points_noalloc.restype = ctypes.c_int
@@ -291,6 +294,38 @@ class Context:
         self._check(_lib.zef_label_points(self._h, pp, n, lp, op, ctypes.byref(o),
                                           ctypes.byref(st) if stats else None))
         return labels, omega, (st.as_dict() if stats else None)
+
+    def label_elements(self, nodes, tets, elem_labels=None, node_labels=None,
+                       opts: LabelOpts | None = None, want_node_labels: bool = False,
+                       stats: bool = True):
+        """Element labels by the four-nodes rule with the priority order.
+        nodes [N][3] float32, tets [M][4] int32 (numpy or torch, host or
+        CUDA).  Returns (elem_labels, node_labels or None, stats or None)."""
+        pp, pk, cuda = _contig(nodes, np.float32, "float32")
+        tp, tk, tcuda = _contig(tets, np.int32, "int32")
+        n = int(np.prod(pk.shape)) // 3
+        m = int(np.prod(tk.shape)) // 4
+        if elem_labels is None:
+            if tcuda:
+                import torch
+                elem_labels = torch.empty(m, dtype=torch.int32, device=tk.device)
+            else:
+                elem_labels = np.empty(m, dtype=np.int32)
+        if node_labels is None and want_node_labels:
+            if cuda:
+                import torch
+                node_labels = torch.empty(n, dtype=torch.int32, device=pk.device)
+            else:
+                node_labels = np.empty(n, dtype=np.int32)
+        ep = elem_labels.data_ptr() if _is_torch(elem_labels) else elem_labels.ctypes.data
+        npp = None
+        if node_labels is not None:
+            npp = node_labels.data_ptr() if _is_torch(node_labels) else node_labels.ctypes.data
+        st = LabelStats()
+        o = opts if opts is not None else make_opts()
+        self._check(_lib.zef_label_elements(self._h, pp, n, tp, m, ep, npp, ctypes.byref(o),
+                                            ctypes.byref(st) if stats else None))
+        return elem_labels, node_labels, (st.as_dict() if stats else None)
 
     def refine_and_relabel(self, nodes, tets, node_labels, num_nodes: int, num_tets: int,
                            levels: int, labels_valid: bool = False, opts: LabelOpts | None = None):

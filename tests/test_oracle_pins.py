@@ -318,3 +318,66 @@ def test_refine_incremental_labels_equal_full_relabel(oracle_mod):
     full, _ = oracle_mod.label_points(n2, [s], [1])
     assert np.array_equal(lab, full)
     assert per[0]["new_nodes"] > 0
+
+
+# ---------------------------------------------------------------- element labels
+def _box_elements_case():
+    """Three boxes (nested, nested, intersecting) over a 5-tet lattice whose
+    nodes sit on integer + 0.5 coordinates and box faces on integers, so no
+    node is on a face and insideness is exact by coordinates."""
+    boxes = {  # id: (lo, hi, subdivisions)
+        1: ((-4.0, -4.0, -4.0), (4.0, 4.0, 4.0), 2),   # outer
+        2: ((-2.0, -2.0, -2.0), (2.0, 2.0, 3.0), 1),   # inside 1
+        3: ((1.0, -1.0, -1.0), (6.0, 1.0, 2.0), 3),    # crosses 1 and 2
+    }
+    surfaces = [zs.Surface(i, f"box{i}", *zs.box_surface(lo, hi, m))
+                for i, (lo, hi, m) in boxes.items()]
+    nodes, tets = zs.lattice_5tet(11, 1.0, (-5.5, -5.5, -5.5))
+    return boxes, surfaces, nodes, tets
+
+
+def _box_brute_force(boxes, priority, nodes, tets):
+    x = nodes.astype(np.float64)
+    lab = np.zeros(tets.shape[0], dtype=np.int32)
+    done = np.zeros(tets.shape[0], dtype=bool)
+    for cid in priority:
+        lo, hi, _ = boxes[cid]
+        inside_node = np.all((x > lo) & (x < hi), axis=1)
+        hit = ~done & inside_node[tets].all(axis=1)
+        lab[hit] = cid
+        done |= hit
+    return lab
+
+
+@pytest.mark.parametrize("priority", [[3, 2, 1], [2, 3, 1], [1, 2, 3]])
+def test_element_four_node_rule_boxes(oracle_mod, priority):
+    boxes, surfaces, nodes, tets = _box_elements_case()
+    elem, node_lab = oracle_mod.label_elements(nodes, tets, surfaces, priority)
+    want = _box_brute_force(boxes, priority, nodes, tets)
+    assert np.array_equal(elem, want)
+    # straddling tets exist and the rule is not "any node inside"
+    first = node_lab[tets]
+    mixed = (first != first[:, :1]).any(axis=1)
+    assert mixed.sum() > 100
+    assert np.any(elem[mixed] != first[mixed].max(axis=1))
+    # a tet whose nodes share one label needs all four inside that box
+    same = ~mixed & (first[:, 0] > 0)
+    assert np.array_equal(elem[same], first[same, 0])
+
+
+def test_element_rule_nonfinite_node(oracle_mod):
+    boxes, surfaces, nodes, tets = _box_elements_case()
+    nodes = nodes.copy()
+    nodes[0] = np.nan
+    elem, node_lab = oracle_mod.label_elements(nodes, tets, surfaces, [1, 2, 3])
+    has0 = (tets == 0).any(axis=1)
+    assert node_lab[0] == -1 and np.all(elem[has0] == -1) and np.all(elem[~has0] >= 0)
+    with pytest.raises(ValueError):
+        oracle_mod.label_elements(nodes, tets[:4] + 10 ** 6, surfaces, [1, 2, 3])
+
+
+def test_box_surface_winding(oracle_mod):
+    v, t = zs.box_surface((-1.0, -2.0, -3.0), (1.0, 2.0, 3.0), 3)
+    assert t.shape == (12 * 9, 3)
+    om = oracle_mod.solid_angle(np.array([[0.1, 0.2, 0.3], [5.0, 0, 0]]), v, t)
+    assert abs(om[0] - 4 * math.pi) < 1e-12 and abs(om[1]) < 1e-12

@@ -227,6 +227,42 @@ def perturbed_ellipsoid(freq: int, axes, amp: float = 3.0, seed: int = 0,
     return _as_f32_surface(x, tris)
 
 
+def box_surface(lo, hi, m: int = 1):
+    """Closed, outward-oriented triangulation of the axis-aligned box
+    [lo, hi]: every face split into an m x m grid of quads, two triangles
+    each (12 m^2 triangles).  A point strictly inside the box has winding
+    number 1, a point strictly outside 0."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    ids = {}
+    verts = []
+
+    def vid(g):
+        if g not in ids:
+            ids[g] = len(verts)
+            verts.append(lo + (hi - lo) * np.asarray(g, dtype=np.float64) / m)
+        return ids[g]
+
+    tris = []
+    for axis in range(3):
+        u, w = [a for a in range(3) if a != axis]
+        for side in (0, m):
+            outward = np.zeros(3)
+            outward[axis] = 1.0 if side == m else -1.0
+            for i in range(m):
+                for j in range(m):
+                    quad = []
+                    for di, dj in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        g = [0, 0, 0]
+                        g[axis], g[u], g[w] = side, i + di, j + dj
+                        quad.append(vid(tuple(g)))
+                    for t in ((quad[0], quad[1], quad[2]), (quad[0], quad[2], quad[3])):
+                        p = [verts[k] for k in t]
+                        nrm = np.cross(p[1] - p[0], p[2] - p[0])
+                        tris.append(t if nrm @ outward > 0 else (t[0], t[2], t[1]))
+    return np.asarray(verts, dtype=np.float32), np.asarray(tris, dtype=np.int32)
+
+
 def torus(R: float, r: float, m: int, k: int, seed: int = 0, amp: float = 0.0,
           center=(0.0, 0.0, 0.0), axis: int = 2):
     """Genus-1 torus of major radius R, minor radius r, an m x k quad grid
