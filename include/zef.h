@@ -153,6 +153,11 @@ typedef struct zef_level_stats {
     int64_t uncertain_pairs;
 } zef_level_stats;
 
+typedef struct zef_relabel_pass {
+    int64_t evaluated;      /* boundary nodes whose solid angles were re-evaluated */
+    int64_t changed;        /* of those, nodes whose label changed */
+} zef_relabel_pass;
+
 /* Pass as `device` to zef_create for a host-only context: it makes no CUDA
    call; compartments can be registered and validated, while labeling and
    refinement return ZEF_ERR_NOT_READY. */
@@ -261,6 +266,31 @@ zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, int64_t n, i
    device-resident counts.  per_level: nullable, `levels` entries. */
 zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels,
                                   const zef_label_opts *opts, zef_level_stats *per_level);
+
+/* Recursive re-labeling at the tissue boundaries (Sec. 2.1.3 item 2, Fig. 3)
+   after the nodes of a labeled mesh changed (moved, or the surfaces were
+   replaced).  One pass: the tets whose four node labels are not all equal
+   form the boundary; the nodes of those tets that this call has not yet
+   evaluated are re-labeled with the solid-angle method; a changed label can
+   move the boundary.  Passes repeat until one changes no label (the boundary
+   no longer changes) or `max_passes` (1..1024) passes ran.  Each node is
+   evaluated at most once per call (its position does not change during it).
+   The pass loop runs on the device as one CUDA graph with a conditional
+   while-node: no host round trip between passes.
+     nodes        [n_nodes][3] float32
+     tets         [n_tets][4] int32 node indices, 0 <= index < n_nodes
+     node_labels  [n_nodes] int32, in: the current labels, out: repaired
+     opts         as zef_label_points (nullable)
+     per_pass     nullable; max_passes entries (passes not run are zeroed)
+     passes, converged  nullable outs: passes run; 1 when the last pass
+                  changed no label, 0 when the pass limit stopped the loop
+   nodes, tets and node_labels must all be host or all device memory; the
+   call synchronizes.  An index outside [0, n_nodes) stops the loop and
+   returns ZEF_ERR_INVALID_ARG. */
+zef_status zef_relabel_boundary(zef_ctx *ctx, const float *nodes, int64_t n_nodes,
+                                const int32_t *tets, int64_t n_tets, int32_t *node_labels,
+                                int32_t max_passes, const zef_label_opts *opts,
+                                zef_relabel_pass *per_pass, int32_t *passes, int32_t *converged);
 
 /* Wait for the context's stream and report any error a kernel recorded
    (ZEF_ERR_TIMEOUT, ZEF_ERR_CAPACITY). */

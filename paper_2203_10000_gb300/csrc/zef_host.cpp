@@ -233,6 +233,8 @@ void zef_destroy(zef_ctx *ctx) {
   fr(b.labels_tmp); fr(b.pts_tmp); fr(b.omega_tmp); fr(b.tune_pts);
   fr(ctx->el_node_labels); fr(ctx->el_masks); fr(ctx->el_tets); fr(ctx->el_labels);
   for (auto &p : ctx->rf_buf) fr(p);
+  for (auto &p : ctx->rb_buf) fr(p);
+  if (ctx->rb_exec) cudaGraphExecDestroy(ctx->rb_exec);
   if (ctx->rf_exec) cudaGraphExecDestroy(ctx->rf_exec);
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
   for (auto &ev : ctx->ev)
@@ -681,6 +683,36 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
 }  // namespace zef
 
 extern "C" {
+
+zef_status zef_relabel_boundary(zef_ctx *ctx, const float *nodes, int64_t n_nodes, const int32_t *tets,
+                                int64_t n_tets, int32_t *node_labels, int32_t max_passes,
+                                const zef_label_opts *opts, zef_relabel_pass *per_pass, int32_t *passes,
+                                int32_t *converged) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
+  if (max_passes < 1 || max_passes > 1024) return fail(ctx, ZEF_ERR_INVALID_ARG, "max_passes must be in [1, 1024]");
+  if (n_nodes < 0 || n_tets < 0 || (n_nodes > 0 && (!nodes || !node_labels)) || (n_tets > 0 && !tets))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad nodes/tets/labels arguments");
+  if (n_nodes > ((int64_t)1 << 31) - 1 || n_tets > ((int64_t)1 << 31) - 1)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "too many nodes or tets (max 2^31-1)");
+  if (n_tets > 0 && n_nodes == 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "tets without nodes");
+  zef_label_opts o;
+  if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
+  fill_default_opts(&o);
+  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
+  if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
+  if (per_pass) std::memset(per_pass, 0, sizeof(zef_relabel_pass) * (size_t)max_passes);
+  if (passes) *passes = 0;
+  if (converged) *converged = 0;
+  DeviceGuard g(ctx->device);
+  zef_status st = ensure_uploaded(ctx);
+  if (st) return st;
+  return relabel_run(ctx, nodes, n_nodes, tets, n_tets, node_labels, max_passes, o, per_pass, passes, converged);
+}
 
 zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_label_opts *opts,
                                   zef_level_stats *per_level) {

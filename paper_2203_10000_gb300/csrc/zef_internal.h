@@ -164,6 +164,12 @@ struct zef_ctx {
   int32_t *el_labels = nullptr;
   int64_t el_cap_nodes = 0, el_cap_masks = 0, el_cap_tets = 0, el_cap_labels = 0;
 
+  // recursive re-labeling scratch and its cached graph
+  void *rb_buf[9] = {};
+  size_t rb_cap[9] = {};
+  cudaGraphExec_t rb_exec = nullptr;
+  uint64_t rb_key = 0;
+
   // refinement scratch
   void *rf_buf[8] = {};
   size_t rf_cap[8] = {};
@@ -203,6 +209,9 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap);
 zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan);
 zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off);
 zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns);
+zef_status relabel_run(zef_ctx *ctx, const float *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                       int32_t *node_labels, int32_t max_passes, const zef_label_opts &opts,
+                       zef_relabel_pass *per_pass, int32_t *passes, int32_t *converged);
 zef_status launch_elem_labels(zef_ctx *ctx, const int32_t *tets, int64_t n_tets, int64_t n_nodes,
                               const int32_t *node_labels, const unsigned long long *masks, int32_t *elem);
 zef_status launch_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);

@@ -105,6 +105,13 @@ _lib.zef_label_points.restype = ctypes.c_int
 _lib.zef_label_elements.argtypes = [_P, _P, _I64, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                     ctypes.POINTER(LabelStats)]
 _lib.zef_label_elements.restype = ctypes.c_int
+class RelabelPass(ctypes.Structure):
+    _fields_ = [("evaluated", ctypes.c_int64), ("changed", ctypes.c_int64)]
+
+
+_lib.zef_relabel_boundary.argtypes = [_P, _P, _I64, _P, _I64, _P, _I32, ctypes.POINTER(LabelOpts),
+                                      ctypes.POINTER(RelabelPass), ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
+_lib.zef_relabel_boundary.restype = ctypes.c_int
 _lib.zef_label_points_noalloc.argtypes = [_P, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                           ctypes.POINTER(LabelStats)]
 _lib.zef_label_points_noalloc.restype = ctypes.c_int
@@ -326,6 +333,30 @@ class Context:
         self._check(_lib.zef_label_elements(self._h, pp, n, tp, m, ep, npp, ctypes.byref(o),
                                             ctypes.byref(st) if stats else None))
         return elem_labels, node_labels, (st.as_dict() if stats else None)
+
+    def relabel_boundary(self, nodes, tets, node_labels, max_passes: int = 64,
+                         opts: LabelOpts | None = None):
+        """Recursive re-labeling at the tissue boundaries; node_labels (int32,
+        same residency as nodes and tets) is repaired in place.  Returns
+        (per_pass [(evaluated, changed), ...], converged)."""
+        pp, pk, _ = _contig(nodes, np.float32, "float32")
+        tp, tk, _ = _contig(tets, np.int32, "int32")
+        if _is_torch(node_labels):
+            if node_labels.dtype.itemsize != 4 or not node_labels.is_contiguous():
+                raise ValueError("node_labels must be a contiguous int32 tensor")
+            lp = node_labels.data_ptr()
+        else:
+            if node_labels.dtype != np.int32 or not node_labels.flags.c_contiguous:
+                raise ValueError("node_labels must be a contiguous int32 array")
+            lp = node_labels.ctypes.data
+        n = int(np.prod(pk.shape)) // 3
+        m = int(np.prod(tk.shape)) // 4
+        per = (RelabelPass * max(1, int(max_passes)))()
+        npass, conv = _I32(0), _I32(0)
+        o = opts if opts is not None else make_opts()
+        self._check(_lib.zef_relabel_boundary(self._h, pp, n, tp, m, lp, int(max_passes), ctypes.byref(o),
+                                              per, ctypes.byref(npass), ctypes.byref(conv)))
+        return [(int(per[i].evaluated), int(per[i].changed)) for i in range(npass.value)], bool(conv.value)
 
     def refine_and_relabel(self, nodes, tets, node_labels, num_nodes: int, num_tets: int,
                            levels: int, labels_valid: bool = False, opts: LabelOpts | None = None):

@@ -381,3 +381,56 @@ def test_box_surface_winding(oracle_mod):
     assert t.shape == (12 * 9, 3)
     om = oracle_mod.solid_angle(np.array([[0.1, 0.2, 0.3], [5.0, 0, 0]]), v, t)
     assert abs(om[0] - 4 * math.pi) < 1e-12 and abs(om[1]) < 1e-12
+
+
+# ---------------------------------------------------------------- recursive re-labeling
+def _box_labels(nodes, lo, hi, cid):
+    x = nodes.astype(np.float64)
+    return np.where(np.all((x > lo) & (x < hi), axis=1), cid, 0).astype(np.int32)
+
+
+@pytest.mark.parametrize("grow", [True, False])
+def test_relabel_boundary_moving_box(oracle_mod, grow):
+    """Labels of box B0 repaired against box B1 (faces 2-3 lattice steps
+    apart): the boundary front reaches every node whose label changed, so the
+    result equals the exact coordinate labels of B1, after several passes."""
+    from oracle import relabel
+    nodes, tets = zs.lattice_5tet(14, 1.0, (-7.5, -7.5, -7.5))
+    small = ((-3.0, -2.0, -4.0), (3.0, 2.0, 1.0))
+    big = ((-5.0, -5.0, -6.0), (6.0, 4.0, 4.0))
+    b0, b1 = (small, big) if grow else (big, small)
+    lab0 = _box_labels(nodes, *b0, 1)
+    surf = zs.Surface(1, "box", *zs.box_surface(*b1, 2))
+    lab, per, conv = relabel.relabel_boundary(nodes, tets, lab0, [surf], [1], 20)
+    want = _box_labels(nodes, *b1, 1)
+    assert conv
+    assert np.array_equal(lab, want)
+    assert len(per) >= 3 and per[-1][1] == 0
+    assert sum(c for _, c in per) == int((lab0 != want).sum())
+    # each node is evaluated at most once
+    assert sum(e for e, _ in per) <= nodes.shape[0]
+
+
+def test_relabel_boundary_fixed_point_and_pass_limit(oracle_mod):
+    from oracle import relabel
+    nodes, tets = zs.lattice_5tet(12, 1.0, (-6.5, -6.5, -6.5))
+    box = ((-3.0, -3.0, -3.0), (3.0, 2.0, 4.0))
+    surf = zs.Surface(1, "box", *zs.box_surface(*box, 1))
+    exact = _box_labels(nodes, *box, 1)
+    lab, per, conv = relabel.relabel_boundary(nodes, tets, exact, [surf], [1], 10)
+    assert conv and len(per) == 1 and per[0][0] > 0 and per[0][1] == 0
+    assert np.array_equal(lab, exact)
+    # a pass limit of one on a moved surface stops before convergence
+    lab0 = _box_labels(nodes, (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), 1)
+    lab, per, conv = relabel.relabel_boundary(nodes, tets, lab0, [surf], [1], 1)
+    assert not conv and len(per) == 1 and per[0][1] > 0
+
+
+def test_relabel_boundary_sphere_equals_full_relabel(oracle_mod):
+    from oracle import relabel
+    nodes, tets = zs.lattice_5tet(16, 0.5, (-4.0, -4.0, -4.0))
+    s0, s1 = _sphere(2.0, 6, 1), _sphere(3.2, 6, 1)
+    lab0, _ = oracle_mod.label_points(nodes, [s0], [1])
+    lab, per, conv = relabel.relabel_boundary(nodes, tets, lab0, [s1], [1], 20)
+    full, _ = oracle_mod.label_points(nodes, [s1], [1])
+    assert conv and np.array_equal(lab, full) and len(per) >= 3
