@@ -215,6 +215,37 @@ def refine_measure(zef, torch, dev):
         torch.cuda.synchronize(dev)
         out = {"workload": w.name, "initial_nodes": n0, "initial_tets": m0, "levels": per,
                "ms_total_incl_initial_labeling": e0.elapsed_time(e1), "final_nodes": n1, "final_tets": m1}
+    # element labels (four-nodes rule) of the refined mesh, then the recursive
+    # boundary re-labeling after every node moved by up to 0.2 mm (seeded)
+    rn, rt, rl = nodes[:n1], tets[:m1], labels[:n1].clone()
+    elem = torch.empty(m1, dtype=torch.int32, device=dev)
+    for rep in range(2):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, est = ctx.label_elements(rn, rt, elem_labels=elem, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    out["elements"] = {"nodes": n1, "tets": m1, "ms": e0.elapsed_time(e1),
+                       "node_pairs_nominal": n1 * w.total_tris,
+                       "note": "node inside bits of every compartment (no priority early exit), AND per tet"}
+    g = torch.Generator(device=dev)
+    g.manual_seed(41)
+    moved = (rn + (torch.rand(rn.shape, generator=g, device=dev) - 0.5) * 0.4).contiguous()
+    for rep in range(2):
+        lab = rl.clone()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        passes, conv = ctx.relabel_boundary(moved, rt, lab, 64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    out["relabel_boundary"] = {"nodes": n1, "tets": m1, "displacement_mm": 0.2, "ms": e0.elapsed_time(e1),
+                               "passes": len(passes), "converged": conv,
+                               "evaluated": sum(e for e, _ in passes), "changed": sum(c for _, c in passes),
+                               "per_pass": passes}
     ctx.close()
     return out
 
@@ -351,6 +382,14 @@ def run_ours(args):
         line["fp64_plain"] = {"points": nsub, "ms_fp32_rescue": s32["ms_total"], "ms_fp64_plain": s64["ms_total"],
                               "speedup": s64["ms_total"] / s32["ms_total"], "labels_equal": same,
                               "fp64_pairs_per_s": s64["pairs_evaluated"] / (s64["ms_total"] * 1e-3)}
+
+    # measured FMA throughput of this GPU (cross-check of the FP32 peak; the
+    # FP64 rate sets the cost of the re-evaluation and of the plain FP64 kernel)
+    if rank == 0:
+        f32 = ctx.fma_rate(fp64=False)
+        f64 = ctx.fma_rate(fp64=True)
+        line["fma_microbench"] = {"fp32_tflops": f32, "fp64_tflops": f64,
+                                  "fp32_frac_of_peak": f32 / line["roofline"]["peak"]}
 
     # end to end through the C ABI with host buffers (copies inside the region)
     if not args.no_e2e:

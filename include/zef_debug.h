@@ -37,6 +37,14 @@ zef_status zef_debug_strip_stats(const zef_ctx *ctx, int32_t index, int64_t *ent
    host-only context. */
 zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);
 
+/* Measured fused multiply-add throughput of the context's device in TFLOP/s
+   (FMA = 2 flops): float (fp64 = 0) or double (fp64 != 0), 8 independent
+   chains per thread on SMs x 8 blocks of 256 threads, best of three timed
+   launches after a warm-up.  Synchronizes.  Used to check the FP32 peak the
+   label kernel is compared with and to measure the FP64 rate that sets the
+   cost of the FP64 re-evaluation and of the plain FP64 kernel. */
+zef_status zef_debug_fma_rate(zef_ctx *ctx, int32_t fp64, double *tflops);
+
 /* Failure-detection probe: launches one block whose threads wait on a device
    barrier that is never signalled, with the given limit in nanoseconds
    (0 < limit_ns <= 2e9).  The wait expires, the kernel records the timeout

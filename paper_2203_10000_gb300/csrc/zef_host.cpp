@@ -888,6 +888,14 @@ extern "C" zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const f
   return zef_synchronize(ctx);
 }
 
+extern "C" zef_status zef_debug_fma_rate(zef_ctx *ctx, int32_t fp64, double *tflops) {
+  if (!ctx || !tflops) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context");
+  DeviceGuard g(ctx->device);
+  return debug_fma_rate(ctx, fp64 != 0, tflops);
+}
+
 extern "C" zef_status zef_debug_wait_probe(zef_ctx *ctx, int64_t limit_ns) {
   if (!ctx) return ZEF_ERR_INVALID_ARG;
   ctx->err.clear();

@@ -214,6 +214,7 @@ zef_status relabel_run(zef_ctx *ctx, const float *nodes, int64_t n_nodes, const 
                        zef_relabel_pass *per_pass, int32_t *passes, int32_t *converged);
 zef_status launch_elem_labels(zef_ctx *ctx, const int32_t *tets, int64_t n_tets, int64_t n_nodes,
                               const int32_t *node_labels, const unsigned long long *masks, int32_t *elem);
+zef_status debug_fma_rate(zef_ctx *ctx, int fp64, double *tflops);
 zef_status launch_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);
 zef_status upload_dop_directions(zef_ctx *ctx);
 zef_status scan_exclusive(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, int64_t len_mul,

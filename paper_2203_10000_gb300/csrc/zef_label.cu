@@ -965,6 +965,28 @@ __global__ void __launch_bounds__(256) k_elem_labels(const int32_t *tets, int64_
   }
 }
 
+// FMA throughput microbenchmark: kChains independent dependent-FMA chains
+// per thread (enough to cover the pipe latency), `iters` rounds; the result
+// is stored only when it equals an impossible value, so nothing is dead code.
+template <class T>
+__global__ void __launch_bounds__(256) k_debug_fma(int iters, T *sink) {
+  constexpr int kChains = 8;
+  T x[kChains];
+  const T a = (T)0.999999, b = (T)1e-7;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = (T)(threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == (T)-12345.678) sink[0] = s;
+}
+
 // The FP32 atan2 of the label kernel applied elementwise (diagnostics: its
 // error is measured against FP64 and CUDA's atan2f).
 __global__ void k_debug_half_angle(const float *y, const float *x, float *out, int64_t n) {
@@ -1636,6 +1658,36 @@ zef_status launch_elem_labels(zef_ctx *ctx, const int32_t *tets, int64_t n_tets,
                                                                           ctx->d_row_ids, elem, ctx->d_status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_elem_labels launch");
+  return ZEF_OK;
+}
+
+zef_status debug_fma_rate(zef_ctx *ctx, int fp64, double *tflops) {
+  const int blocks = ctx->num_sms * 8, threads = 256, iters = fp64 ? 256 : 4096;
+  void *sink = nullptr;
+  cudaError_t e = cudaMalloc(&sink, 16);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(sink)");
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up
+    cudaEventRecord(t0, ctx->stream);
+    if (fp64) k_debug_fma<double><<<blocks, threads, 0, ctx->stream>>>(iters, (double *)sink);
+    else k_debug_fma<float><<<blocks, threads, 0, ctx->stream>>>(iters, (float *)sink);
+    cudaEventRecord(t1, ctx->stream);
+    e = cudaEventSynchronize(t1);
+    if (e != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFree(sink);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "k_debug_fma");
+  const double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
+  *tflops = flops / (best * 1e-3) / 1e12;
   return ZEF_OK;
 }
 

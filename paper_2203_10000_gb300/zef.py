@@ -129,6 +129,8 @@ _lib.zef_debug_strip_entries.argtypes = [_P, _I32, _P, _I64, ctypes.POINTER(_I64
 _lib.zef_debug_strip_entries.restype = ctypes.c_int
 _lib.zef_debug_wait_probe.argtypes = [_P, _I64]
 _lib.zef_debug_wait_probe.restype = ctypes.c_int
+_lib.zef_debug_fma_rate.argtypes = [_P, _I32, ctypes.POINTER(ctypes.c_double)]
+_lib.zef_debug_fma_rate.restype = ctypes.c_int
 _lib.zef_debug_half_angle.argtypes = [_P, _P, _P, _P, _I64]
 _lib.zef_debug_half_angle.restype = ctypes.c_int
 
@@ -179,6 +181,9 @@ def make_opts(margin=0.0, winding_tol=0.0, precision=ZEF_FP32_RESCUE, block_thre
     return o
 
 
+_CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
+
+
 class Context:
     """One libzef context on one CUDA device (zef_create / zef_destroy)."""
 
@@ -189,6 +194,12 @@ class Context:
                 import torch
                 if torch.cuda.is_available():
                     stream = torch.cuda.current_stream(device).cuda_stream
+                    # handle 0 is torch's legacy default stream: pass
+                    # cudaStreamLegacy so the library's work stays ordered
+                    # with torch's (a NULL stream would make the context
+                    # create its own non-blocking stream)
+                    if stream == 0:
+                        stream = _CUDA_STREAM_LEGACY
             except Exception:  # pragma: no cover
                 stream = None
         st = _lib.zef_create(ctypes.byref(self._h), int(device), _P(stream) if stream else None)
@@ -256,6 +267,12 @@ class Context:
         """Run the bounded-wait probe; returns the status code (expected
         ZEF_ERR_TIMEOUT) without raising."""
         return int(_lib.zef_debug_wait_probe(self._h, int(limit_ns)))
+
+    def fma_rate(self, fp64: bool = False) -> float:
+        """Measured FMA throughput of the device in TFLOP/s (diagnostics)."""
+        v = ctypes.c_double(0.0)
+        self._check(_lib.zef_debug_fma_rate(self._h, 1 if fp64 else 0, ctypes.byref(v)))
+        return float(v.value)
 
     def half_angle(self, y, x, out):
         """The FP32 label kernel's atan2(y, x) applied elementwise to device

@@ -105,6 +105,18 @@ def test_fp32_atan2_within_atan2f_bound(zef):
     assert torch.isnan(ctx.half_angle(z, z.clone(), torch.empty_like(z))).all()
 
 
+def test_fma_microbenchmark_is_sane(zef):
+    """Measured FMA rates: FP32 within reach of 152 SMs x 128 lanes x 2 flop
+    at up to 2.07 GHz (80.5 TFLOP/s), FP64 far below FP32 on this part."""
+    ctx = zef.Context(0)
+    f32, f64 = ctx.fma_rate(False), ctx.fma_rate(True)
+    print(f"FMA TFLOP/s: fp32 {f32:.2f}, fp64 {f64:.3f}")
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    assert 0.3 * nominal < f32 < 1.05 * nominal
+    assert 0 < f64 < 0.5 * f32
+
+
 # ------------------------------------------------------------------ small case
 def test_config0_parity(zef, oracle_mod):
     w = zs.config0()
