@@ -367,70 +367,34 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &e, float b, float f
   e = e + f + err;
 }
 
-// Representative evaluation of a warp tile for compartment cp: one pass over
-// the compartment's triangles (lane l takes triangles l, l + 32, ...) that both
-// tests every triangle's box against the tile's box wb and sums the plain
-// FP32 Van Oosterom-Strackee half angles of one representative point (the
-// tile's first finite point).  Returns 1 with the winding number in *k when no
-// triangle box meets wb and the representative's Omega is certain (the same
-// tests as classify_store, with the conditioning bound scaled by r1 r2 r3);
-// 0 when the tile has to be evaluated point by point.
-template <int P>
-__device__ __forceinline__ int coherent_tile(const LabelArgs &a, const DevComp *cp, const float *wb,
-                                             const PState (&st)[P], uint32_t usable, int lane, int *k) {
-  float rx = 0.f, ry = 0.f, rz = 0.f;
-  bool have = false;
-#pragma unroll
-  for (int q = 0; q < P; ++q) {
-    const unsigned m = __ballot_sync(0xffffffffu, (usable >> q) & 1u);
-    if (!have && m) {
-      const int src = __ffs(m) - 1;
-      rx = __shfl_sync(0xffffffffu, st[q].px, src);
-      ry = __shfl_sync(0xffffffffu, st[q].py, src);
-      rz = __shfl_sync(0xffffffffu, st[q].pz, src);
-      have = true;
-    }
-  }
-  if (!have) return 0;
-  const int tri_cnt = __ldg(&cp->tri_cnt);
-  const float4 *T = a.tris + (int64_t)__ldg(&cp->tri_off) * 3;
-  const float lx = wb[0], ly = wb[1], lz = wb[2], hx = wb[3], hy = wb[4], hz = wb[5];
-  float sum = 0.f, comp = 0.f, bad = __int_as_float(0x7f800000);
-  for (int t0 = 0; t0 < tri_cnt; t0 += 32) {
-    const int t = t0 + lane;
-    bool ov = false;
-    float term = 0.f;
-    if (t < tri_cnt) {
-      const float4 A = T[3 * t], B = T[3 * t + 1], C = T[3 * t + 2];
-      ov = !(fmaxf(A.x, fmaxf(B.x, C.x)) < lx || fminf(A.x, fminf(B.x, C.x)) > hx ||
-             fmaxf(A.y, fmaxf(B.y, C.y)) < ly || fminf(A.y, fminf(B.y, C.y)) > hy ||
-             fmaxf(A.z, fmaxf(B.z, C.z)) < lz || fminf(A.z, fminf(B.z, C.z)) > hz);
-      const float x1 = A.x - rx, y1 = A.y - ry, z1 = A.z - rz;
-      const float x2 = B.x - rx, y2 = B.y - ry, z2 = B.z - rz;
-      const float x3 = C.x - rx, y3 = C.y - ry, z3 = C.z - rz;
-      const float q1 = fmaf(x1, x1, fmaf(y1, y1, z1 * z1));
-      const float q2 = fmaf(x2, x2, fmaf(y2, y2, z2 * z2));
-      const float q3 = fmaf(x3, x3, fmaf(y3, y3, z3 * z3));
-      const float r1 = q1 * rsqrtf(q1), r2 = q2 * rsqrtf(q2), r3 = q3 * rsqrtf(q3);
-      const float cx = fmaf(y2, z3, -z2 * y3), cy = fmaf(z2, x3, -x2 * z3), cz = fmaf(x2, y3, -y2 * x3);
-      const float N = fmaf(x1, cx, fmaf(y1, cy, z1 * cz));
-      const float d12 = fmaf(x1, x2, fmaf(y1, y2, z1 * z2));
-      const float d13 = fmaf(x1, x3, fmaf(y1, y3, z1 * z3));
-      const float d23 = fmaf(x2, x3, fmaf(y2, y3, z2 * z3));
-      const float r123 = r1 * r2 * r3;
-      const float D = fmaf(d12, r3, fmaf(d13, r2, fmaf(d23, r1, r123)));
-      term = half_angle(N, D);
-      bad = fminf(bad, fmaf(-kKappa, r123, fmaxf(fabsf(N), D)));
-    }
-    if (__any_sync(0xffffffffu, ov)) return 0;
-    const float y = term - comp;
-    const float tt = sum + y;
-    comp = (tt - sum) - y;
-    sum = tt;
-  }
-  // butterfly reduction of the compensated partials (every lane ends with the
-  // same value: IEEE addition is commutative)
-  float h = sum, he = -comp;
+// Plain FP32 Van Oosterom-Strackee half angle of triangle (A, B, C) seen
+// from r; bad = min(bad, max(|N|, D) - kappa r1 r2 r3).
+__device__ __forceinline__ void vos_term(float rx, float ry, float rz, float4 A, float4 B, float4 C, float &term,
+                                         float &bad) {
+  const float x1 = A.x - rx, y1 = A.y - ry, z1 = A.z - rz;
+  const float x2 = B.x - rx, y2 = B.y - ry, z2 = B.z - rz;
+  const float x3 = C.x - rx, y3 = C.y - ry, z3 = C.z - rz;
+  const float q1 = fmaf(x1, x1, fmaf(y1, y1, z1 * z1));
+  const float q2 = fmaf(x2, x2, fmaf(y2, y2, z2 * z2));
+  const float q3 = fmaf(x3, x3, fmaf(y3, y3, z3 * z3));
+  const float r1 = q1 * rsqrtf(q1), r2 = q2 * rsqrtf(q2), r3 = q3 * rsqrtf(q3);
+  const float cx = fmaf(y2, z3, -z2 * y3), cy = fmaf(z2, x3, -x2 * z3), cz = fmaf(x2, y3, -y2 * x3);
+  const float N = fmaf(x1, cx, fmaf(y1, cy, z1 * cz));
+  const float d12 = fmaf(x1, x2, fmaf(y1, y2, z1 * z2));
+  const float d13 = fmaf(x1, x3, fmaf(y1, y3, z1 * z3));
+  const float d23 = fmaf(x2, x3, fmaf(y2, y3, z2 * z3));
+  const float r123 = r1 * r2 * r3;
+  const float D = fmaf(d12, r3, fmaf(d13, r2, fmaf(d23, r1, r123)));
+  term = half_angle(N, D);
+  bad = fminf(bad, fmaf(-kKappa, r123, fmaxf(fabsf(N), D)));
+}
+
+// Certainty of a representative's FP32 sum after the lanes' compensated
+// partials (h, he) and conditioning minima are combined by a butterfly
+// (every lane ends with the same value: IEEE addition is commutative).
+// True with the winding number in *k when certain (the tests of
+// classify_store).
+__device__ __forceinline__ bool rep_certain(const LabelArgs &a, float h, float he, float bad, int *k) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const float ph = __shfl_xor_sync(0xffffffffu, h, o);
@@ -443,9 +407,117 @@ __device__ __forceinline__ int coherent_tile(const LabelArgs &a, const DevComp *
   const float kf = rintf(h * kInvTwoPi);
   const float dist = 2.f * fabsf(fmaf(-kTwoPi, kf, h));
   const bool unc = !isfinite(om) || !(bad > 0.f) || !(dist <= a.winding_tol) || !(fabsf(om - kTwoPi) >= a.margin);
-  if (unc) return 0;
+  if (unc) return false;
   *k = (int)kf;
-  return 1;
+  return true;
+}
+
+// One pass over compartment cp's triangles (lane l takes triangles l, l + 32,
+// ...) summing the plain FP32 Van Oosterom-Strackee half angles of the point
+// (rx, ry, rz).  With a box wb (non-null) the pass also tests every triangle's
+// box against wb and stops at the first chunk of 32 triangles in which one
+// meets it, returning that chunk's first index in *t_hit (otherwise -1).
+// Returns true with the winding number in *k when the pass completed and the
+// point's Omega is certain (the tests of classify_store, with the conditioning
+// bound scaled by r1 r2 r3).
+__device__ __forceinline__ bool rep_pass(const LabelArgs &a, const DevComp *cp, const float *wb, float rx,
+                                         float ry, float rz, int lane, int *k, int *t_hit) {
+  const int tri_cnt = __ldg(&cp->tri_cnt);
+  const float4 *T = a.tris + (int64_t)__ldg(&cp->tri_off) * 3;
+  float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+  if (wb) {
+    lx = wb[0]; ly = wb[1]; lz = wb[2]; hx = wb[3]; hy = wb[4]; hz = wb[5];
+  }
+  *t_hit = -1;
+  float sum = 0.f, comp = 0.f, bad = __int_as_float(0x7f800000);
+  for (int t0 = 0; t0 < tri_cnt; t0 += 32) {
+    const int t = t0 + lane;
+    bool ov = false;
+    float term = 0.f;
+    if (t < tri_cnt) {
+      const float4 A = T[3 * t], B = T[3 * t + 1], C = T[3 * t + 2];
+      if (wb)
+        ov = !(fmaxf(A.x, fmaxf(B.x, C.x)) < lx || fminf(A.x, fminf(B.x, C.x)) > hx ||
+               fmaxf(A.y, fmaxf(B.y, C.y)) < ly || fminf(A.y, fminf(B.y, C.y)) > hy ||
+               fmaxf(A.z, fmaxf(B.z, C.z)) < lz || fminf(A.z, fminf(B.z, C.z)) > hz);
+      vos_term(rx, ry, rz, A, B, C, term, bad);
+    }
+    if (wb && __any_sync(0xffffffffu, ov)) {
+      *t_hit = t0;
+      return false;
+    }
+    const float y = term - comp;
+    const float tt = sum + y;
+    comp = (tt - sum) - y;
+    sum = tt;
+  }
+  return rep_certain(a, sum, -comp, bad, k);
+}
+
+// Representatives of several groups (coordinates rp[g], groups in u) in one
+// pass over cp's triangles: each triangle is loaded once for all of them.
+// Returns the groups whose representative is certain; their winding numbers
+// go to k[g].
+template <int NG>
+__device__ __forceinline__ uint32_t group_reps(const LabelArgs &a, const DevComp *cp, uint32_t u,
+                                               const float (*rp)[3], int lane, int (&k)[NG]) {
+  const int tri_cnt = __ldg(&cp->tri_cnt);
+  const float4 *T = a.tris + (int64_t)__ldg(&cp->tri_off) * 3;
+  float sum[NG], comp[NG], bad[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    sum[g] = comp[g] = 0.f;
+    bad[g] = __int_as_float(0x7f800000);
+  }
+  for (int t = lane; t < tri_cnt; t += 32) {
+    const float4 A = T[3 * t], B = T[3 * t + 1], C = T[3 * t + 2];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      if ((u >> g) & 1u) {
+        float term;
+        vos_term(rp[g][0], rp[g][1], rp[g][2], A, B, C, term, bad[g]);
+        const float y = term - comp[g];
+        const float tt = sum[g] + y;
+        comp[g] = (tt - sum[g]) - y;
+        sum[g] = tt;
+      }
+  }
+  uint32_t certain = 0;
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+    if (((u >> g) & 1u) && rep_certain(a, sum[g], -comp[g], bad[g], &k[g])) certain |= 1u << g;
+  return certain;
+}
+
+// Groups of a tile (16 consecutive points each, boxes gb[g]) whose box meets
+// the box of some triangle of cp, from triangle t_begin on (the earlier ones
+// miss the whole tile box wb).  Only the groups in `need` are tested; the
+// pass ends once all of them are hit.
+template <int NG>
+__device__ __forceinline__ uint32_t touched_groups(const LabelArgs &a, const DevComp *cp, const float *wb,
+                                                   const float (*gb)[6], uint32_t need, int t_begin, int lane) {
+  const int tri_cnt = __ldg(&cp->tri_cnt);
+  const float4 *T = a.tris + (int64_t)__ldg(&cp->tri_off) * 3;
+  uint32_t hit = 0;
+  for (int t0 = t_begin; t0 < tri_cnt; t0 += 32) {
+    const int t = t0 + lane;
+    if (t < tri_cnt) {
+      const float4 A = T[3 * t], B = T[3 * t + 1], C = T[3 * t + 2];
+      const float ux = fmaxf(A.x, fmaxf(B.x, C.x)), lx = fminf(A.x, fminf(B.x, C.x));
+      const float uy = fmaxf(A.y, fmaxf(B.y, C.y)), ly = fminf(A.y, fminf(B.y, C.y));
+      const float uz = fmaxf(A.z, fmaxf(B.z, C.z)), lz = fminf(A.z, fminf(B.z, C.z));
+      if (!(ux < wb[0] || lx > wb[3] || uy < wb[1] || ly > wb[4] || uz < wb[2] || lz > wb[5])) {
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (((need >> g) & 1u) && !(ux < gb[g][0] || lx > gb[g][3] || uy < gb[g][1] || ly > gb[g][4] ||
+                                      uz < gb[g][2] || lz > gb[g][5]))
+            hit |= 1u << g;
+      }
+    }
+    hit = __reduce_or_sync(0xffffffffu, hit);
+    if (hit == need) break;
+  }
+  return hit;
 }
 
 // ------------------------------------------------------------------ FP32 persistent kernel
@@ -457,12 +529,143 @@ __device__ __forceinline__ int coherent_tile(const LabelArgs &a, const DevComp *
 // There is no block-wide barrier on the hot path, so a warp that finishes a
 // tile early moves straight on to the next one.  Without Omega output a point
 // that is certainly inside a compartment needs no lower-priority one (Sec. 2.1:
-// the first compartment of the hierarchy wins), and the warp leaves the tile
-// once all its points are decided.
+// the first compartment of the hierarchy wins): groups whose points are all
+// decided skip the later compartments, and the warp leaves the tile once all
+// its points are decided.
 // V = 0: one atan2 per group of four strip steps, on the product of their
 //        (D + i N) factors with wrap counting (the default);
 // V = 1: one atan2 per triangle.
 constexpr int kWChunk = 128;  // strip entries per warp buffer (4 KB)
+
+// Streams compartment cp's strip entries through the warp's double buffer and
+// accumulates the FP32 sums of the NA point slots of every lane.  Returns
+// false when a bounded wait expired.
+template <int NA, int V>
+__device__ __forceinline__ bool stream_sums(const LabelArgs &a, const DevComp *cp, Entry *wbuf, uint64_t *bar,
+                                            uint32_t &ph0, uint32_t &ph1, int lane, PState (&st)[NA]) {
+  const int entry_cnt = __ldg(&cp->entry_cnt);
+  const Entry *gsrc = a.entries + __ldg(&cp->entry_off);
+  const int nchunks = (entry_cnt + kWChunk - 1) / kWChunk;
+  if (lane == 0) {
+    tma_load_1d(wbuf, gsrc, min(kWChunk, entry_cnt) * (uint32_t)sizeof(Entry), &bar[0]);
+    if (nchunks > 1)
+      tma_load_1d(wbuf + kWChunk, gsrc + kWChunk, min(kWChunk, entry_cnt - kWChunk) * (uint32_t)sizeof(Entry),
+                  &bar[1]);
+  }
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    st[q].grp = st[q].sum = st[q].comp = 0.f;
+    st[q].bad = __int_as_float(0x7f800000);
+    st[q].kp = st[q].kn = 0u;
+  }
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int b = ch & 1;
+    const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
+    if (__any_sync(0xffffffffu, !ok)) return false;
+    if (b) ph1 ^= 1; else ph0 ^= 1;
+    const Entry *E = wbuf + b * kWChunk;
+    const int cnt = min(kWChunk, entry_cnt - ch * kWChunk);
+    if (ch == 0) {
+      const float4 v0 = E[0].v;
+#pragma unroll
+      for (int q = 0; q < NA; ++q) window_init(st[q], v0);
+    }
+    for (int g = 0; g < cnt; g += kGroup) {
+      if constexpr (V == 0) {
+#pragma unroll 1
+        for (int j = 0; j < kGroup; j += 4) {
+          const Entry *e = E + g + j;
+          const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
+          const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
+#pragma unroll
+          for (int q = 0; q < NA; ++q) {
+            float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+            geom_step(st[q], v0, n0, N0, D0);
+            geom_step(st[q], v1, n1, N1, D1);
+            cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
+            geom_step(st[q], v2, n2, N0, D0);
+            geom_step(st[q], v3, n3, N1, D1);
+            cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
+            cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
+            st[q].grp += half_angle(I, R);
+          }
+        }
+      } else {
+#pragma unroll 4
+        for (int j = 0; j < kGroup; ++j) {
+          const float4 Vv = E[g + j].v;
+          const float4 Nn = E[g + j].n;
+#pragma unroll
+          for (int q = 0; q < NA; ++q) vos_step(st[q], Vv, Nn);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NA; ++q) kahan_flush(st[q]);
+    }
+    __syncwarp();  // every lane is done with buffer b before it is refilled
+    if (lane == 0 && ch + 2 < nchunks)
+      tma_load_1d(wbuf + b * kWChunk, gsrc + (int64_t)(ch + 2) * kWChunk,
+                  min(kWChunk, entry_cnt - (ch + 2) * kWChunk) * (uint32_t)sizeof(Entry), &bar[b]);
+  }
+  return true;
+}
+
+// Point-by-point evaluation of the groups in `act` (m of them), packed two
+// per slot of 32 lanes (NA = ceil(m / 2) slots): slot j holds the groups at
+// positions 2j (lanes 0-15) and 2j + 1 (lanes 16-31) of the ascending list of
+// `act`.  Classifies every evaluated point and sets bit q of `done` for the
+// points (in the tile's own layout, point base + 32 q + lane) certainly
+// inside.  Returns false when a bounded wait expired.
+template <int NA, int V, int P>
+__device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, const float *thr, Entry *wbuf,
+                                            uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane, int base, int n,
+                                            uint32_t act, uint32_t list, int m, uint32_t &done) {
+  PState st[NA];
+  int idx[NA];
+  const int half = lane >> 4;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    const int pos = 2 * j + half;
+    const int g = pos < m ? (int)((list >> (4 * pos)) & 15u) : -1;
+    const int i = g >= 0 ? base + 16 * g + (lane & 15) : n;
+    const bool valid = i < n;
+    const float4 p = a.spts[valid ? i : base];
+    st[j].px = p.x;
+    st[j].py = p.y;
+    st[j].pz = p.z;
+    idx[j] = (valid && finite3(p.x, p.y, p.z)) ? i : -1;
+  }
+  if (!stream_sums<NA, V>(a, cp, wbuf, bar, ph0, ph1, lane, st)) return false;
+  const DevComp c = *cp;
+  uint32_t in_bits[NA];
+  int evaluated = 0;
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    bool inside = false;
+    if (idx[j] >= 0)
+      inside = classify_store(a, c, thr, idx[j], st[j].px, st[j].py, st[j].pz, st[j].sum - st[j].comp,
+                              (int)st[j].kp - (int)st[j].kn, st[j].bad);
+    in_bits[j] = __ballot_sync(0xffffffffu, inside);
+    evaluated += __popc(__ballot_sync(0xffffffffu, idx[j] >= 0));
+  }
+  // back to the tile's layout: the group of point (q, lane) is 2 q + half; its
+  // position in the packed list is the number of active groups below it
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int g = 2 * q + half;
+    if ((act >> g) & 1u) {
+      const int pos = __popc(act & ((1u << g) - 1u));
+      uint32_t bits = 0;
+#pragma unroll
+      for (int j = 0; j < NA; ++j)
+        if (j == (pos >> 1)) bits = in_bits[j];
+      if ((bits >> (16 * (pos & 1) + (lane & 15))) & 1u) done |= 1u << q;
+    }
+  }
+  if (lane == 0)
+    atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), (unsigned long long)evaluated * c.tri_cnt);
+  return true;
+}
 
 // Register budget: 128 registers (16 warps per SM) with two points per
 // thread, which measured fastest; unconstrained with four.
@@ -475,11 +678,14 @@ template <int NT, int P, int V>
 __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(LabelArgs a) {
   constexpr int NW = NT / 32;
   constexpr int TILE = 32 * P;
+  constexpr int NG = 2 * P;  // groups of 16 consecutive points
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[NW][2];
   __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
   __shared__ float s_wbox[NW][6];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ float s_gbox[NW][NG][6];
+  __shared__ float s_rep[NW][NG][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, half = lane >> 4;
   Entry *wbuf = reinterpret_cast<Entry *>(smem_raw) + wid * 2 * kWChunk;
   uint64_t *bar = bars[wid];
   if (lane == 0) {
@@ -493,7 +699,6 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
   const int n = (int)a.counters[CNT_N];  // < 2^31 (checked on the host)
   const int64_t nitems = a.counters[CNT_ITEMS];
   const bool early = a.early;
-  constexpr uint32_t all_done = (1u << P) - 1u;
   for (;;) {
     int64_t item = 0;
     if (lane == 0) item = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_WORK), 1ull);
@@ -501,8 +706,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
     if (item >= nitems) break;
     const int tile = a.items[item].x;
     const int base = tile * TILE;
-    PState st[P];
-    uint32_t done = 0;  // bit q: point q is invalid, non-finite or certainly inside an earlier compartment
+    uint32_t done = 0;    // bit q: point q is invalid, non-finite or certainly inside an earlier compartment
     uint32_t usable = 0;  // bit q: point q is valid and finite
     float wb[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
 #pragma unroll
@@ -510,24 +714,33 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       const int i = base + q * 32 + lane;
       const bool valid = i < n;
       const float4 p = a.spts[valid ? i : base];
-      st[q].px = p.x;
-      st[q].py = p.y;
-      st[q].pz = p.z;
-      const bool fin = finite3(p.x, p.y, p.z);
-      if (!valid || !fin) {
-        done |= 1u << q;
-      } else {
-        usable |= 1u << q;
-        wb[0] = fminf(wb[0], p.x); wb[1] = fminf(wb[1], p.y); wb[2] = fminf(wb[2], p.z);
-        wb[3] = fmaxf(wb[3], p.x); wb[4] = fmaxf(wb[4], p.y); wb[5] = fmaxf(wb[5], p.z);
+      const bool ok = valid && finite3(p.x, p.y, p.z);
+      if (!ok) done |= 1u << q;
+      else usable |= 1u << q;
+      // box of the point's group of 16 (half-warp reduction), then the tile's
+      float g[6] = {ok ? p.x : INFINITY, ok ? p.y : INFINITY, ok ? p.z : INFINITY,
+                    ok ? p.x : -INFINITY, ok ? p.y : -INFINITY, ok ? p.z : -INFINITY};
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          g[k] = fminf(g[k], __shfl_xor_sync(0xffffffffu, g[k], o));
+          g[3 + k] = fmaxf(g[3 + k], __shfl_xor_sync(0xffffffffu, g[3 + k], o));
+        }
+      if ((lane & 15) == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s_gbox[wid][2 * q + half][k] = g[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        wb[k] = fminf(wb[k], g[k]);
+        wb[3 + k] = fmaxf(wb[3 + k], g[3 + k]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      for (int o = 16; o > 0; o >>= 1) {
-        wb[k] = fminf(wb[k], __shfl_xor_sync(0xffffffffu, wb[k], o));
-        wb[3 + k] = fmaxf(wb[3 + k], __shfl_xor_sync(0xffffffffu, wb[3 + k], o));
-      }
+    for (int k = 0; k < 3; ++k) {
+      wb[k] = fminf(wb[k], __shfl_xor_sync(0xffffffffu, wb[k], 16));
+      wb[3 + k] = fmaxf(wb[3 + k], __shfl_xor_sync(0xffffffffu, wb[3 + k], 16));
+    }
     // the tile's box lives in shared memory while the compartments are walked
     if (lane == 0)
       for (int k = 0; k < 6; ++k) s_wbox[wid][k] = wb[k];
@@ -540,111 +753,120 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       const float *thr = a.dop + (int64_t)s_rowcomp[r] * kDop;
       // winding number 0 for every point of the tile
       if (box_misses(s_wbox[wid], cp) || dop_box_misses(s_wbox[wid], thr)) continue;
-      if (early && __all_sync(0xffffffffu, done == all_done)) break;
+      // groups with a point that still needs this compartment
+      uint32_t need = 0;
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const uint32_t b = __ballot_sync(0xffffffffu, ((usable >> q) & 1u) && !(early && ((done >> q) & 1u)));
+        need |= ((b & 0xffffu) ? 1u : 0u) << (2 * q);
+        need |= ((b >> 16) ? 1u : 0u) << (2 * q + 1);
+      }
+      if (!need) {
+        if (early) break;  // every point decided: no later compartment matters
+        continue;          // no usable point in the tile
+      }
+      uint32_t coh = 0;  // groups whose points take a representative's winding number
+      int kg[NG];
+#pragma unroll
+      for (int g = 0; g < NG; ++g) kg[g] = 0;
       if (a.coherence) {
-        // Tile coherence: when no triangle's box meets the tile's box, the
-        // surface does not cross the box (convex, hence connected), so every
-        // point of the tile has the winding number of any one of them.
-        int k_tile = 0;
-        const int rc = coherent_tile(a, cp, s_wbox[wid], st, usable, lane, &k_tile);
-        if (rc == 1) {
+        // Coherence: where no triangle's box meets a box of points, the
+        // surface does not cross that box (convex, hence connected), so all
+        // its points have the winding number of any one of them.  First the
+        // whole tile (representative: its first usable point), then, if some
+        // triangle box meets the tile, each group of 16 points.
+        // the tile's first usable point (positions are re-read from memory,
+        // not held in registers across the hot loop)
+        int first = -1;
+#pragma unroll
+        for (int q = P - 1; q >= 0; --q) {
+          const uint32_t b = __ballot_sync(0xffffffffu, (usable >> q) & 1u);
+          if (b) first = base + 32 * q + __ffs(b) - 1;
+        }
+        const float4 rp = a.spts[first];
+        const float rx = rp.x, ry = rp.y, rz = rp.z;
+        int k_t = 0, t_hit = -1;
+        unsigned long long reps = 0;
+        if (rep_pass(a, cp, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit)) {
+          coh = need;
+#pragma unroll
+          for (int g = 0; g < NG; ++g) kg[g] = k_t;
+          reps += __ldg(&cp->tri_cnt);
+        } else if (t_hit < 0) {
+          reps += __ldg(&cp->tri_cnt);  // completed, but the representative is uncertain
+        } else {
+          reps += t_hit;
+          uint32_t untouched = need & ~touched_groups<NG>(a, cp, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
+          // an odd number of touched groups leaves half a slot of lanes free:
+          // one untouched group is evaluated there instead of by its
+          // representative
+          if ((__popc(need & ~untouched) & 1) && untouched) untouched &= untouched - 1u;
+          if (untouched) {
+            // each group's first usable point, in shared memory for the pass
+            uint32_t ub[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) ub[q] = __ballot_sync(0xffffffffu, (usable >> q) & 1u);
+            if (lane == 0) {
+#pragma unroll
+              for (int g = 0; g < NG; ++g)
+                if ((untouched >> g) & 1u) {
+                  const uint32_t gl = (ub[g >> 1] >> (16 * (g & 1))) & 0xffffu;
+                  const float4 gp = a.spts[base + 32 * (g >> 1) + 16 * (g & 1) + __ffs(gl) - 1];
+                  s_rep[wid][g][0] = gp.x;
+                  s_rep[wid][g][1] = gp.y;
+                  s_rep[wid][g][2] = gp.z;
+                }
+            }
+            __syncwarp();
+            int kk[NG];
+            const uint32_t cert = group_reps<NG>(a, cp, untouched, s_rep[wid], lane, kk);
+            __syncwarp();
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+              if ((cert >> g) & 1u) kg[g] = kk[g];
+            coh |= cert;
+            reps += (unsigned long long)__popc(untouched) * __ldg(&cp->tri_cnt);
+          }
+        }
+        if (coh) {
           const DevComp c = *cp;
+          int assigned = 0;
 #pragma unroll
           for (int q = 0; q < P; ++q) {
-            const int i = base + q * 32 + lane;
-            if (i < n && classify_coherent(a, c, thr, i, st[q].px, st[q].py, st[q].pz, k_tile))
-              done |= 1u << q;
-          }
-          if (lane == 0) {
-            atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), (unsigned long long)c.tri_cnt);
-            atomicAdd((unsigned long long *)(a.counters + CNT_COHERENT),
-                      (unsigned long long)max(0, min(TILE, n - base)));
-          }
-          continue;
-        }
-      }
-      const int entry_cnt = __ldg(&cp->entry_cnt);
-      const Entry *gsrc = a.entries + __ldg(&cp->entry_off);
-      const int nchunks = (entry_cnt + kWChunk - 1) / kWChunk;
-      if (lane == 0) {
-        tma_load_1d(wbuf, gsrc, min(kWChunk, entry_cnt) * (uint32_t)sizeof(Entry), &bar[0]);
-        if (nchunks > 1)
-          tma_load_1d(wbuf + kWChunk, gsrc + kWChunk, min(kWChunk, entry_cnt - kWChunk) * (uint32_t)sizeof(Entry),
-                      &bar[1]);
-      }
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        st[q].grp = st[q].sum = st[q].comp = 0.f;
-        st[q].bad = __int_as_float(0x7f800000);
-        st[q].kp = st[q].kn = 0u;
-      }
-      for (int ch = 0; ch < nchunks; ++ch) {
-        const int b = ch & 1;
-        const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
-        if (__any_sync(0xffffffffu, !ok)) {
-          timed_out = true;
-          break;
-        }
-        if (b) ph1 ^= 1; else ph0 ^= 1;
-        const Entry *E = wbuf + b * kWChunk;
-        const int cnt = min(kWChunk, entry_cnt - ch * kWChunk);
-        if (ch == 0) {
-          const float4 v0 = E[0].v;
-#pragma unroll
-          for (int q = 0; q < P; ++q) window_init(st[q], v0);
-        }
-        for (int g = 0; g < cnt; g += kGroup) {
-          if constexpr (V == 0) {
-#pragma unroll 1
-            for (int j = 0; j < kGroup; j += 4) {
-              const Entry *e = E + g + j;
-              const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
-              const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
-#pragma unroll
-              for (int q = 0; q < P; ++q) {
-                float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
-                geom_step(st[q], v0, n0, N0, D0);
-                geom_step(st[q], v1, n1, N1, D1);
-                cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
-                geom_step(st[q], v2, n2, N0, D0);
-                geom_step(st[q], v3, n3, N1, D1);
-                cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
-                cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
-                st[q].grp += half_angle(I, R);
-              }
+            const int g = 2 * q + half;
+            const bool mine = ((coh >> g) & 1u) && ((usable >> q) & 1u);
+            if (mine) {
+              const int i = base + q * 32 + lane;
+              const float4 p = a.spts[i];
+              if (classify_coherent(a, c, thr, i, p.x, p.y, p.z, half ? kg[2 * q + 1] : kg[2 * q]))
+                done |= 1u << q;
             }
-          } else {
-#pragma unroll 4
-            for (int j = 0; j < kGroup; ++j) {
-              const float4 Vv = E[g + j].v;
-              const float4 Nn = E[g + j].n;
-#pragma unroll
-              for (int q = 0; q < P; ++q) vos_step(st[q], Vv, Nn);
-            }
+            assigned += __popc(__ballot_sync(0xffffffffu, mine));
           }
-#pragma unroll
-          for (int q = 0; q < P; ++q) kahan_flush(st[q]);
+          if (lane == 0)
+            atomicAdd((unsigned long long *)(a.counters + CNT_COHERENT), (unsigned long long)assigned);
         }
-        __syncwarp();  // every lane is done with buffer b before it is refilled
-        if (lane == 0 && ch + 2 < nchunks)
-          tma_load_1d(wbuf + b * kWChunk, gsrc + (int64_t)(ch + 2) * kWChunk,
-                      min(kWChunk, entry_cnt - (ch + 2) * kWChunk) * (uint32_t)sizeof(Entry), &bar[b]);
+        if (lane == 0 && reps)
+          atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), reps);
       }
-      if (timed_out) break;
-      const DevComp c = *cp;
+      const uint32_t act = need & ~coh;
+      if (!act) continue;
+      uint32_t list = 0;
+      int m = 0;
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const int i = base + q * 32 + lane;
-        if (i < n) {
-          const bool inside = classify_store(a, c, a.dop + (int64_t)s_rowcomp[r] * kDop, i, st[q].px, st[q].py,
-                                             st[q].pz, st[q].sum - st[q].comp, (int)st[q].kp - (int)st[q].kn,
-                                             st[q].bad);
-          if (inside) done |= 1u << q;
-        }
+      for (int g = 0; g < NG; ++g)
+        if ((act >> g) & 1u) list |= (uint32_t)g << (4 * m++);
+      bool ok = true;
+      switch ((m + 1) >> 1) {
+        case 1: ok = eval_groups<1, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
+        case 2: ok = eval_groups<(P >= 2 ? 2 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
+        case 3: ok = eval_groups<(P >= 3 ? 3 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
+        default: ok = eval_groups<P, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
       }
-      if (lane == 0)
-        atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL),
-                  (unsigned long long)((int64_t)max(0, min(TILE, n - base)) * c.tri_cnt));
+      if (!ok) {
+        timed_out = true;
+        break;
+      }
     }
     if (timed_out) {
       if (lane == 0) record_timeout(a.status, 1);
