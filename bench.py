@@ -383,6 +383,9 @@ def run_ours(args):
                               "speedup": s64["ms_total"] / s32["ms_total"], "labels_equal": same,
                               "fp64_pairs_per_s": s64["pairs_evaluated"] / (s64["ms_total"] * 1e-3)}
 
+    line["coherent_pairs_per_step"] = st["coherent_pairs"]
+    line["representative_pairs_per_step"] = st["representative_pairs"]
+
     # measured FMA throughput of this GPU (cross-check of the FP32 peak; the
     # FP64 rate sets the cost of the re-evaluation and of the plain FP64 kernel)
     if rank == 0:
@@ -426,7 +429,6 @@ def run_ours(args):
                                      "pairs_evaluated_per_step": snc["pairs_evaluated"],
                                      "evaluated_pairs_per_s": snc["pairs_evaluated"] / (msnc * 1e-3),
                                      "ms_label_kernel": snc["ms_label"]}
-        line["coherent_pairs_per_step"] = st["coherent_pairs"]
 
     if rank == 0 and not args.no_refine:
         line["refine"] = refine_measure(zef, torch, dev)

@@ -124,8 +124,10 @@ typedef struct zef_label_stats {
     float ms_label;            /* device time of the main labeling kernel */
     float ms_rescue;           /* device time of the FP64 re-evaluation */
     float reserved;
-    int64_t coherent_pairs;    /* (point, compartment) pairs decided by a tile's
-                                  representative point */
+    int64_t coherent_pairs;    /* (point, compartment) pairs decided by the
+                                  representative point of a tile or group */
+    int64_t representative_pairs; /* of pairs_evaluated: point x triangle pairs
+                                     of those representatives */
 } zef_label_stats;
 
 /* Mesh for zef_refine_and_relabel.  All four arrays must be device memory or

@@ -667,6 +667,7 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
     stats->work_items = h[CNT_ITEMS];
     stats->tiles = h[CNT_TILES];
     stats->coherent_pairs = h[CNT_COHERENT];
+    stats->representative_pairs = h[CNT_REP_PAIRS];
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;

@@ -112,6 +112,7 @@ enum Counter {
   CNT_ABORT,          // refinement stopped (capacity)
   CNT_OWN_LEN,        // 6 x flagged tets of the level
   CNT_COHERENT,       // (point, compartment) pairs decided by a tile representative
+  CNT_REP_PAIRS,      // point x triangle pairs of tile and group representatives
   CNT_COUNT_ = 24
 };
 

@@ -846,8 +846,10 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
           if (lane == 0)
             atomicAdd((unsigned long long *)(a.counters + CNT_COHERENT), (unsigned long long)assigned);
         }
-        if (lane == 0 && reps)
+        if (lane == 0 && reps) {
           atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), reps);
+          atomicAdd((unsigned long long *)(a.counters + CNT_REP_PAIRS), reps);
+        }
       }
       const uint32_t act = need & ~coh;
       if (!act) continue;
@@ -1238,6 +1240,7 @@ __global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
     cnt[CNT_PAIRS_EVAL] = 0;
     cnt[CNT_PAIRS_RESCUE] = 0;
     cnt[CNT_COHERENT] = 0;
+    cnt[CNT_REP_PAIRS] = 0;
     int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
     for (int k = 0; k < 3; ++k) {
       box[k] = INT32_MAX;

@@ -174,6 +174,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
     stats->work_items = h[CNT_ITEMS];
     stats->tiles = h[CNT_TILES];
     stats->coherent_pairs = h[CNT_COHERENT];
+    stats->representative_pairs = h[CNT_REP_PAIRS];
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;

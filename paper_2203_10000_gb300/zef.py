@@ -61,7 +61,7 @@ class LabelStats(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
                 ("ms_total", ctypes.c_float), ("ms_label", ctypes.c_float),
                 ("ms_rescue", ctypes.c_float), ("reserved", ctypes.c_float),
-                ("coherent_pairs", ctypes.c_int64)]
+                ("coherent_pairs", ctypes.c_int64), ("representative_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
