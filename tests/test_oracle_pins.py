@@ -266,7 +266,7 @@ def test_refine_single_tet_one_to_eight():
     nodes = np.array([[0, 0, 0], [4, 0, 0], [0, 4, 0], [0, 0, 4], [9, 9, 9]], dtype=np.float32)
     tets = np.array([[0, 1, 2, 3], [1, 2, 3, 4]], dtype=np.int32)
     # node 0 differs from the rest: only tet 0 straddles a label boundary
-    new_nodes, out, flagged = refine.refine_level(nodes, tets, np.array([1, 2, 2, 2, 2]))
+    new_nodes, out, flagged, _ = refine.refine_level(nodes, tets, np.array([1, 2, 2, 2, 2]))
     assert flagged.tolist() == [0]
     assert new_nodes.shape == (6, 3)
     assert out.shape == (2 + 7, 4)
@@ -434,3 +434,92 @@ def test_relabel_boundary_sphere_equals_full_relabel(oracle_mod):
     lab, per, conv = relabel.relabel_boundary(nodes, tets, lab0, [s1], [1], 20)
     full, _ = oracle_mod.label_points(nodes, [s1], [1])
     assert conv and np.array_equal(lab, full) and len(per) >= 3
+
+
+# ---------------------------------------------------------------- conforming refinement
+def _faces_conform(nodes, tets, lo, hi):
+    """Every face is shared by exactly two tets except faces on the domain
+    box, which belong to one: no hanging node anywhere."""
+    from collections import Counter
+    faces = Counter()
+    for t in tets:
+        a, b, c, d = (int(x) for x in t)
+        for f in ((a, b, c), (a, b, d), (a, c, d), (b, c, d)):
+            faces[tuple(sorted(f))] += 1
+    x = nodes.astype(np.float64)
+    for f, k in faces.items():
+        if k == 2:
+            continue
+        if k != 1:
+            return False
+        p = x[list(f)]
+        on_box = any(np.all(p[:, ax] == lo[ax]) or np.all(p[:, ax] == hi[ax]) for ax in range(3))
+        if not on_box:
+            return False
+    return True
+
+
+def test_conforming_single_red_tet_needs_no_promotion():
+    """One red tet in a conforming mesh: every neighbour shares one of its
+    edges or one of its faces, both green patterns, so nothing is promoted;
+    the result conforms and keeps the volume."""
+    from oracle import refine
+    nodes, tets = zs.lattice_5tet(3, 1.0, (0.0, 0.0, 0.0))
+    labels = np.zeros(nodes.shape[0], np.int32)
+    centre = 5 * 13 + 4           # the central tet of the middle cell
+    labels[tets[centre][0]] = 1   # one node differs: every tet holding it flags
+    flagged = refine.flag_tets(tets, labels)
+    red = refine.closure(tets, flagged)
+    assert red.sum() >= flagged.sum()
+    n1, t1, fl, st = refine.refine_level(nodes, tets, labels, conforming=True)
+    allnodes = np.concatenate([nodes, n1])
+    assert _faces_conform(allnodes, t1, (0, 0, 0), (3, 3, 3))
+    v0 = sum(_vol(nodes, t) for t in tets)
+    v1 = [_vol(allnodes, t) for t in t1]
+    assert min(v1) > 0 and abs(sum(v1) - v0) < 1e-9 * v0
+    # the pattern classes, and a single red tet promotes nothing
+    assert refine.green_pattern(0b000001) == ("edge", 0, 1)
+    assert refine.green_pattern(0b100001) == "red"          # opposite edges 01, 23
+    assert refine.green_pattern(0b001011) == ("face", 0, 1, 2)
+    assert refine.green_pattern(0b000111) == "red"          # three edges at vertex 0
+    assert refine.green_pattern(0b000011) == ("two", 0, 1, 2)
+    red_one = np.zeros(tets.shape[0], bool)
+    red_one[centre] = True
+    assert refine.closure(tets, red_one).sum() == 1
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_conforming_refinement_of_a_sphere(oracle_mod, levels):
+    from oracle import refine
+    s = zs.config0().surfaces[0]
+    nodes, tets = zs.lattice_5tet(5, 0.6, (-1.5, -1.5, -1.5))
+    n2, t2, lab, per = refine.refine_and_relabel(nodes, tets, [s], [1], levels=levels, conforming=True)
+    assert _faces_conform(n2, t2, (-1.5, -1.5, -1.5), (1.5, 1.5, 1.5))
+    v0 = sum(_vol(nodes, t) for t in tets)
+    v2 = [_vol(n2, t) for t in t2]
+    assert min(v2) > 0 and abs(sum(v2) - v0) < 1e-9 * v0
+    assert all(p["green"] > 0 for p in per)
+    # the incremental labels equal a full re-labeling of the final nodes
+    full, _ = oracle_mod.label_points(n2, [s], [1])
+    assert np.array_equal(lab, full)
+    # closure property of the last level: every tet that is not red has an
+    # empty or green pattern; every promoted tet has a red pattern from the
+    # other red tets alone
+    n1, t1, l1, _ = refine.refine_and_relabel(nodes, tets, [s], [1], levels=levels - 1, conforming=True)
+    fl = refine.flag_tets(t1, l1)
+    red = refine.closure(t1, fl)
+    keys = [refine._edge_keys(t) for t in t1]
+    split = set(k for i in np.nonzero(red)[0] for k in keys[i])
+    for i in range(t1.shape[0]):
+        if red[i] and fl[i]:
+            continue
+        if red[i]:
+            others = set(k for j in np.nonzero(red)[0] if j != i for k in keys[j])
+            mask = sum(1 << e for e in range(6) if keys[i][e] in others)
+            assert refine.green_pattern(mask) == "red"
+        else:
+            mask = sum(1 << e for e in range(6) if keys[i][e] in split)
+            assert refine.green_pattern(mask) != "red"
+    # without closure the same level leaves hanging nodes
+    n3, t3, _, _ = refine.refine_and_relabel(nodes, tets, [s], [1], levels=levels)
+    assert not _faces_conform(n3, t3, (-1.5, -1.5, -1.5), (1.5, 1.5, 1.5))
