@@ -215,6 +215,24 @@ def refine_measure(zef, torch, dev):
         torch.cuda.synchronize(dev)
         out = {"workload": w.name, "initial_nodes": n0, "initial_tets": m0, "levels": per,
                "ms_total_incl_initial_labeling": e0.elapsed_time(e1), "final_nodes": n1, "final_tets": m1}
+    # the same three levels closed into a conforming mesh (Fig. 2 c-e)
+    ncap_c, tcap_c = 8_000_000, 26_000_000
+    nodes_c = torch.zeros((ncap_c, 3), dtype=torch.float32, device=dev)
+    tets_c = torch.zeros((tcap_c, 4), dtype=torch.int32, device=dev)
+    labels_c = torch.zeros(ncap_c, dtype=torch.int32, device=dev)
+    for rep in range(2):
+        nodes_c[:n0].copy_(src_n)
+        tets_c[:m0].copy_(src_t)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cn1, cm1, cper = ctx.refine_and_relabel(nodes_c, tets_c, labels_c, n0, m0, 3, conforming=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    out["conforming"] = {"levels": cper, "ms_total_incl_initial_labeling": e0.elapsed_time(e1),
+                         "final_nodes": cn1, "final_tets": cm1}
+    del nodes_c, tets_c, labels_c
     # element labels (four-nodes rule) of the refined mesh, then the recursive
     # boundary re-labeling after every node moved by up to 0.2 mm (seeded)
     rn, rt, rl = nodes[:n1], tets[:m1], labels[:n1].clone()

@@ -143,8 +143,26 @@ typedef struct zef_mesh {
     int64_t tet_capacity;
     int32_t labels_valid;  /* nonzero: node_labels[0, num_nodes) already hold
                               labels; 0: label every node first */
-    int32_t reserved;
+    int32_t flags;         /* ZEF_REFINE_CONFORMING or 0 */
 } zef_mesh;
+
+/* zef_mesh.flags: close every level into a conforming mesh (Sec. 2.1.2,
+   Fig. 2 c-e).  Besides the 1 -> 8 split of the flagged tets, a tet whose
+   split edges are one edge, two edges with a common vertex, or the three
+   edges of one face is split into two, three or four ("green"); a tet with
+   any other pattern is split into eight as well, repeated until no tet
+   changes.  Green templates replace corners by edge midpoints: one edge
+   (i, j): T[j<-m], T[i<-m]; two edges (p, q), (p, r) with q < r: the corner
+   T[q<-m_pq, r<-m_pr], then T[q<-m_pq, p<-m_pr], T[p<-m_pq] when the quad
+   diagonal m_pq-r is not longer than q-m_pr (float32 squared lengths), else
+   T[r<-m_pr, p<-m_pq], T[p<-m_pr]; face (p, q, r), p < q < r: the corners
+   T[q<-m_pq, r<-m_pr], T[p<-m_pq, r<-m_qr], T[p<-m_pr, q<-m_qr] and the
+   centre T[p<-m_qr, q<-m_pr, r<-m_pq].  New nodes are the edge midpoints of
+   the tets split into eight, numbered by first appearance over those tets in
+   index order; a split tet's slot receives its first child, the other
+   children of the eight-way splits are appended in their order, then the
+   other children of the green splits in tet index order. */
+#define ZEF_REFINE_CONFORMING 1
 
 typedef struct zef_level_stats {
     int64_t flagged_tets;   /* tets whose four node labels were not all equal */
@@ -153,6 +171,8 @@ typedef struct zef_level_stats {
     int64_t tets;           /* tet count after the level */
     int64_t pairs_evaluated;
     int64_t uncertain_pairs;
+    int64_t promoted_tets;  /* conforming: tets split into eight by the closure */
+    int64_t green_tets;     /* conforming: tets split along one to three edges */
 } zef_level_stats;
 
 typedef struct zef_relabel_pass {

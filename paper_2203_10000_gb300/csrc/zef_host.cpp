@@ -726,6 +726,7 @@ zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, 
       mesh->num_nodes > mesh->node_capacity || mesh->num_tets > mesh->tet_capacity ||
       mesh->node_capacity >= ((int64_t)1 << 31) || mesh->tet_capacity >= ((int64_t)1 << 31))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad mesh arrays or capacities");
+  if (mesh->flags & ~(int32_t)ZEF_REFINE_CONFORMING) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown mesh flags");
   zef_label_opts o;
   if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
   fill_default_opts(&o);

@@ -113,7 +113,12 @@ enum Counter {
   CNT_OWN_LEN,        // 6 x flagged tets of the level
   CNT_COHERENT,       // (point, compartment) pairs decided by a tile representative
   CNT_REP_PAIRS,      // point x triangle pairs of tile and group representatives
-  CNT_COUNT_ = 24
+  CNT_LEVEL_SEED,     // conforming refinement: tets flagged by their labels
+  CNT_CL_CHANGED,     // closure: tets promoted in the current pass
+  CNT_CL_ITER,        // closure passes of the level
+  CNT_CL_GREEN,       // tets split along one to three edges
+  CNT_CL_GEXTRA,      // children those splits add
+  CNT_COUNT_ = 32
 };
 
 struct LaunchShape {
@@ -172,8 +177,8 @@ struct zef_ctx {
   uint64_t rb_key = 0;
 
   // refinement scratch
-  void *rf_buf[8] = {};
-  size_t rf_cap[8] = {};
+  void *rf_buf[10] = {};
+  size_t rf_cap[10] = {};
   cudaGraphExec_t rf_exec = nullptr;
   uint64_t rf_key = 0;
 };

@@ -72,13 +72,14 @@ class Mesh(ctypes.Structure):
                 ("node_labels", ctypes.c_void_p), ("num_nodes", ctypes.c_int64),
                 ("num_tets", ctypes.c_int64), ("node_capacity", ctypes.c_int64),
                 ("tet_capacity", ctypes.c_int64), ("labels_valid", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 class LevelStats(ctypes.Structure):
     _fields_ = [("flagged_tets", ctypes.c_int64), ("new_nodes", ctypes.c_int64),
                 ("nodes", ctypes.c_int64), ("tets", ctypes.c_int64),
-                ("pairs_evaluated", ctypes.c_int64), ("uncertain_pairs", ctypes.c_int64)]
+                ("pairs_evaluated", ctypes.c_int64), ("uncertain_pairs", ctypes.c_int64),
+                ("promoted_tets", ctypes.c_int64), ("green_tets", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +116,7 @@ _lib.zef_relabel_boundary.restype = ctypes.c_int
 _lib.zef_label_points_noalloc.argtypes = [_P, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                           ctypes.POINTER(LabelStats)]
 _lib.zef_label_points_noalloc.restype = ctypes.c_int
+ZEF_REFINE_CONFORMING = 1
 NOALLOC_MAX_POINTS = 65536
 _lib.zef_refine_and_relabel.argtypes = [_P, ctypes.POINTER(Mesh), _I32, ctypes.POINTER(LabelOpts),
                                         ctypes.POINTER(LevelStats)]
@@ -376,7 +378,8 @@ class Context:
         return [(int(per[i].evaluated), int(per[i].changed)) for i in range(npass.value)], bool(conv.value)
 
     def refine_and_relabel(self, nodes, tets, node_labels, num_nodes: int, num_tets: int,
-                           levels: int, labels_valid: bool = False, opts: LabelOpts | None = None):
+                           levels: int, labels_valid: bool = False, opts: LabelOpts | None = None,
+                           conforming: bool = False):
         """In-place refinement of preallocated arrays (capacities = their
         lengths).  Returns (num_nodes, num_tets, per-level stats)."""
         m = Mesh()
@@ -388,6 +391,7 @@ class Context:
         m.node_capacity = int(nodes.shape[0])
         m.tet_capacity = int(tets.shape[0])
         m.labels_valid = 1 if labels_valid else 0
+        m.flags = ZEF_REFINE_CONFORMING if conforming else 0
         per = (LevelStats * max(1, levels))()
         o = opts if opts is not None else make_opts()
         self._check(_lib.zef_refine_and_relabel(self._h, ctypes.byref(m), int(levels), ctypes.byref(o), per))
