@@ -1,0 +1,116 @@
+"""Oracle of the post-processing steps of Sec. 2.2: Taubin smoothing
+(Sec. 2.2.1) and inflation (Sec. 2.2.2), in FP64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Readings where the printed formulas are garbled or silent:
+  * smoothing: N_i is node i together with the nodes joined to it by a mesh
+    edge (volumetric smoothing); the printed sums of neighbour positions are
+    read as the Laplacian L(x)_i = sum_{j in N_i} (x_j - x_i) / |N_i|; one
+    iteration is x' = x + lambda L(x) (forward step) followed by
+    x'' = x' - mu L(x') (backward step); nodes marked fixed do not move; the
+    iteration stops after the first iteration whose forward step satisfies
+    ||x' - x||_2 / ||x^(0)||_2 <= xi, or after max_iters;
+  * inflation, for one compartment surface S: an edge whose one node is
+    inside S (Omega > 2 pi) and whose other node is outside crosses S; d is
+    the distance from the inside node to the intersection of the edge with S
+    nearest to it, e the unit vector from the inside node along the edge;
+    each inside node moves by zeta d e averaged over its crossing edges.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import label_points
+
+
+def unique_edges(tets) -> np.ndarray:
+    """Sorted unique node pairs (a < b) of the tets' six edges."""
+    t = np.asarray(tets, dtype=np.int64).reshape(-1, 4)
+    pairs = np.concatenate([t[:, [i, j]] for i, j in ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))])
+    pairs.sort(axis=1)
+    return np.unique(pairs, axis=0)
+
+
+def laplacian(x: np.ndarray, edges: np.ndarray) -> np.ndarray:
+    """L(x)_i = sum over j in N_i of (x_j - x_i) / |N_i|, N_i = {i} + edge neighbours."""
+    acc = np.zeros_like(x)
+    a, b = edges[:, 0], edges[:, 1]
+    np.add.at(acc, a, x[b] - x[a])
+    np.add.at(acc, b, x[a] - x[b])
+    deg = np.bincount(edges.ravel(), minlength=x.shape[0]) + 1
+    return acc / deg[:, None]
+
+
+def taubin_smooth(nodes, tets, lam: float, mu: float, xi: float, max_iters: int, fixed=None):
+    """Returns (positions float64 (N, 3), iterations run)."""
+    x = np.asarray(nodes, dtype=np.float64).reshape(-1, 3).copy()
+    edges = unique_edges(tets)
+    fix = np.zeros(x.shape[0], bool) if fixed is None else np.asarray(fixed, bool)
+    x0 = np.linalg.norm(x)
+    it = 0
+    while it < max_iters:
+        xh = x + lam * laplacian(x, edges)
+        xh[fix] = x[fix]
+        step = np.linalg.norm(xh - x) / x0
+        x = xh - mu * laplacian(xh, edges)
+        x[fix] = xh[fix]
+        it += 1
+        if step <= xi:
+            break
+    return x, it
+
+
+def segment_surface_distance(p, q, verts, tris):
+    """Distance from p to the intersection of segment [p, q] with the
+    triangles that is nearest to p (inf when none), by the plane of each
+    triangle and a point-in-triangle test with barycentric coordinates."""
+    p = np.asarray(p, np.float64)
+    q = np.asarray(q, np.float64)
+    v = np.asarray(verts, np.float64)[np.asarray(tris)]
+    a, b, c = v[:, 0], v[:, 1], v[:, 2]
+    n = np.cross(b - a, c - a)
+    d = q - p
+    den = n @ d
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.einsum("ij,ij->i", n, a - p) / den
+        x = p + t[:, None] * d
+    # barycentric coordinates of x in each triangle
+    v0, v1, v2 = b - a, c - a, x - a
+    d00 = np.einsum("ij,ij->i", v0, v0)
+    d01 = np.einsum("ij,ij->i", v0, v1)
+    d11 = np.einsum("ij,ij->i", v1, v1)
+    d20 = np.einsum("ij,ij->i", v2, v0)
+    d21 = np.einsum("ij,ij->i", v2, v1)
+    den2 = d00 * d11 - d01 * d01
+    with np.errstate(divide="ignore", invalid="ignore"):
+        bv = (d11 * d20 - d01 * d21) / den2
+        bw = (d00 * d21 - d01 * d20) / den2
+    hit = (den != 0) & (t >= 0) & (t <= 1) & (bv >= 0) & (bw >= 0) & (bv + bw <= 1)
+    if not hit.any():
+        return np.inf
+    return float(t[hit].min() * np.linalg.norm(d))
+
+
+def inflate(nodes, tets, surface, zeta: float):
+    """One inflation of the nodes inside `surface` (an object with .id,
+    .verts, .tris) towards it.  Returns (positions float64, moved node count)."""
+    x = np.asarray(nodes, dtype=np.float64).reshape(-1, 3).copy()
+    edges = unique_edges(tets)
+    lab, _ = label_points(np.asarray(nodes, np.float32), [surface], [surface.id])
+    inside = lab == surface.id
+    disp = np.zeros_like(x)
+    cnt = np.zeros(x.shape[0], np.int64)
+    for a, b in edges:
+        if inside[a] == inside[b]:
+            continue
+        i, j = (a, b) if inside[a] else (b, a)
+        d = segment_surface_distance(x[i], x[j], surface.verts, surface.tris)
+        if not np.isfinite(d):
+            continue
+        e = (x[j] - x[i]) / np.linalg.norm(x[j] - x[i])
+        disp[i] += zeta * d * e
+        cnt[i] += 1
+    moved = cnt > 0
+    x[moved] += disp[moved] / cnt[moved, None]
+    return x, int(moved.sum())

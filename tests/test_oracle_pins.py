@@ -523,3 +523,94 @@ def test_conforming_refinement_of_a_sphere(oracle_mod, levels):
     # without closure the same level leaves hanging nodes
     n3, t3, _, _ = refine.refine_and_relabel(nodes, tets, [s], [1], levels=levels)
     assert not _faces_conform(n3, t3, (-1.5, -1.5, -1.5), (1.5, 1.5, 1.5))
+
+
+# ---------------------------------------------------------------- post-processing (Sec. 2.2)
+def _edge_sets_brute(tets, n):
+    adj = [set() for _ in range(n)]
+    for t in tets:
+        for a in t:
+            for b in t:
+                if a != b:
+                    adj[int(a)].add(int(b))
+    return adj
+
+
+def test_taubin_step_matches_spectral_factors():
+    """One Taubin iteration equals (I - mu M)(I + lambda M) x with
+    M = (D + I)^-1 (A - D) from a brute-force adjacency, i.e. every
+    eigenvector of M with eigenvalue -k is scaled by (1 - lambda k)(1 + mu k)."""
+    from oracle import postprocess as pp
+    nodes, tets = zs.lattice_5tet(3, 1.0, (0.0, 0.0, 0.0))
+    rng = np.random.default_rng(3)
+    x = nodes.astype(np.float64) + rng.normal(0, 0.2, nodes.shape)
+    n = x.shape[0]
+    adj = _edge_sets_brute(tets, n)
+    A = np.zeros((n, n))
+    for i, s in enumerate(adj):
+        A[i, list(s)] = 1.0
+    D = np.diag(A.sum(1))
+    M = np.linalg.solve(D + np.eye(n), A - D)
+    lam, mu = 0.4, 0.4
+    out, it = pp.taubin_smooth(x, tets, lam, mu, xi=10.0, max_iters=1)
+    assert it == 1
+    want = (np.eye(n) - mu * M) @ ((np.eye(n) + lam * M) @ x)
+    np.testing.assert_allclose(out, want, rtol=0, atol=1e-12)
+    w, V = np.linalg.eig(M)
+    k = -w.real
+    assert np.all(k > -1e-12) and np.all(k < 2.0 + 1e-12)
+    c = np.linalg.solve(V, x)                      # modal coordinates
+    c2 = np.linalg.solve(V, out)
+    factor = ((1 - lam * k) * (1 + mu * k))[:, None]
+    np.testing.assert_allclose(c2.real, (factor * c).real, atol=1e-9)
+
+
+def test_taubin_fixed_nodes_translation_and_stop():
+    from oracle import postprocess as pp
+    nodes, tets = zs.lattice_5tet(4, 1.0, (0.0, 0.0, 0.0))
+    rng = np.random.default_rng(4)
+    x = nodes.astype(np.float64) + rng.normal(0, 0.1, nodes.shape)
+    fixed = np.any((nodes == 0) | (nodes == 4), axis=1)
+    a, ia = pp.taubin_smooth(x, tets, 0.4, 0.4, 0.0, 5, fixed)
+    b, ib = pp.taubin_smooth(x + [10.0, -3.0, 7.0], tets, 0.4, 0.4, 0.0, 5, fixed)
+    assert ia == ib == 5
+    np.testing.assert_allclose(b - [10.0, -3.0, 7.0], a, atol=1e-12)
+    assert np.array_equal(a[fixed], x[fixed])
+    _, i1 = pp.taubin_smooth(x, tets, 0.4, 0.4, 0.9, 50, fixed)
+    assert i1 == 1
+
+
+def test_inflation_towards_box_faces():
+    """Nodes inside a box move along their crossing edges by zeta times the
+    distance to the face they cross (exact for axis-aligned planes)."""
+    from oracle import postprocess as pp
+    nodes, tets = zs.lattice_5tet(6, 1.0, (-3.0, -3.0, -3.0))
+    lo, hi = np.array([-1.7, -1.4, -2.3]), np.array([1.6, 1.3, 0.8])
+    surf = zs.Surface(1, "box", *zs.box_surface(lo, hi, 1))
+    zeta = 0.05
+    out, moved = pp.inflate(nodes, tets, surf, zeta)
+    x = nodes.astype(np.float64)
+    inside = np.all((x > lo) & (x < hi), axis=1)
+    edges = pp.unique_edges(tets)
+    disp = np.zeros_like(x)
+    cnt = np.zeros(len(x))
+    for a, b in edges:
+        if inside[a] == inside[b]:
+            continue
+        i, j = (a, b) if inside[a] else (b, a)
+        d = x[j] - x[i]
+        # first box face crossed along the edge, by coordinates
+        ts = []
+        for ax in range(3):
+            if d[ax] > 0:
+                ts.append((hi[ax] - x[i, ax]) / d[ax])
+            elif d[ax] < 0:
+                ts.append((lo[ax] - x[i, ax]) / d[ax])
+        t = min(t for t in ts if t >= 0)
+        disp[i] += zeta * t * d
+        cnt[i] += 1
+    m = cnt > 0
+    want = x.copy()
+    want[m] += disp[m] / cnt[m, None]
+    assert moved == int(m.sum()) > 10
+    np.testing.assert_allclose(out, want, atol=1e-12)
