@@ -314,6 +314,52 @@ zef_status zef_relabel_boundary(zef_ctx *ctx, const float *nodes, int64_t n_node
                                 int32_t max_passes, const zef_label_opts *opts,
                                 zef_relabel_pass *per_pass, int32_t *passes, int32_t *converged);
 
+/* Taubin smoothing parameters (Sec. 2.2.1; the experiments of the paper use
+   lambda = mu = 0.4). */
+typedef struct zef_smooth_opts {
+    float lambda;       /* forward step, 0 <= lambda < 1 */
+    float mu;           /* backward step, 0 <= mu < 1 */
+    float xi;           /* stop after the first iteration whose forward step
+                           satisfies ||x' - x||_2 / ||x^(0)||_2 <= xi */
+    int32_t max_iters;  /* 1 .. 100000 */
+} zef_smooth_opts;
+
+/* Taubin smoothing of the mesh nodes in place (Sec. 2.2.1, volumetric: the
+   neighbourhood N_i of node i is i itself and every node joined to it by a
+   tet edge).  One iteration: x' = x + lambda L(x), then x'' = x' - mu L(x'),
+   with L(x)_i = sum over j in N_i of (x_j - x_i) / |N_i|, summed in
+   ascending neighbour order in float32 (deterministic); nodes with
+   fixed[i] != 0 (nullable array) do not move.  The iteration loop runs on
+   the device as one CUDA graph with a conditional while-node.
+     nodes      [n_nodes][3] float32, in/out
+     tets       [n_tets][4] int32 node indices
+     fixed      nullable; [n_nodes] uint8
+     iterations nullable out: iterations run
+   nodes, tets and fixed must all be host or all device memory; the call
+   synchronizes.  Errors: ZEF_ERR_INVALID_ARG (parameters, an index outside
+   [0, n_nodes), mixed residency), ZEF_ERR_NOT_READY (host-only context). */
+zef_status zef_taubin_smooth(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets,
+                             int64_t n_tets, const uint8_t *fixed, const zef_smooth_opts *opts,
+                             int32_t *iterations);
+
+/* One inflation of the nodes inside compartment `compartment_id`'s surface S
+   towards S (Sec. 2.2.2).  A mesh edge with one node inside S (Omega > 2 pi)
+   and the other outside crosses S; the inside node i moves by
+   zeta t (x_j - x_i) averaged over its crossing edges (i, j), t the edge
+   parameter of the intersection with S nearest to x_i (float32
+   Moller-Trumbore against S's triangles, inclusive by 2^-20 so that an edge
+   through a shared triangle edge still hits), i.e. by zeta times the
+   distance to S along the unit edge vector.  Every other node keeps its
+   position.
+     nodes  [n_nodes][3] float32, in/out;  tets [n_tets][4] int32
+     zeta   0 <= zeta < 1 (0.05 in the paper's experiments)
+     moved  nullable out: nodes moved
+   nodes and tets must both be host or both device memory; the call
+   synchronizes.  Errors: ZEF_ERR_INVALID_ARG (unknown id, zeta, an index
+   outside [0, n_nodes)), ZEF_ERR_NOT_READY. */
+zef_status zef_inflate(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                       int32_t compartment_id, float zeta, int64_t *moved);
+
 /* Wait for the context's stream and report any error a kernel recorded
    (ZEF_ERR_TIMEOUT, ZEF_ERR_CAPACITY). */
 zef_status zef_synchronize(zef_ctx *ctx);

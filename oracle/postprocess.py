@@ -15,7 +15,9 @@ Readings where the printed formulas are garbled or silent:
     inside S (Omega > 2 pi) and whose other node is outside crosses S; d is
     the distance from the inside node to the intersection of the edge with S
     nearest to it, e the unit vector from the inside node along the edge;
-    each inside node moves by zeta d e averaged over its crossing edges.
+    each inside node moves by zeta d e averaged over its crossing edges; the
+    triangles are closed (an edge through a shared triangle edge or vertex
+    crosses there), tested with a 1e-12 rounding guard.
 """
 from __future__ import annotations
 
@@ -86,7 +88,8 @@ def segment_surface_distance(p, q, verts, tris):
     with np.errstate(divide="ignore", invalid="ignore"):
         bv = (d11 * d20 - d01 * d21) / den2
         bw = (d00 * d21 - d01 * d20) / den2
-    hit = (den != 0) & (t >= 0) & (t <= 1) & (bv >= 0) & (bw >= 0) & (bv + bw <= 1)
+    g = 1e-12   # rounding guard: an edge through a shared triangle edge or vertex still hits
+    hit = (den != 0) & (t >= -g) & (t <= 1 + g) & (bv >= -g) & (bw >= -g) & (bv + bw <= 1 + g)
     if not hit.any():
         return np.inf
     return float(t[hit].min() * np.linalg.norm(d))

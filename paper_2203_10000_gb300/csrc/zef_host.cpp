@@ -234,6 +234,7 @@ void zef_destroy(zef_ctx *ctx) {
   fr(ctx->el_node_labels); fr(ctx->el_masks); fr(ctx->el_tets); fr(ctx->el_labels);
   for (auto &p : ctx->rf_buf) fr(p);
   for (auto &p : ctx->rb_buf) fr(p);
+  for (auto &p : ctx->pp_buf) fr(p);
   if (ctx->rb_exec) cudaGraphExecDestroy(ctx->rb_exec);
   if (ctx->rf_exec) cudaGraphExecDestroy(ctx->rf_exec);
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
@@ -713,6 +714,45 @@ zef_status zef_relabel_boundary(zef_ctx *ctx, const float *nodes, int64_t n_node
   zef_status st = ensure_uploaded(ctx);
   if (st) return st;
   return relabel_run(ctx, nodes, n_nodes, tets, n_tets, node_labels, max_passes, o, per_pass, passes, converged);
+}
+
+zef_status zef_taubin_smooth(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                             const uint8_t *fixed, const zef_smooth_opts *opts, int32_t *iterations) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context");
+  if (!opts || n_nodes < 0 || n_tets < 0 || (n_nodes > 0 && !nodes) || (n_tets > 0 && !tets))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad smoothing arguments");
+  if (n_nodes > ((int64_t)1 << 31) - 1 || n_tets > ((int64_t)1 << 31) - 1)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "too many nodes or tets (max 2^31-1)");
+  if (n_tets > 0 && n_nodes == 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "tets without nodes");
+  if (!(opts->lambda >= 0.f && opts->lambda < 1.f) || !(opts->mu >= 0.f && opts->mu < 1.f) ||
+      !(opts->xi >= 0.f) || opts->max_iters < 1 || opts->max_iters > 100000)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "smoothing parameters out of range");
+  if (iterations) *iterations = 0;
+  if (n_nodes == 0) return ZEF_OK;
+  DeviceGuard g(ctx->device);
+  return taubin_run(ctx, nodes, n_nodes, tets, n_tets, fixed, *opts, iterations);
+}
+
+zef_status zef_inflate(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                       int32_t compartment_id, float zeta, int64_t *moved) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context");
+  if (n_nodes < 0 || n_tets < 0 || (n_nodes > 0 && !nodes) || (n_tets > 0 && !tets))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad inflation arguments");
+  if (n_nodes > ((int64_t)1 << 31) - 1 || n_tets > ((int64_t)1 << 31) - 1)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "too many nodes or tets (max 2^31-1)");
+  if (n_tets > 0 && n_nodes == 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "tets without nodes");
+  if (!(zeta >= 0.f && zeta < 1.f)) return fail(ctx, ZEF_ERR_INVALID_ARG, "zeta must be in [0, 1)");
+  if (moved) *moved = 0;
+  if (n_nodes == 0) return ZEF_OK;
+  DeviceGuard g(ctx->device);
+  zef_status st = ensure_uploaded(ctx);
+  if (st) return st;
+  return inflate_run(ctx, nodes, n_nodes, tets, n_tets, compartment_id, zeta, moved);
 }
 
 zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_label_opts *opts,

@@ -170,6 +170,10 @@ struct zef_ctx {
   int32_t *el_labels = nullptr;
   int64_t el_cap_nodes = 0, el_cap_masks = 0, el_cap_tets = 0, el_cap_labels = 0;
 
+  // post-processing scratch (smoothing, inflation)
+  void *pp_buf[14] = {};
+  size_t pp_cap[14] = {};
+
   // recursive re-labeling scratch and its cached graph
   void *rb_buf[9] = {};
   size_t rb_cap[9] = {};
@@ -218,6 +222,10 @@ zef_status launch_wait_probe(zef_ctx *ctx, int64_t limit_ns);
 zef_status relabel_run(zef_ctx *ctx, const float *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                        int32_t *node_labels, int32_t max_passes, const zef_label_opts &opts,
                        zef_relabel_pass *per_pass, int32_t *passes, int32_t *converged);
+zef_status taubin_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m, const uint8_t *fixed,
+                      const zef_smooth_opts &o, int32_t *iters_out);
+zef_status inflate_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m, int32_t id,
+                       float zeta, int64_t *moved_out);
 zef_status launch_elem_labels(zef_ctx *ctx, const int32_t *tets, int64_t n_tets, int64_t n_nodes,
                               const int32_t *node_labels, const unsigned long long *masks, int32_t *elem);
 zef_status debug_fma_rate(zef_ctx *ctx, int fp64, double *tflops);

@@ -106,6 +106,17 @@ _lib.zef_label_points.restype = ctypes.c_int
 _lib.zef_label_elements.argtypes = [_P, _P, _I64, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                     ctypes.POINTER(LabelStats)]
 _lib.zef_label_elements.restype = ctypes.c_int
+class SmoothOpts(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("mu", ctypes.c_float), ("xi", ctypes.c_float),
+                ("max_iters", ctypes.c_int32)]
+
+
+_lib.zef_taubin_smooth.argtypes = [_P, _P, _I64, _P, _I64, _P, ctypes.POINTER(SmoothOpts), ctypes.POINTER(_I32)]
+_lib.zef_taubin_smooth.restype = ctypes.c_int
+_lib.zef_inflate.argtypes = [_P, _P, _I64, _P, _I64, _I32, ctypes.c_float, ctypes.POINTER(_I64)]
+_lib.zef_inflate.restype = ctypes.c_int
+
+
 class RelabelPass(ctypes.Structure):
     _fields_ = [("evaluated", ctypes.c_int64), ("changed", ctypes.c_int64)]
 
@@ -352,6 +363,47 @@ class Context:
         self._check(_lib.zef_label_elements(self._h, pp, n, tp, m, ep, npp, ctypes.byref(o),
                                             ctypes.byref(st) if stats else None))
         return elem_labels, node_labels, (st.as_dict() if stats else None)
+
+    @staticmethod
+    def _inplace_f32(nodes):
+        if _is_torch(nodes):
+            if nodes.dtype.itemsize != 4 or not nodes.is_contiguous() or nodes.is_floating_point() is False:
+                raise ValueError("nodes must be a contiguous float32 tensor")
+            return nodes.data_ptr()
+        if nodes.dtype != np.float32 or not nodes.flags.c_contiguous:
+            raise ValueError("nodes must be a contiguous float32 array")
+        return nodes.ctypes.data
+
+    def taubin_smooth(self, nodes, tets, lam: float = 0.4, mu: float = 0.4, xi: float = 0.0,
+                      max_iters: int = 10, fixed=None) -> int:
+        """Taubin smoothing of `nodes` in place; returns the iterations run."""
+        xp = self._inplace_f32(nodes)
+        tp, tk, _ = _contig(tets, np.int32, "int32")
+        fp, fk = None, None
+        if fixed is not None:
+            if _is_torch(fixed):
+                fk = fixed.contiguous()
+                fp = fk.data_ptr()
+            else:
+                fk = np.ascontiguousarray(fixed, dtype=np.uint8)
+                fp = fk.ctypes.data
+        n = int(np.prod(nodes.shape)) // 3
+        m = int(np.prod(tk.shape)) // 4
+        o = SmoothOpts(lam, mu, xi, int(max_iters))
+        it = _I32(0)
+        self._check(_lib.zef_taubin_smooth(self._h, xp, n, tp, m, fp, ctypes.byref(o), ctypes.byref(it)))
+        return int(it.value)
+
+    def inflate(self, nodes, tets, compartment_id: int, zeta: float = 0.05) -> int:
+        """One inflation of `nodes` in place towards the compartment's surface;
+        returns the number of nodes moved."""
+        xp = self._inplace_f32(nodes)
+        tp, tk, _ = _contig(tets, np.int32, "int32")
+        n = int(np.prod(nodes.shape)) // 3
+        m = int(np.prod(tk.shape)) // 4
+        moved = _I64(0)
+        self._check(_lib.zef_inflate(self._h, xp, n, tp, m, int(compartment_id), float(zeta), ctypes.byref(moved)))
+        return int(moved.value)
 
     def relabel_boundary(self, nodes, tets, node_labels, max_passes: int = 64,
                          opts: LabelOpts | None = None):
