@@ -25,7 +25,7 @@ PER_FILE = {
     # FP32 hot loop: flush denormals so rsqrtf/__fdividef map to single MUFU ops
     "zef_label.cu": ["-ftz=true", "-Xptxas", "-v"],
 }
-SOURCES = ["zef_host.cpp", "zef_label.cu", "zef_refine.cu", "zef_relabel.cu", "zef_post.cu", "zef_noalloc.cu"]
+SOURCES = ["zef_host.cpp", "zef_tree.cpp", "zef_label.cu", "zef_refine.cu", "zef_relabel.cu", "zef_post.cu", "zef_noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -222,6 +222,8 @@ void zef_destroy(zef_ctx *ctx) {
   };
   fr(ctx->d_entries);
   fr(ctx->d_tris);
+  fr(ctx->d_nodes);
+  fr(ctx->d_ctri);
   fr(ctx->d_comps);
   fr(ctx->d_row_ids);
   fr(ctx->d_lpt);
@@ -455,6 +457,16 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
   ch.tri_off = (int64_t)(ctx->h_tris.size() / 3);
   if (ch.entry_off + ch.entry_cnt > INT32_MAX || ch.tri_off + nt > INT32_MAX)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "total surface size exceeds the library limit");
+  // cap tree (exact far-field replacement of patches, zef_tree.cpp)
+  {
+    const int64_t node_base = (int64_t)ctx->h_nodes.size(), tri_base = (int64_t)ctx->h_ctri.size() / 4;
+    int64_t leaf = 0;
+    build_cap_tree(V.data(), T.data(), nt, node_base, tri_base, ctx->h_nodes, ctx->h_ctri, &ch.cap_root, &leaf);
+    ch.ctri_off = tri_base;
+    ch.ctri_leaf = leaf;
+    if ((int64_t)ctx->h_ctri.size() / 4 > INT32_MAX || (int64_t)ctx->h_nodes.size() > INT32_MAX)
+      return fail(ctx, ZEF_ERR_INVALID_ARG, "total surface size exceeds the library limit");
+  }
   ctx->h_entries.insert(ctx->h_entries.end(), ent.begin(), ent.end());
   for (int64_t t = 0; t < nt; ++t)
     for (int q = 0; q < 3; ++q) {
@@ -844,6 +856,35 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
   for (float4 &t : ts) {
     t.x *= s; t.y *= s; t.z *= s;
   }
+  // cap trees: vertices scale by s, normals and kappa |n| by s^2 (exact)
+  std::vector<CapNode> ns(ctx->h_nodes);
+  for (CapNode &nd : ns)
+    for (int k = 0; k < 3; ++k) {
+      nd.lo[k] *= s;
+      nd.hi[k] *= s;
+    }
+  std::vector<float4> cs(ctx->h_ctri);
+  for (size_t k = 0; k < cs.size(); k += 4) {
+    for (int q = 0; q < 3; ++q) {
+      cs[k + q].x *= s; cs[k + q].y *= s; cs[k + q].z *= s;
+    }
+    cs[k].w *= s2;
+    cs[k + 3].x *= s2; cs[k + 3].y *= s2; cs[k + 3].z *= s2;
+  }
+  if (ctx->d_nodes_cap < (int64_t)ns.size()) {
+    if (ctx->d_nodes) cudaFree(ctx->d_nodes);
+    ctx->d_nodes = nullptr;
+    CK(cudaMalloc(&ctx->d_nodes, std::max<size_t>(ns.size(), 1) * sizeof(CapNode)), "cudaMalloc(cap nodes)");
+    ctx->d_nodes_cap = (int64_t)ns.size();
+  }
+  if (ctx->d_ctri_cap < (int64_t)cs.size()) {
+    if (ctx->d_ctri) cudaFree(ctx->d_ctri);
+    ctx->d_ctri = nullptr;
+    CK(cudaMalloc(&ctx->d_ctri, std::max<size_t>(cs.size(), 1) * sizeof(float4)), "cudaMalloc(cap triangles)");
+    ctx->d_ctri_cap = (int64_t)cs.size();
+  }
+  if (!ns.empty()) CK(cudaMemcpy(ctx->d_nodes, ns.data(), ns.size() * sizeof(CapNode), cudaMemcpyHostToDevice), "upload cap nodes");
+  if (!cs.empty()) CK(cudaMemcpy(ctx->d_ctri, cs.data(), cs.size() * sizeof(float4), cudaMemcpyHostToDevice), "upload cap triangles");
   std::vector<DevComp> dc(C);
   std::vector<int32_t> rows(C), lpt(C);
   for (int i = 0; i < C; ++i) {
@@ -857,6 +898,10 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
     d.entry_cnt = (int32_t)h.entry_cnt;
     d.tri_off = (int32_t)h.tri_off;
     d.tri_cnt = (int32_t)h.nt;
+    d.cap_root = h.cap_root;
+    d.ctri_off = (int32_t)h.ctri_off;
+    d.ctri_leaf = (int32_t)h.ctri_leaf;
+    d.pad_ = 0;
     d.id = h.id;
     d.row = -1;
     for (int r = 0; r < C; ++r)
@@ -928,6 +973,35 @@ extern "C" zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const f
   zef_status st = launch_debug_half_angle(ctx, y, x, out, n);
   if (st) return st;
   return zef_synchronize(ctx);
+}
+
+extern "C" zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int64_t *n_nodes, int64_t *n_tris,
+                                         float *boxes, int32_t *links, float *tris) {
+  if (!ctx || index < 0 || index >= (int32_t)ctx->comps.size() || !n_nodes || !n_tris) return ZEF_ERR_INVALID_ARG;
+  const CompHost &c = ctx->comps[(size_t)index];
+  const bool last = index + 1 == (int32_t)ctx->comps.size();
+  const int64_t node_end = last ? (int64_t)ctx->h_nodes.size() : ctx->comps[(size_t)index + 1].cap_root;
+  const int64_t tri_end = last ? (int64_t)ctx->h_ctri.size() / 4 : ctx->comps[(size_t)index + 1].ctri_off;
+  *n_nodes = node_end - c.cap_root;
+  *n_tris = tri_end - c.ctri_off;
+  for (int64_t k = 0; k < *n_nodes; ++k) {
+    const CapNode &nd = ctx->h_nodes[(size_t)(c.cap_root + k)];
+    if (boxes)
+      for (int d = 0; d < 3; ++d) {
+        boxes[6 * k + d] = nd.lo[d];
+        boxes[6 * k + 3 + d] = nd.hi[d];
+      }
+    if (links) {
+      links[6 * k + 0] = nd.left < 0 ? -1 : nd.left - c.cap_root;
+      links[6 * k + 1] = nd.right < 0 ? -1 : nd.right - c.cap_root;
+      links[6 * k + 2] = nd.tri_begin - (int32_t)c.ctri_off;
+      links[6 * k + 3] = nd.tri_cnt;
+      links[6 * k + 4] = nd.cap_begin - (int32_t)c.ctri_off;
+      links[6 * k + 5] = nd.cap_cnt;
+    }
+  }
+  if (tris) std::memcpy(tris, ctx->h_ctri.data() + 4 * c.ctri_off, (size_t)*n_tris * 4 * sizeof(float4));
+  return ZEF_OK;
 }
 
 extern "C" zef_status zef_debug_fma_rate(zef_ctx *ctx, int32_t fp64, double *tflops) {

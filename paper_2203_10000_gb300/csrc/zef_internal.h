@@ -34,7 +34,24 @@ struct __align__(16) DevComp {
   int32_t tri_cnt;
   int32_t id;         // user id
   int32_t row;        // priority row (0 = highest priority)
+  int32_t cap_root;   // root of the cap tree (zef_tree.cpp)
+  int32_t ctri_off;   // first triangle of the compartment's cap-tree block
+  int32_t ctri_leaf;  // triangles of its leaves (the caps follow)
+  int32_t pad_;
 };
+
+// Node of a compartment's cap tree (zef_tree.cpp): the box of the patch's
+// triangles and its cap apex, children (-1 for a leaf), the leaf's triangles
+// and the node's cap triangles in the cap-tree triangle array.
+struct CapNode {
+  float lo[3], hi[3];
+  int32_t left, right;
+  int32_t tri_begin, tri_cnt;
+  int32_t cap_begin, cap_cnt;
+};
+constexpr int kCapLeaf = 64;  // triangles per leaf patch
+void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_base, int64_t tri_base,
+                    std::vector<CapNode> &nodes, std::vector<float4> &tri, int32_t *root, int64_t *leaf_tris);
 
 // Device status word bits (ctx->d_status[0]); [1] holds detail.
 enum : uint32_t {
@@ -63,6 +80,8 @@ struct CompHost {
   int64_t nv, nt;
   float lo[3], hi[3];
   int64_t entry_off, entry_cnt, tri_off, nstrips;
+  int32_t cap_root;                // cap tree: root node, triangle block, leaf triangles
+  int64_t ctri_off, ctri_leaf;
   double dop[kDop];  // max over the vertices of d_k . v (unscaled coordinates)
 };
 
@@ -140,6 +159,8 @@ struct zef_ctx {
   std::vector<int32_t> priority;      // ids, highest priority first
   std::vector<zef::Entry> h_entries;
   std::vector<float4> h_tris;         // 3 per triangle (w unused)
+  std::vector<zef::CapNode> h_nodes;  // cap trees of all compartments
+  std::vector<float4> h_ctri;         // cap-tree triangles, 4 float4 each
 
   bool dirty = true;
   // power of two applied to every coordinate on the device so that the
@@ -152,6 +173,9 @@ struct zef_ctx {
   int32_t *d_row_ids = nullptr;       // priority row -> id
   int32_t *d_lpt = nullptr;           // LPT rank -> comp index
   float *d_dop = nullptr;             // [C][kDop] hull support bounds (scaled coordinates)
+  zef::CapNode *d_nodes = nullptr;    // cap trees (scaled)
+  float4 *d_ctri = nullptr;           // cap-tree triangles (scaled)
+  int64_t d_nodes_cap = 0, d_ctri_cap = 0;
   int64_t d_entries_cap = 0, d_tris_cap = 0;
 
   uint32_t *d_status = nullptr;       // [2]

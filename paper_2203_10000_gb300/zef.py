@@ -142,6 +142,8 @@ _lib.zef_debug_strip_entries.argtypes = [_P, _I32, _P, _I64, ctypes.POINTER(_I64
 _lib.zef_debug_strip_entries.restype = ctypes.c_int
 _lib.zef_debug_wait_probe.argtypes = [_P, _I64]
 _lib.zef_debug_wait_probe.restype = ctypes.c_int
+_lib.zef_debug_cap_tree.argtypes = [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P, _P, _P]
+_lib.zef_debug_cap_tree.restype = ctypes.c_int
 _lib.zef_debug_fma_rate.argtypes = [_P, _I32, ctypes.POINTER(ctypes.c_double)]
 _lib.zef_debug_fma_rate.restype = ctypes.c_int
 _lib.zef_debug_half_angle.argtypes = [_P, _P, _P, _P, _I64]
@@ -280,6 +282,19 @@ class Context:
         """Run the bounded-wait probe; returns the status code (expected
         ZEF_ERR_TIMEOUT) without raising."""
         return int(_lib.zef_debug_wait_probe(self._h, int(limit_ns)))
+
+    def cap_tree(self, index: int):
+        """(boxes float32 (n, 6), links int32 (n, 6), triangles float32 (m, 16))
+        of compartment `index`'s cap tree (diagnostics)."""
+        nn, nt = _I64(0), _I64(0)
+        self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(nt),
+                                            None, None, None))
+        boxes = np.empty((nn.value, 6), np.float32)
+        links = np.empty((nn.value, 6), np.int32)
+        tris = np.empty((nt.value, 16), np.float32)
+        self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(nt),
+                                            boxes.ctypes.data, links.ctypes.data, tris.ctypes.data))
+        return boxes, links, tris
 
     def fma_rate(self, fp64: bool = False) -> float:
         """Measured FMA throughput of the device in TFLOP/s (diagnostics)."""

@@ -180,3 +180,58 @@ def test_strip_efficiency_head_surfaces(zef):
         n_ent, n_strips = ctx.strip_stats(i)
         # entries = T + 2 strips + padding; overhead under 10 %
         assert n_ent < 1.10 * s.ntris, (s.name, n_ent, s.ntris, n_strips)
+
+
+def _tree_omega(oracle_mod, p, tri16):
+    v = tri16[:, [0, 1, 2, 4, 5, 6, 8, 9, 10]].reshape(-1, 3).astype(np.float64)
+    t = np.arange(v.shape[0], dtype=np.int32).reshape(-1, 3)
+    return oracle_mod.solid_angle(p, v, t) if t.size else np.zeros(p.shape[0])
+
+
+@pytest.mark.parametrize("which", ["sphere", "torus", "ellipsoid"])
+def test_cap_tree_identity(zef, oracle_mod, which):
+    """Every node of the library's cap tree: outside the node's box its
+    caps' solid angle equals that of its leaf triangles (FP64 oracle), the
+    leaves cover every triangle once, and the root (the closed surface) has
+    no cap."""
+    if which == "sphere":
+        s = zs.config0().surfaces[0]
+        v, t = s.verts, s.tris
+    elif which == "torus":
+        v, t = zs.torus(10.0, 3.0, 40, 18, seed=1, amp=0.5)
+    else:
+        v, t = zs.perturbed_ellipsoid(16, (9.0, 7.0, 5.0), amp=1.0, seed=3)
+    ctx = _host_ctx(zef)
+    ctx.add_compartment(1, v, t)
+    boxes, links, tris = ctx.cap_tree(0)
+    assert links[0, 5] == 0                                    # root: closed, no cap
+    leaves = links[links[:, 0] < 0]
+    assert leaves[:, 3].sum() == t.shape[0] and leaves[:, 3].max() <= 64
+    rng = np.random.default_rng(7)
+    checked = 0
+
+    def leaf_tris(k):
+        if links[k, 0] < 0:
+            return [tris[links[k, 2]:links[k, 2] + links[k, 3]]]
+        return leaf_tris(links[k, 0]) + leaf_tris(links[k, 1])
+
+    for k in rng.choice(len(boxes), size=min(40, len(boxes)), replace=False):
+        lo, hi = boxes[k, :3].astype(np.float64), boxes[k, 3:].astype(np.float64)
+        if links[k, 5] == 0:
+            continue
+        ext = hi - lo
+        # points just outside the box on every side, and farther away
+        pts = np.concatenate([lo + rng.uniform(0, 1, (8, 3)) * ext + np.eye(3)[rng.integers(0, 3, 8)] * ext * 1.01,
+                              lo - rng.uniform(0.01, 3.0, (8, 3)) * ext.max()])
+        outside = np.any((pts < lo) | (pts > hi), axis=1)
+        pts = pts[outside]
+        patch = np.concatenate(leaf_tris(k))
+        cap = tris[links[k, 4]:links[k, 4] + links[k, 5]]
+        a = _tree_omega(oracle_mod, pts, patch)
+        b = _tree_omega(oracle_mod, pts, cap)
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-9)
+        checked += 1
+    assert checked >= 10
+    # normals and kappa terms as documented
+    n = np.cross(tris[:, 4:7].astype(np.float64) - tris[:, 0:3], tris[:, 8:11].astype(np.float64) - tris[:, 0:3])
+    np.testing.assert_allclose(tris[:, 12:15], n, rtol=1e-5, atol=1e-6 * np.abs(n).max())
