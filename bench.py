@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-refine", action="store_true", help="skip the refine-and-relabel measurement")
     ap.add_argument("--no-compare", action="store_true", help="skip the tile-coherence-off comparison step")
     ap.add_argument("--shape", default="", help="threads,ppt override")
-    ap.add_argument("--kernel", type=int, default=0, help="FP32 kernel form (0 grouped, 1 per triangle)")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="FP32 kernel form (0 cap trees, 1 strips with grouped products, 2 strips per triangle)")
     return ap.parse_args()
 
 

@@ -83,8 +83,12 @@ typedef struct zef_label_opts {
        Default 1e-3 (<= 0 selects the default). */
     float margin;
     /* A pair is also uncertain when Omega32 is farther than winding_tol from
-       the nearest multiple of 4 pi (Omega of a closed surface at a point off
-       the surface is 4 pi times an integer).  Default 4e-6. */
+       the nearest multiple of 4 pi k (Omega of a closed surface at a point
+       off the surface is 4 pi times the winding number k).  A pair that is
+       certain reports Omega = 4 pi k exactly.  Default 1e-4: the rounding
+       error of an FP32 sum stays orders of magnitude below 2 pi - winding_tol,
+       and the errors of about 4 pi that a wrong sign of a near-zero N can
+       cause are caught by the conditioning test. */
     float winding_tol;
     /* zef_precision */
     int32_t precision;
@@ -92,9 +96,12 @@ typedef struct zef_label_opts {
        autotuned choice.  Valid: threads 128 or 256, points 2 or 4. */
     int32_t block_threads;
     int32_t points_per_thread;
-    /* Form of the FP32 kernel: 0 = one atan2 per group of four triangles,
-       taken of the product of their (D + iN) factors with 2 pi wraps counted
-       exactly (default); 1 = one atan2 per triangle. */
+    /* Form of the FP32 kernel: 0 = the whole surface as triangle strips, one
+       atan2 per group of four triangles taken of the product of their
+       (D + iN) factors with 2 pi wraps counted exactly; 1 = strips, one atan2
+       per triangle; 2 = cap trees (zef_tree.cpp): for each tile of points the
+       patches whose box misses the tile are replaced by their caps, exact
+       since outside that box a cap subtends its patch (default). */
     int32_t kernel;
     /* ZEF_NO_TILE_COHERENCE or 0 (see below). */
     uint32_t flags;
@@ -226,10 +233,13 @@ zef_status zef_compartment_priority(zef_ctx *ctx, const int32_t *ids, int32_t n)
              whose surface encloses the point (Omega > 2 pi); 0 when none;
              -1 for a point with a non-finite coordinate
      omega   nullable; [C][n] float32 out, row r = the r-th compartment in
-             priority order: the solid angle Omega in steradians (0 exactly
-             where the point is outside the compartment's bounding box or
-             convex-hull bound, 4 pi k exactly for the points of a tile the
-             surface provably does not cross; NaN for non-finite points)
+             priority order: the solid angle Omega in steradians: 4 pi k
+             exactly wherever the winding number k is certified (0 outside
+             the compartment's bounding box or convex-hull bound, the tile's
+             k where the surface provably does not cross a tile, the FP32
+             sum's k within winding_tol), the FP64 sum for the pairs
+             re-evaluated in FP64, the FP32 sum with ZEF_FP32_ONLY for
+             uncertain pairs; NaN for non-finite points
      opts    nullable = defaults;  stats nullable (non-NULL synchronizes) */
 zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
                             float *omega, const zef_label_opts *opts, zef_label_stats *stats);

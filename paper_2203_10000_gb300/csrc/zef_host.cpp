@@ -599,7 +599,7 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
   zef_label_opts o;
   if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
   fill_default_opts(&o);
-  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
+  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
@@ -715,7 +715,7 @@ zef_status zef_relabel_boundary(zef_ctx *ctx, const float *nodes, int64_t n_node
   zef_label_opts o;
   if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
   fill_default_opts(&o);
-  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
+  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
@@ -782,7 +782,7 @@ zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, 
   zef_label_opts o;
   if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
   fill_default_opts(&o);
-  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
+  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
@@ -929,6 +929,7 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
   CK(cudaMemcpy(ctx->d_row_ids, rows.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice), "upload rows");
   CK(cudaMemcpy(ctx->d_lpt, lpt.data(), C * sizeof(int32_t), cudaMemcpyHostToDevice), "upload lpt");
   ctx->dirty = false;
+  ++ctx->gen;
   return ZEF_OK;
 }
 

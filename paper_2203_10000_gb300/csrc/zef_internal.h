@@ -140,6 +140,10 @@ enum Counter {
   CNT_COUNT_ = 32
 };
 
+// zef_label_opts.kernel -> kernel template form: 0 (default) cap trees = 2,
+// 1 strips with grouped products = 0, 2 strips with one atan2 per triangle = 1
+inline int kernel_variant(int kernel) { return kernel == 0 ? 2 : kernel - 1; }
+
 struct LaunchShape {
   int threads;
   int ppt;
@@ -163,6 +167,7 @@ struct zef_ctx {
   std::vector<float4> h_ctri;         // cap-tree triangles, 4 float4 each
 
   bool dirty = true;
+  uint64_t gen = 0;   // upload generation: cached graphs keyed on it see every change of the surfaces
   // power of two applied to every coordinate on the device so that the
   // registered surfaces fit in [-64, 64]^3 (exact; solid angles are scale
   // invariant); keeps products of four (D, N) factors far from overflow

@@ -37,7 +37,7 @@
 //
 // A (point, compartment) pair is sent to the FP64 re-evaluation when
 //   |Omega32 - 2 pi| < margin                (the stated margin), or
-//   Omega32 is farther than winding_tol from 4 pi Z (the closed-surface
+//   Omega32 is farther than winding_tol (1e-4) from 4 pi Z (the closed-surface
 //      invariant; catches FP32 errors of any size except near 4 pi k), or
 //   some triangle had max(|N|, D) < kappa |n| r_c: the point lies within a
 //      relative distance kappa of that triangle's plane in a position where
@@ -100,6 +100,19 @@ __device__ __forceinline__ void fence_barrier_init() {
 __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Arm the barrier with the byte count of several copies (one arrival) ...
+__device__ __forceinline__ void tma_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// ... then start each of them.
+__device__ __forceinline__ void tma_copy_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           smem_u32(dst)),
@@ -275,6 +288,8 @@ struct LabelArgs {
   int coherence;  // tile representatives allowed
   int early;      // priority early exit: a point certainly inside needs no later compartment
   unsigned long long *masks_out;  // nullable: inside bits per point in the caller's order
+  const CapNode *nodes;  // cap trees
+  const float4 *ctri;    // cap-tree triangles, 4 float4 each
 };
 
 // Classification of one (point, compartment) pair after the FP32 sum:
@@ -327,9 +342,13 @@ __device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp
     const bool unc = !(bad > 0.f) || !(dist <= a.winding_tol) || !(fabsf(omega - kTwoPi) >= a.margin);
     if (unc && !a.fp32_only) {
       atomicOr(a.unc_mask + i, bit);
-    } else if (omega > kTwoPi) {
-      atomicOr(a.in_mask + i, bit);
-      inside = true;
+    } else {
+      // a certified winding number K + k: Omega is exactly 4 pi (K + k)
+      if (!unc) omega = kFourPi * ((float)K + k);
+      if (omega > kTwoPi) {
+        atomicOr(a.in_mask + i, bit);
+        inside = true;
+      }
     }
   }
   if (a.omega) a.omega[(int64_t)c.row * a.omega_ld + a.perm[i]] = omega;
@@ -610,6 +629,267 @@ __device__ __forceinline__ bool stream_sums(const LabelArgs &a, const DevComp *c
   return true;
 }
 
+// ------------------------------------------------------------------ cap trees (kernel form 2)
+// For a box of points, the triangles that stand for a compartment's surface:
+// a depth-first walk of its cap tree emits the cap of every node whose box
+// misses the point box (outside that box the cap subtends the node's patch
+// exactly) and the triangles of every leaf whose box meets it.  The result
+// is a list of ranges of the cap-tree triangle array (contiguous leaves
+// merged); more than kMaxRanges ranges fall back to all leaf triangles.
+constexpr int kMaxRanges = 192;
+
+__device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb, int2 *out, int *total) {
+  int stack[48];
+  int sp = 0, n = 0, tot = 0;
+  stack[sp++] = __ldg(&cp->cap_root);
+  while (sp > 0) {
+    const CapNode nd = a.nodes[stack[--sp]];
+    const bool far = nd.hi[0] < wb[0] || nd.lo[0] > wb[3] || nd.hi[1] < wb[1] || nd.lo[1] > wb[4] ||
+                     nd.hi[2] < wb[2] || nd.lo[2] > wb[5];
+    int b, c;
+    if (far) {
+      b = nd.cap_begin;
+      c = nd.cap_cnt;
+    } else if (nd.left < 0) {
+      b = nd.tri_begin;
+      c = nd.tri_cnt;
+    } else {
+      if (sp + 2 > 48) {  // deeper than any tree of 2^28 triangles: cannot happen
+        n = -1;
+        break;
+      }
+      stack[sp++] = nd.right;
+      stack[sp++] = nd.left;
+      continue;
+    }
+    if (c <= 0) continue;
+    tot += c;
+    if (n > 0 && out[n - 1].x + out[n - 1].y == b) {
+      out[n - 1].y += c;
+    } else if (n < kMaxRanges) {
+      out[n++] = make_int2(b, c);
+    } else {
+      n = -1;
+      break;
+    }
+  }
+  if (n < 0) {  // every leaf triangle: the compartment's own triangles
+    out[0] = make_int2(__ldg(&cp->ctri_off), __ldg(&cp->ctri_leaf));
+    n = 1;
+    tot = out[0].y;
+  }
+  *total = tot;
+  return n;
+}
+
+// Position of flattened triangle j of a range list; the cursor (range r,
+// first flattened index of r) only moves forward.
+__device__ __forceinline__ int range_tri(const int2 *rng, int &r, int &rb, int j) {
+  while (j >= rb + rng[r].y) {
+    rb += rng[r].y;
+    ++r;
+  }
+  return rng[r].x + (j - rb);
+}
+
+// Van Oosterom-Strackee half angle of a stored triangle (A, B, C, n) seen
+// from r: N = R_A . n, D = r_A r_B r_C + (R_A . R_B) r_C + (R_A . R_C) r_B +
+// (R_B . R_C) r_A; bad = min(bad, max(|N|, D) - kappa |n| r_A).
+__device__ __forceinline__ void tri_nd(float px, float py, float pz, float4 A, float4 B, float4 C, float4 nn,
+                                       float &N, float &D, float &bad) {
+  const float ax = A.x - px, ay = A.y - py, az = A.z - pz;
+  const float bx = B.x - px, by = B.y - py, bz = B.z - pz;
+  const float cx = C.x - px, cy = C.y - py, cz = C.z - pz;
+  const float qa = fmaf(ax, ax, fmaf(ay, ay, az * az));
+  const float qb = fmaf(bx, bx, fmaf(by, by, bz * bz));
+  const float qc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  const float ra = qa * rsqrtf(qa), rb = qb * rsqrtf(qb), rc = qc * rsqrtf(qc);
+  N = fmaf(ax, nn.x, fmaf(ay, nn.y, az * nn.z));
+  const float dab = fmaf(ax, bx, fmaf(ay, by, az * bz));
+  const float dac = fmaf(ax, cx, fmaf(ay, cy, az * cz));
+  const float dbc = fmaf(bx, cx, fmaf(by, cy, bz * cz));
+  D = fmaf(ra * rb, rc, fmaf(dab, rc, fmaf(dac, rb, dbc * ra)));
+  bad = fminf(bad, fmaf(-A.w, ra, fmaxf(fabsf(N), D)));
+}
+
+// rep_pass over a range list (flattened triangles from 0)
+__device__ __forceinline__ bool rep_pass_caps(const LabelArgs &a, const int2 *rng, int total, const float *wb,
+                                              float rx, float ry, float rz, int lane, int *k, int *t_hit) {
+  float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+  if (wb) {
+    lx = wb[0]; ly = wb[1]; lz = wb[2]; hx = wb[3]; hy = wb[4]; hz = wb[5];
+  }
+  *t_hit = -1;
+  float sum = 0.f, comp = 0.f, bad = __int_as_float(0x7f800000);
+  int r = 0, rb = 0;
+  for (int t0 = 0; t0 < total; t0 += 32) {
+    const int j = t0 + lane;
+    bool ov = false;
+    float term = 0.f;
+    if (j < total) {
+      const float4 *T = a.ctri + 4 * (int64_t)range_tri(rng, r, rb, j);
+      const float4 A = T[0], B = T[1], C = T[2], nn = T[3];
+      if (wb)
+        ov = !(fmaxf(A.x, fmaxf(B.x, C.x)) < lx || fminf(A.x, fminf(B.x, C.x)) > hx ||
+               fmaxf(A.y, fmaxf(B.y, C.y)) < ly || fminf(A.y, fminf(B.y, C.y)) > hy ||
+               fmaxf(A.z, fmaxf(B.z, C.z)) < lz || fminf(A.z, fminf(B.z, C.z)) > hz);
+      float N, D;
+      tri_nd(rx, ry, rz, A, B, C, nn, N, D, bad);
+      term = half_angle(N, D);
+    }
+    if (wb && __any_sync(0xffffffffu, ov)) {
+      *t_hit = t0;
+      return false;
+    }
+    const float y = term - comp;
+    const float tt = sum + y;
+    comp = (tt - sum) - y;
+    sum = tt;
+  }
+  return rep_certain(a, sum, -comp, bad, k);
+}
+
+template <int NG>
+__device__ __forceinline__ uint32_t touched_groups_caps(const LabelArgs &a, const int2 *rng, int total,
+                                                        const float *wb, const float (*gb)[6], uint32_t need,
+                                                        int t_begin, int lane) {
+  uint32_t hit = 0;
+  int r = 0, rb = 0;
+  for (int t0 = t_begin; t0 < total; t0 += 32) {
+    const int j = t0 + lane;
+    if (j < total) {
+      const float4 *T = a.ctri + 4 * (int64_t)range_tri(rng, r, rb, j);
+      const float4 A = T[0], B = T[1], C = T[2];
+      const float ux = fmaxf(A.x, fmaxf(B.x, C.x)), lx = fminf(A.x, fminf(B.x, C.x));
+      const float uy = fmaxf(A.y, fmaxf(B.y, C.y)), ly = fminf(A.y, fminf(B.y, C.y));
+      const float uz = fmaxf(A.z, fmaxf(B.z, C.z)), lz = fminf(A.z, fminf(B.z, C.z));
+      if (!(ux < wb[0] || lx > wb[3] || uy < wb[1] || ly > wb[4] || uz < wb[2] || lz > wb[5])) {
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (((need >> g) & 1u) && !(ux < gb[g][0] || lx > gb[g][3] || uy < gb[g][1] || ly > gb[g][4] ||
+                                      uz < gb[g][2] || lz > gb[g][5]))
+            hit |= 1u << g;
+      }
+    }
+    hit = __reduce_or_sync(0xffffffffu, hit);
+    if (hit == need) break;
+  }
+  return hit;
+}
+
+template <int NG>
+__device__ __forceinline__ uint32_t group_reps_caps(const LabelArgs &a, const int2 *rng, int total, uint32_t u,
+                                                    const float (*rp)[3], int lane, int (&k)[NG]) {
+  float sum[NG], comp[NG], bad[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    sum[g] = comp[g] = 0.f;
+    bad[g] = __int_as_float(0x7f800000);
+  }
+  int r = 0, rb = 0;
+  for (int j = lane; j < total; j += 32) {
+    const float4 *T = a.ctri + 4 * (int64_t)range_tri(rng, r, rb, j);
+    const float4 A = T[0], B = T[1], C = T[2], nn = T[3];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+      if ((u >> g) & 1u) {
+        float N, D;
+        tri_nd(rp[g][0], rp[g][1], rp[g][2], A, B, C, nn, N, D, bad[g]);
+        const float y = half_angle(N, D) - comp[g];
+        const float tt = sum[g] + y;
+        comp[g] = (tt - sum[g]) - y;
+        sum[g] = tt;
+      }
+  }
+  uint32_t certain = 0;
+#pragma unroll
+  for (int g = 0; g < NG; ++g)
+    if (((u >> g) & 1u) && rep_certain(a, sum[g], -comp[g], bad[g], &k[g])) certain |= 1u << g;
+  return certain;
+}
+
+// Point-by-point sums over a range list: chunks of kCapChunk triangles (4 KB)
+// gathered into the warp's double buffer by one or more bulk copies on one
+// mbarrier; every lane multiplies the (D + i N) factors of four consecutive
+// triangles with wrap counting (missing ones are the identity) and takes one
+// atan2 per four, the group sums Kahan-compensated every 16 triangles.
+constexpr int kCapChunk = 64;
+
+template <int NA>
+__device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 *rng, int total, float4 *wbuf,
+                                                 uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane,
+                                                 PState (&st)[NA]) {
+  const int nchunks = (total + kCapChunk - 1) / kCapChunk;
+  int fr = 0, fb = 0;  // lane 0's fill cursor over the ranges
+  auto fill = [&](int ch, int b) {
+    const int j0 = ch * kCapChunk, j1 = min(total, j0 + kCapChunk);
+    tma_expect(&bar[b], (uint32_t)(j1 - j0) * 64u);
+    int j = j0;
+    while (j < j1) {
+      while (j >= fb + rng[fr].y) {
+        fb += rng[fr].y;
+        ++fr;
+      }
+      const int take = min(j1 - j, fb + rng[fr].y - j);
+      tma_copy_1d(wbuf + b * 4 * kCapChunk + 4 * (j - j0), a.ctri + 4 * (int64_t)(rng[fr].x + (j - fb)),
+                  (uint32_t)take * 64u, &bar[b]);
+      j += take;
+    }
+  };
+  if (lane == 0) {
+    if (nchunks > 0) fill(0, 0);
+    if (nchunks > 1) fill(1, 1);
+  }
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    st[q].grp = st[q].sum = st[q].comp = 0.f;
+    st[q].bad = __int_as_float(0x7f800000);
+    st[q].kp = st[q].kn = 0u;
+  }
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int b = ch & 1;
+    const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
+    if (__any_sync(0xffffffffu, !ok)) return false;
+    if (b) ph1 ^= 1; else ph0 ^= 1;
+    const float4 *E = wbuf + b * 4 * kCapChunk;
+    const int cnt = min(kCapChunk, total - ch * kCapChunk);
+    for (int g = 0; g < cnt; g += kGroup) {
+#pragma unroll 1
+      for (int j = g; j < min(cnt, g + kGroup); j += 4) {
+        float R[NA], I[NA];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (j + k < cnt) {
+            const float4 *T = E + 4 * (j + k);
+            const float4 A = T[0], B = T[1], C = T[2], nn = T[3];
+#pragma unroll
+            for (int q = 0; q < NA; ++q) {
+              float N, D;
+              tri_nd(st[q].px, st[q].py, st[q].pz, A, B, C, nn, N, D, st[q].bad);
+              if (k == 0) {
+                R[q] = D;
+                I[q] = N;
+              } else {
+                float cr, ci;
+                cmul_wrap(R[q], I[q], D, N, cr, ci, st[q].kp, st[q].kn);
+                R[q] = cr;
+                I[q] = ci;
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NA; ++q) st[q].grp += half_angle(I[q], R[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NA; ++q) kahan_flush(st[q]);
+    }
+    __syncwarp();  // every lane is done with buffer b before it is refilled
+    if (lane == 0 && ch + 2 < nchunks) fill(ch + 2, b);
+  }
+  return true;
+}
+
 // Point-by-point evaluation of the groups in `act` (m of them), packed two
 // per slot of 32 lanes (NA = ceil(m / 2) slots): slot j holds the groups at
 // positions 2j (lanes 0-15) and 2j + 1 (lanes 16-31) of the ascending list of
@@ -619,7 +899,8 @@ __device__ __forceinline__ bool stream_sums(const LabelArgs &a, const DevComp *c
 template <int NA, int V, int P>
 __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, const float *thr, Entry *wbuf,
                                             uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane, int base, int n,
-                                            uint32_t act, uint32_t list, int m, uint32_t &done) {
+                                            uint32_t act, uint32_t list, int m, uint32_t &done, const int2 *rng,
+                                            int rtotal) {
   PState st[NA];
   int idx[NA];
   const int half = lane >> 4;
@@ -635,7 +916,12 @@ __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, 
     st[j].pz = p.z;
     idx[j] = (valid && finite3(p.x, p.y, p.z)) ? i : -1;
   }
-  if (!stream_sums<NA, V>(a, cp, wbuf, bar, ph0, ph1, lane, st)) return false;
+  if constexpr (V == 2) {
+    if (!stream_sums_caps<NA>(a, rng, rtotal, reinterpret_cast<float4 *>(wbuf), bar, ph0, ph1, lane, st))
+      return false;
+  } else {
+    if (!stream_sums<NA, V>(a, cp, wbuf, bar, ph0, ph1, lane, st)) return false;
+  }
   const DevComp c = *cp;
   uint32_t in_bits[NA];
   int evaluated = 0;
@@ -663,7 +949,8 @@ __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, 
     }
   }
   if (lane == 0)
-    atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), (unsigned long long)evaluated * c.tri_cnt);
+    atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL),
+              (unsigned long long)evaluated * (V == 2 ? rtotal : c.tri_cnt));
   return true;
 }
 
@@ -685,6 +972,9 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
   __shared__ float s_wbox[NW][6];
   __shared__ float s_gbox[NW][NG][6];
   __shared__ float s_rep[NW][NG][3];
+  constexpr int RN = V == 2 ? kMaxRanges : 1;
+  __shared__ int2 s_rng[NW][RN];   // form 2: the tile's range list of the compartment
+  __shared__ int s_rtot[NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, half = lane >> 4;
   Entry *wbuf = reinterpret_cast<Entry *>(smem_raw) + wid * 2 * kWChunk;
   uint64_t *bar = bars[wid];
@@ -765,6 +1055,17 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         if (early) break;  // every point decided: no later compartment matters
         continue;          // no usable point in the tile
       }
+      int rtotal = 0;  // form 2: triangles standing for the surface near this tile
+      if constexpr (V == 2) {
+        if (lane == 0) {
+          int tot = 0;
+          cap_ranges(a, cp, s_wbox[wid], s_rng[wid], &tot);
+          s_rtot[wid] = tot;
+        }
+        __syncwarp();
+        rtotal = s_rtot[wid];
+      }
+      const unsigned long long surf = V == 2 ? (unsigned long long)rtotal : (unsigned long long)__ldg(&cp->tri_cnt);
       uint32_t coh = 0;  // groups whose points take a representative's winding number
       int kg[NG];
 #pragma unroll
@@ -787,16 +1088,26 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         const float rx = rp.x, ry = rp.y, rz = rp.z;
         int k_t = 0, t_hit = -1;
         unsigned long long reps = 0;
-        if (rep_pass(a, cp, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit)) {
+        bool cert;
+        if constexpr (V == 2)
+          cert = rep_pass_caps(a, s_rng[wid], rtotal, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit);
+        else
+          cert = rep_pass(a, cp, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit);
+        if (cert) {
           coh = need;
 #pragma unroll
           for (int g = 0; g < NG; ++g) kg[g] = k_t;
-          reps += __ldg(&cp->tri_cnt);
+          reps += surf;
         } else if (t_hit < 0) {
-          reps += __ldg(&cp->tri_cnt);  // completed, but the representative is uncertain
+          reps += surf;  // completed, but the representative is uncertain
         } else {
           reps += t_hit;
-          uint32_t untouched = need & ~touched_groups<NG>(a, cp, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
+          uint32_t touched;
+          if constexpr (V == 2)
+            touched = touched_groups_caps<NG>(a, s_rng[wid], rtotal, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
+          else
+            touched = touched_groups<NG>(a, cp, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
+          uint32_t untouched = need & ~touched;
           // an odd number of touched groups leaves half a slot of lanes free:
           // one untouched group is evaluated there instead of by its
           // representative
@@ -819,13 +1130,17 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
             }
             __syncwarp();
             int kk[NG];
-            const uint32_t cert = group_reps<NG>(a, cp, untouched, s_rep[wid], lane, kk);
+            uint32_t gcert;
+            if constexpr (V == 2)
+              gcert = group_reps_caps<NG>(a, s_rng[wid], rtotal, untouched, s_rep[wid], lane, kk);
+            else
+              gcert = group_reps<NG>(a, cp, untouched, s_rep[wid], lane, kk);
             __syncwarp();
 #pragma unroll
             for (int g = 0; g < NG; ++g)
-              if ((cert >> g) & 1u) kg[g] = kk[g];
-            coh |= cert;
-            reps += (unsigned long long)__popc(untouched) * __ldg(&cp->tri_cnt);
+              if ((gcert >> g) & 1u) kg[g] = kk[g];
+            coh |= gcert;
+            reps += (unsigned long long)__popc(untouched) * surf;
           }
         }
         if (coh) {
@@ -860,10 +1175,10 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         if ((act >> g) & 1u) list |= (uint32_t)g << (4 * m++);
       bool ok = true;
       switch ((m + 1) >> 1) {
-        case 1: ok = eval_groups<1, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
-        case 2: ok = eval_groups<(P >= 2 ? 2 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
-        case 3: ok = eval_groups<(P >= 3 ? 3 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
-        default: ok = eval_groups<P, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done); break;
+        case 1: ok = eval_groups<1, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
+        case 2: ok = eval_groups<(P >= 2 ? 2 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
+        case 3: ok = eval_groups<(P >= 3 ? 3 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
+        default: ok = eval_groups<P, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
       }
       if (!ok) {
         timed_out = true;
@@ -1068,6 +1383,98 @@ __device__ void strip_half_angle64(const Entry *E, int s, int e, double px, doub
   }
   *sum = acc;
   *wraps = K;
+}
+
+// FP64 re-evaluation over the cap tree: one block per uncertain pair, the
+// point's own range list (the tree walked for the point's zero-size box, so
+// leaves near the point and caps of every farther node), threads split the
+// triangles, plain FP64 Van Oosterom-Strackee terms with the exact triple
+// product, fixed-order block reduction.  Outside a node's box its cap
+// subtends its patch exactly, so the sum is Omega up to FP64 rounding.
+__global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
+  __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
+  __shared__ int64_t s_group;
+  __shared__ int s_cnt;
+  __shared__ int s_list[kRescueT];
+  __shared__ unsigned long long s_mask[kRescueT];
+  __shared__ double s_red[kRescueT / 32];
+  __shared__ int2 s_rng[kMaxRanges];
+  __shared__ int s_nr, s_tot;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
+  const int64_t n = a.counters[CNT_N];
+  const int64_t ngroups = (n + kRescueT - 1) / kRescueT;
+  for (;;) {
+    if (tid == 0) {
+      s_group = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_UNC_WORK), 1ull);
+      s_cnt = 0;
+    }
+    __syncthreads();
+    const int64_t g = s_group;
+    if (g >= ngroups) break;
+    const int64_t mine = g * kRescueT + tid;
+    const unsigned long long m = mine < n ? a.unc_mask[mine] : 0ull;
+    if (m) {
+      const int k = atomicAdd(&s_cnt, 1);
+      s_list[k] = tid;
+      s_mask[k] = m;
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int e = 0; e < cnt; ++e) {
+      const int64_t i = g * kRescueT + s_list[e];
+      unsigned long long mm = s_mask[e];
+      const float4 p = a.spts[i];
+      const double px = p.x, py = p.y, pz = p.z;
+      unsigned long long set_bits = 0ull;
+      while (mm) {
+        const int row = __ffsll((long long)mm) - 1;
+        mm &= mm - 1;
+        const DevComp *cp = a.comps + s_rowcomp[row];
+        if (tid == 0) {
+          const float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
+          int tot = 0;
+          s_nr = cap_ranges(a, cp, box, s_rng, &tot);
+          s_tot = tot;
+        }
+        __syncthreads();
+        const int total = s_tot;
+        double part = 0.0;
+        int r = 0, rb = 0;
+        for (int j = tid; j < total; j += kRescueT) {
+          const float4 *T = a.ctri + 4 * (int64_t)range_tri(s_rng, r, rb, j);
+          const float4 A = T[0], B = T[1], C = T[2];
+          const double x1 = (double)A.x - px, y1 = (double)A.y - py, z1 = (double)A.z - pz;
+          const double x2 = (double)B.x - px, y2 = (double)B.y - py, z2 = (double)B.z - pz;
+          const double x3 = (double)C.x - px, y3 = (double)C.y - py, z3 = (double)C.z - pz;
+          const double r1 = sqrt(x1 * x1 + y1 * y1 + z1 * z1);
+          const double r2 = sqrt(x2 * x2 + y2 * y2 + z2 * z2);
+          const double r3 = sqrt(x3 * x3 + y3 * y3 + z3 * z3);
+          const double N = x1 * (y2 * z3 - z2 * y3) + y1 * (z2 * x3 - x2 * z3) + z1 * (x2 * y3 - y2 * x3);
+          const double D = r1 * r2 * r3 + (x1 * x2 + y1 * y2 + z1 * z2) * r3 + (x1 * x3 + y1 * y3 + z1 * z3) * r2 +
+                           (x2 * x3 + y2 * y3 + z2 * z3) * r1;
+          part += atan2(N, D);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) s_red[wid] = part;
+        __syncthreads();
+        double half = 0.0;
+#pragma unroll
+        for (int w = 0; w < kRescueT / 32; ++w) half += s_red[w];
+        __syncthreads();
+        const double om = 2.0 * half;
+        if (om > 6.283185307179586476925) set_bits |= 1ull << row;
+        if (tid == 0) {
+          if (a.omega) a.omega[(int64_t)row * a.omega_ld + a.perm[i]] = (float)om;
+          atomicAdd((unsigned long long *)(a.counters + CNT_UNC), 1ull);
+          atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)total);
+        }
+      }
+      if (tid == 0 && set_bits) atomicOr(a.in_mask + i, set_bits);
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(kRescueT) k_rescue64(LabelArgs a) {
@@ -1578,6 +1985,7 @@ zef_status dispatch_variant(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
 }
 
 zef_status dispatch_label32(zef_ctx *ctx, const LabelArgs &a, LaunchShape s) {
+  if (s.variant == 2) return dispatch_variant<2>(ctx, a, s);
   return s.variant == 1 ? dispatch_variant<1>(ctx, a, s) : dispatch_variant<0>(ctx, a, s);
 }
 
@@ -1625,7 +2033,7 @@ bool shape_valid(int threads, int ppt) {
 
 void fill_default_opts(zef_label_opts *o) {
   if (!(o->margin > 0.f)) o->margin = 1e-3f;
-  if (!(o->winding_tol > 0.f)) o->winding_tol = 4e-6f;
+  if (!(o->winding_tol > 0.f)) o->winding_tol = 1e-4f;
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -1669,12 +2077,12 @@ LaunchShape choose_shape(zef_ctx *ctx, const zef_label_opts &o, int64_t n, bool 
   *need_tune = false;
   if (o.precision == ZEF_FP64_PLAIN) return LaunchShape{128, 2};
   if (o.block_threads && o.points_per_thread)
-    return LaunchShape{o.block_threads, o.points_per_thread, o.kernel};
+    return LaunchShape{o.block_threads, o.points_per_thread, kernel_variant(o.kernel)};
   const uint64_t key = tune_key(ctx, o, n);
   for (const auto &kv : ctx->tune_cache)
     if (kv.first == key) return kv.second;
   *need_tune = n >= 4096;  // small calls: not worth timing
-  return LaunchShape{256, 4, o.kernel};
+  return LaunchShape{256, 2, kernel_variant(o.kernel)};
 }
 
 // plan.pts must be device memory with plan.n_cap points at offset 0.
@@ -1691,10 +2099,10 @@ zef_status autotune(zef_ctx *ctx, const LabelPlan &plan, LaunchShape *best) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_gather_stride launch");
   float best_ms = 3.0e38f;
-  LaunchShape pick{256, 4, plan.opts.kernel};
+  LaunchShape pick{256, 2, kernel_variant(plan.opts.kernel)};
   for (const LaunchShape &c0 : kCandidates) {
     LaunchShape c = c0;
-    c.variant = plan.opts.kernel;
+    c.variant = kernel_variant(plan.opts.kernel);
     LabelPlan p = plan;
     p.pts = b.tune_pts;
     p.labels = b.labels_tmp;
@@ -1846,6 +2254,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.fp32_only = plan.opts.precision == ZEF_FP32_ONLY;
   a.coherence = !(plan.opts.flags & ZEF_NO_TILE_COHERENCE);
   a.early = plan.omega == nullptr && !plan.full_masks;
+  a.nodes = ctx->d_nodes;
+  a.ctri = ctx->d_ctri;
   a.masks_out = plan.masks;
   if (plan.timed) cudaEventRecord(ctx->ev[1], s);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
@@ -1859,7 +2269,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   if (plan.timed) cudaEventRecord(ctx->ev[2], s);
   if (plan.timed) cudaEventRecord(ctx->ev[3], s);
   if (plan.opts.precision == ZEF_FP32_RESCUE) {
-    k_rescue64<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+    if (plan.shape.variant == 2) k_rescue64_caps<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+    else k_rescue64<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
   }
   if (plan.timed) cudaEventRecord(ctx->ev[4], s);
   k_resolve<<<g, 256, 0, s>>>(a, plan.pts, plan.labels, ctx->d_row_ids);

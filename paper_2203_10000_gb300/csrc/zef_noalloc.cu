@@ -92,7 +92,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
   zef_label_opts o;
   if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
   fill_default_opts(&o);
-  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 1)
+  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
@@ -143,8 +143,8 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
   plan.d_off = view.counters + CNT_OFF;
   plan.opts = o;
   if (o.precision == ZEF_FP64_PLAIN) plan.shape = LaunchShape{128, 2};
-  else if (o.block_threads) plan.shape = LaunchShape{o.block_threads, o.points_per_thread, o.kernel};
-  else plan.shape = LaunchShape{256, 4, o.kernel};
+  else if (o.block_threads) plan.shape = LaunchShape{o.block_threads, o.points_per_thread, kernel_variant(o.kernel)};
+  else plan.shape = LaunchShape{256, 2, kernel_variant(o.kernel)};
   plan.timed = stats != nullptr;
 
   // The pipeline enqueues its kernels with the pointers of ctx->lb; point it

@@ -636,9 +636,9 @@ zef_status refine_run(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_la
   if ((st = label_reserve(ctx, std::max<int64_t>(new_cap, mesh->labels_valid ? 1 : N0)))) return st;
   LabelBuffers &b = ctx->lb;
 
-  LaunchShape shape{256, 4, opts.kernel};
+  LaunchShape shape{256, 2, kernel_variant(opts.kernel)};
   if (opts.precision == ZEF_FP64_PLAIN) shape = LaunchShape{128, 2};
-  else if (opts.block_threads) shape = LaunchShape{opts.block_threads, opts.points_per_thread, opts.kernel};
+  else if (opts.block_threads) shape = LaunchShape{opts.block_threads, opts.points_per_thread, kernel_variant(opts.kernel)};
 
   // initial labeling of every node (not graph-captured: host-known count)
   if (!mesh->labels_valid && N0 > 0) {
@@ -687,7 +687,7 @@ zef_status refine_run(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_la
                        (uint64_t)(uintptr_t)b.spts, (uint64_t)(uintptr_t)b.flags, (uint64_t)(uintptr_t)b.hist,
                        (uint64_t)(uintptr_t)b.counters, (uint64_t)b.cap_points, (uint64_t)shape.threads,
                        (uint64_t)shape.ppt, (uint64_t)shape.variant, (uint64_t)opts.precision, fbits(opts.margin),
-                       fbits(opts.winding_tol), (uint64_t)(uintptr_t)ctx->d_entries, (uint64_t)conforming,
+                       fbits(opts.winding_tol), (uint64_t)(uintptr_t)ctx->d_entries, (uint64_t)conforming, ctx->gen,
                        (uint64_t)(uintptr_t)r.state, (uint64_t)(uintptr_t)r.gx})
       key = hash_mix(key, v);
     if (!ctx->rf_exec || ctx->rf_key != key) {

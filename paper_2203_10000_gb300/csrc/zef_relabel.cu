@@ -208,9 +208,9 @@ zef_status relabel_run(zef_ctx *ctx, const float *nodes_in, int64_t n, const int
   if ((st = label_reserve(ctx, n))) return st;
   LabelBuffers &b = ctx->lb;
 
-  LaunchShape shape{256, 4, opts.kernel};
+  LaunchShape shape{256, 2, kernel_variant(opts.kernel)};
   if (opts.precision == ZEF_FP64_PLAIN) shape = LaunchShape{128, 2};
-  else if (opts.block_threads) shape = LaunchShape{opts.block_threads, opts.points_per_thread, opts.kernel};
+  else if (opts.block_threads) shape = LaunchShape{opts.block_threads, opts.points_per_thread, kernel_variant(opts.kernel)};
 
   RB r;
   r.nodes = nodes;
@@ -238,7 +238,7 @@ zef_status relabel_run(zef_ctx *ctx, const float *nodes_in, int64_t n, const int
                      (uint64_t)(uintptr_t)b.spts, (uint64_t)(uintptr_t)b.flags, (uint64_t)(uintptr_t)b.hist,
                      (uint64_t)(uintptr_t)b.counters, (uint64_t)b.cap_points, (uint64_t)shape.threads,
                      (uint64_t)shape.ppt, (uint64_t)shape.variant, (uint64_t)opts.precision, bits(opts.margin),
-                     bits(opts.winding_tol), (uint64_t)opts.flags, (uint64_t)(uintptr_t)ctx->d_entries})
+                     bits(opts.winding_tol), (uint64_t)opts.flags, (uint64_t)(uintptr_t)ctx->d_entries, ctx->gen})
     key = mix(key, v);
   if (!ctx->rb_exec || ctx->rb_key != key) {
     if (ctx->rb_exec) {

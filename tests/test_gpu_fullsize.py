@@ -42,22 +42,24 @@ def near_surface_rows(w, count, seed, radius=0.6, probe=2_000_000):
     return np.sort(rng.choice(near, size=count, replace=False))
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("cfg,n_uniform,n_near", [("config2", 3000, 3000),
                                                   ("config4", 1500, 2500)])
-def test_full_size_sampled_parity(zef, oracle_mod, cfg, n_uniform, n_near):
+def test_full_size_sampled_parity(zef, oracle_mod, cfg, n_uniform, n_near, kernel):
     w = getattr(zs, cfg)()
     ctx = zef.Context(0)
     for s in w.surfaces:
         ctx.add_compartment(s.id, s.verts, s.tris)
     ctx.set_priority(w.priority)
     pts = torch.from_numpy(w.points).cuda()
-    lab, _, st = ctx.label_points(pts, want_omega=False)
+    lab, _, st = ctx.label_points(pts, want_omega=False, opts=zef.make_opts(kernel=kernel))
     torch.cuda.synchronize()
     lab = lab.cpu().numpy()
     n = w.points.shape[0]
     assert st["points"] == n and st["nonfinite_points"] == 0
     assert st["pairs_nominal"] == n * w.total_tris
     assert 0 < st["pairs_evaluated"] < st["pairs_nominal"]
+    print(f"{cfg} kernel {kernel}: {st['ms_label']:.1f} ms label, {st['pairs_evaluated']:.3e} pairs")
     # every label is one of the registered ids or the bounding box
     assert np.isin(np.unique(lab), np.array([0] + list(w.priority))).all()
 

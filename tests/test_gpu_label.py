@@ -156,9 +156,10 @@ def test_launch_shapes_ragged_tail(zef, oracle_mod, shape):
     assert np.array_equal(om, om2) and np.array_equal(lab, lab2)
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_kernel_forms_match_oracle(zef, oracle_mod, kernel):
-    """Grouped complex products (0) and one atan2 per triangle (1)."""
+    """Cap trees (0, the default: far patches replaced by their caps), strips
+    with grouped complex products (1), strips with one atan2 per triangle (2)."""
     w = zs.config0()
     ctx = make_ctx(zef, w.surfaces, w.priority)
     lab, om, st = gpu_label(ctx, w.points, opts=zef.make_opts(kernel=kernel))
@@ -350,13 +351,14 @@ def test_priority_intersecting_spheres(zef, oracle_mod):
 
 
 # ------------------------------------------------------------------ full-size head workload
-def test_config1_full_size_sampled(zef, oracle_mod):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_config1_full_size_sampled(zef, oracle_mod, kernel):
     """All 5,000,000 centroids of the 2 mm lattice against the three-layer
     head; a seeded sample is checked against the oracle element by element and
     every Omega against the closed-surface invariant."""
     w = zs.config1()
     ctx = make_ctx(zef, w.surfaces, w.priority)
-    lab, om, st = gpu_label(ctx, w.points)
+    lab, om, st = gpu_label(ctx, w.points, opts=zef.make_opts(kernel=kernel))
     assert st["points"] == 5_000_000
     # invariant at full size: every Omega is 0 or 4 pi to within 1e-5
     d = np.minimum(np.abs(om), np.abs(om - FOUR_PI))
