@@ -430,6 +430,7 @@ def run_ours(args):
 
     line["coherent_pairs_per_step"] = st["coherent_pairs"]
     line["representative_pairs_per_step"] = st["representative_pairs"]
+    line["lane_walk_items_per_step"] = st["lane_walk_items"]
 
     # measured FMA throughput of this GPU (cross-check of the FP32 peak; the
     # FP64 rate sets the cost of the re-evaluation and of the plain FP64 kernel)

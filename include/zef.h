@@ -96,14 +96,15 @@ typedef struct zef_label_opts {
        autotuned choice.  Valid: threads 128 or 256, points 2 or 4. */
     int32_t block_threads;
     int32_t points_per_thread;
-    /* Form of the FP32 kernel: 0 = the whole surface as triangle strips, one
-       atan2 per group of four triangles taken of the product of their
-       (D + iN) factors with 2 pi wraps counted exactly; 1 = strips, one atan2
-       per triangle; 2 = cap trees (zef_tree.cpp): for each tile of points the
-       patches whose box misses the tile are replaced by their caps, exact
-       since outside that box a cap subtends its patch (default). */
+    /* Form of the FP32 kernel: 0 = cap trees (default): for each tile of
+       points the patches whose box misses the tile are replaced by their
+       caps, exact since outside that box a cap subtends its patch, and the
+       remaining leaves and caps are streamed as strips; 1 = the whole surface
+       as triangle strips, one atan2 per group of four triangles taken of the
+       product of their (D + iN) factors with 2 pi wraps counted exactly;
+       2 = whole-surface strips, one atan2 per triangle. */
     int32_t kernel;
-    /* ZEF_NO_TILE_COHERENCE or 0 (see below). */
+    /* ZEF_NO_TILE_COHERENCE and / or ZEF_POINT_WALK, or 0 (see below). */
     uint32_t flags;
     int32_t reserved;
 } zef_label_opts;
@@ -115,6 +116,13 @@ typedef struct zef_label_opts {
    the representative must be certain, or the tile is evaluated point by
    point.  This flag evaluates every point instead. */
 #define ZEF_NO_TILE_COHERENCE 1u
+/* Kernel form 0: by default the points of a tile share one list of leaf and
+   cap segments (the tree walked for the tile's box), except where that list
+   is longer than 2048 entries and more than three times the longest of the
+   points' own walks (a tile whose box spans much of a surface): there every
+   point walks the tree for itself.  This flag makes every point walk the
+   tree for itself. */
+#define ZEF_POINT_WALK 2u
 
 typedef struct zef_label_stats {
     int64_t points;            /* N */
@@ -135,6 +143,9 @@ typedef struct zef_label_stats {
                                   representative point of a tile or group */
     int64_t representative_pairs; /* of pairs_evaluated: point x triangle pairs
                                      of those representatives */
+    int64_t lane_walk_items;   /* kernel form 0: (tile, compartment) pairs whose
+                                  points each walked their own cap tree (the
+                                  tile's shared list of segments was too long) */
 } zef_label_stats;
 
 /* Mesh for zef_refine_and_relabel.  All four arrays must be device memory or

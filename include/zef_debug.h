@@ -38,17 +38,20 @@ zef_status zef_debug_strip_stats(const zef_ctx *ctx, int32_t index, int64_t *ent
 zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);
 
 /* Cap tree of compartment `index` (registration order), unscaled: for each
-   node its box (lo x, y, z, hi x, y, z: the patch's triangles and its cap
-   apex), and six int32 (left child, right child (-1 for a leaf), first leaf
-   triangle, leaf triangle count, first cap triangle, cap triangle count;
-   triangle indices relative to the compartment's block); the block's
-   triangles as 16 floats each (A x, y, z, kappa |n|, B x, y, z, 0, C x, y, z,
-   0, n x, y, z, 0 with n = (B - A) x (C - A)).  *n_nodes and *n_tris receive
-   the counts; the arrays (nullable) must hold them.  The identity the tree
-   serves: outside a node's box, the solid angle of the node's leaf
-   triangles equals that of its cap triangles.  Works on host-only contexts. */
-zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int64_t *n_nodes, int64_t *n_tris,
-                              float *boxes, int32_t *links, float *tris);
+   node its box (lo x, y, z, hi x, y, z of the patch's vertices) and eight
+   int32 (left child, right child (-1 for a leaf), first entry and entry
+   count of the leaf's strip segment (0, 0 for an inner node), first entry
+   and entry count of the node's cap segment, triangles of the leaf segment,
+   triangles of the cap segment; entries relative to the compartment's
+   block); the block's entries as 8 floats each (vertex x, y, z, weight;
+   n x, y, z, kappa |n|), weight 2 opening a segment, +-1 closing a
+   triangle window in its own / reversed orientation, 0 for the windows that
+   repeat a vertex.  *n_nodes and *n_entries receive the counts; the arrays
+   (nullable) must hold them.  The identity the tree serves: outside a
+   node's box, the solid angle of the node's leaf triangles equals that of
+   its cap triangles.  Works on host-only contexts. */
+zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int64_t *n_nodes, int64_t *n_entries,
+                              float *boxes, int32_t *links, float *entries);
 
 /* Measured fused multiply-add throughput of the context's device in TFLOP/s
    (FMA = 2 flops): float (fp64 = 0) or double (fp64 != 0), 8 independent

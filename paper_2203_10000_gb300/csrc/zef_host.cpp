@@ -223,7 +223,7 @@ void zef_destroy(zef_ctx *ctx) {
   fr(ctx->d_entries);
   fr(ctx->d_tris);
   fr(ctx->d_nodes);
-  fr(ctx->d_ctri);
+  fr(ctx->d_cseg);
   fr(ctx->d_comps);
   fr(ctx->d_row_ids);
   fr(ctx->d_lpt);
@@ -459,12 +459,12 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
     return fail(ctx, ZEF_ERR_INVALID_ARG, "total surface size exceeds the library limit");
   // cap tree (exact far-field replacement of patches, zef_tree.cpp)
   {
-    const int64_t node_base = (int64_t)ctx->h_nodes.size(), tri_base = (int64_t)ctx->h_ctri.size() / 4;
+    const int64_t node_base = (int64_t)ctx->h_nodes.size(), seg_base = (int64_t)ctx->h_cseg.size();
     int64_t leaf = 0;
-    build_cap_tree(V.data(), T.data(), nt, node_base, tri_base, ctx->h_nodes, ctx->h_ctri, &ch.cap_root, &leaf);
-    ch.ctri_off = tri_base;
-    ch.ctri_leaf = leaf;
-    if ((int64_t)ctx->h_ctri.size() / 4 > INT32_MAX || (int64_t)ctx->h_nodes.size() > INT32_MAX)
+    build_cap_tree(V.data(), T.data(), nt, node_base, seg_base, ctx->h_nodes, ctx->h_cseg, &ch.cap_root, &leaf);
+    ch.cseg_off = seg_base;
+    ch.cseg_leaf = leaf;
+    if ((int64_t)ctx->h_nodes.size() > INT32_MAX || (int64_t)ctx->h_cseg.size() > INT32_MAX)
       return fail(ctx, ZEF_ERR_INVALID_ARG, "total surface size exceeds the library limit");
   }
   ctx->h_entries.insert(ctx->h_entries.end(), ent.begin(), ent.end());
@@ -601,6 +601,7 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
+  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -681,6 +682,7 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
     stats->tiles = h[CNT_TILES];
     stats->coherent_pairs = h[CNT_COHERENT];
     stats->representative_pairs = h[CNT_REP_PAIRS];
+    stats->lane_walk_items = h[CNT_LANE_TILES];
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;
@@ -717,6 +719,7 @@ zef_status zef_relabel_boundary(zef_ctx *ctx, const float *nodes, int64_t n_node
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
+  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (per_pass) std::memset(per_pass, 0, sizeof(zef_relabel_pass) * (size_t)max_passes);
@@ -784,6 +787,7 @@ zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, 
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
+  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   DeviceGuard g(ctx->device);
@@ -863,28 +867,25 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
       nd.lo[k] *= s;
       nd.hi[k] *= s;
     }
-  std::vector<float4> cs(ctx->h_ctri);
-  for (size_t k = 0; k < cs.size(); k += 4) {
-    for (int q = 0; q < 3; ++q) {
-      cs[k + q].x *= s; cs[k + q].y *= s; cs[k + q].z *= s;
-    }
-    cs[k].w *= s2;
-    cs[k + 3].x *= s2; cs[k + 3].y *= s2; cs[k + 3].z *= s2;
-  }
   if (ctx->d_nodes_cap < (int64_t)ns.size()) {
     if (ctx->d_nodes) cudaFree(ctx->d_nodes);
     ctx->d_nodes = nullptr;
     CK(cudaMalloc(&ctx->d_nodes, std::max<size_t>(ns.size(), 1) * sizeof(CapNode)), "cudaMalloc(cap nodes)");
     ctx->d_nodes_cap = (int64_t)ns.size();
   }
-  if (ctx->d_ctri_cap < (int64_t)cs.size()) {
-    if (ctx->d_ctri) cudaFree(ctx->d_ctri);
-    ctx->d_ctri = nullptr;
-    CK(cudaMalloc(&ctx->d_ctri, std::max<size_t>(cs.size(), 1) * sizeof(float4)), "cudaMalloc(cap triangles)");
-    ctx->d_ctri_cap = (int64_t)cs.size();
-  }
   if (!ns.empty()) CK(cudaMemcpy(ctx->d_nodes, ns.data(), ns.size() * sizeof(CapNode), cudaMemcpyHostToDevice), "upload cap nodes");
-  if (!cs.empty()) CK(cudaMemcpy(ctx->d_ctri, cs.data(), cs.size() * sizeof(float4), cudaMemcpyHostToDevice), "upload cap triangles");
+  std::vector<Entry> gs(ctx->h_cseg);
+  for (Entry &e : gs) {
+    e.v.x *= s; e.v.y *= s; e.v.z *= s;
+    e.n.x *= s2; e.n.y *= s2; e.n.z *= s2; e.n.w *= s2;
+  }
+  if (ctx->d_cseg_cap < (int64_t)gs.size()) {
+    if (ctx->d_cseg) cudaFree(ctx->d_cseg);
+    ctx->d_cseg = nullptr;
+    CK(cudaMalloc(&ctx->d_cseg, std::max<size_t>(gs.size(), 1) * sizeof(Entry)), "cudaMalloc(cap segments)");
+    ctx->d_cseg_cap = (int64_t)gs.size();
+  }
+  if (!gs.empty()) CK(cudaMemcpy(ctx->d_cseg, gs.data(), gs.size() * sizeof(Entry), cudaMemcpyHostToDevice), "upload cap segments");
   std::vector<DevComp> dc(C);
   std::vector<int32_t> rows(C), lpt(C);
   for (int i = 0; i < C; ++i) {
@@ -899,8 +900,8 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
     d.tri_off = (int32_t)h.tri_off;
     d.tri_cnt = (int32_t)h.nt;
     d.cap_root = h.cap_root;
-    d.ctri_off = (int32_t)h.ctri_off;
-    d.ctri_leaf = (int32_t)h.ctri_leaf;
+    d.cseg_off = (int32_t)h.cseg_off;
+    d.cseg_leaf = (int32_t)h.cseg_leaf;
     d.pad_ = 0;
     d.id = h.id;
     d.row = -1;
@@ -976,15 +977,15 @@ extern "C" zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const f
   return zef_synchronize(ctx);
 }
 
-extern "C" zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int64_t *n_nodes, int64_t *n_tris,
-                                         float *boxes, int32_t *links, float *tris) {
-  if (!ctx || index < 0 || index >= (int32_t)ctx->comps.size() || !n_nodes || !n_tris) return ZEF_ERR_INVALID_ARG;
+extern "C" zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int64_t *n_nodes, int64_t *n_entries,
+                                         float *boxes, int32_t *links, float *entries) {
+  if (!ctx || index < 0 || index >= (int32_t)ctx->comps.size() || !n_nodes || !n_entries) return ZEF_ERR_INVALID_ARG;
   const CompHost &c = ctx->comps[(size_t)index];
   const bool last = index + 1 == (int32_t)ctx->comps.size();
   const int64_t node_end = last ? (int64_t)ctx->h_nodes.size() : ctx->comps[(size_t)index + 1].cap_root;
-  const int64_t tri_end = last ? (int64_t)ctx->h_ctri.size() / 4 : ctx->comps[(size_t)index + 1].ctri_off;
+  const int64_t seg_end = last ? (int64_t)ctx->h_cseg.size() : ctx->comps[(size_t)index + 1].cseg_off;
   *n_nodes = node_end - c.cap_root;
-  *n_tris = tri_end - c.ctri_off;
+  *n_entries = seg_end - c.cseg_off;
   for (int64_t k = 0; k < *n_nodes; ++k) {
     const CapNode &nd = ctx->h_nodes[(size_t)(c.cap_root + k)];
     if (boxes)
@@ -993,15 +994,19 @@ extern "C" zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int6
         boxes[6 * k + 3 + d] = nd.hi[d];
       }
     if (links) {
-      links[6 * k + 0] = nd.left < 0 ? -1 : nd.left - c.cap_root;
-      links[6 * k + 1] = nd.right < 0 ? -1 : nd.right - c.cap_root;
-      links[6 * k + 2] = nd.tri_begin - (int32_t)c.ctri_off;
-      links[6 * k + 3] = nd.tri_cnt;
-      links[6 * k + 4] = nd.cap_begin - (int32_t)c.ctri_off;
-      links[6 * k + 5] = nd.cap_cnt;
+      int32_t *l = links + 8 * k;
+      l[0] = nd.left < 0 ? -1 : nd.left - c.cap_root;
+      l[1] = nd.right < 0 ? -1 : nd.right - c.cap_root;
+      l[2] = nd.left < 0 ? nd.leaf_begin - (int32_t)c.cseg_off : 0;
+      l[3] = nd.left < 0 ? nd.leaf_cnt : 0;
+      l[4] = nd.cap_begin - (int32_t)c.cseg_off;
+      l[5] = nd.cap_cnt;
+      l[6] = nd.left < 0 ? nd.leaf_tris : 0;
+      l[7] = nd.cap_tris;
     }
   }
-  if (tris) std::memcpy(tris, ctx->h_ctri.data() + 4 * c.ctri_off, (size_t)*n_tris * 4 * sizeof(float4));
+  if (entries)
+    std::memcpy(entries, ctx->h_cseg.data() + c.cseg_off, (size_t)*n_entries * sizeof(Entry));
   return ZEF_OK;
 }
 

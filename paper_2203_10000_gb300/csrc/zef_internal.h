@@ -35,23 +35,29 @@ struct __align__(16) DevComp {
   int32_t id;         // user id
   int32_t row;        // priority row (0 = highest priority)
   int32_t cap_root;   // root of the cap tree (zef_tree.cpp)
-  int32_t ctri_off;   // first triangle of the compartment's cap-tree block
-  int32_t ctri_leaf;  // triangles of its leaves (the caps follow)
+  int32_t cseg_off;   // first entry of the compartment's cap-tree segment block
+  int32_t cseg_leaf;  // entries of its leaf segments (the caps' follow)
   int32_t pad_;
 };
 
 // Node of a compartment's cap tree (zef_tree.cpp): the box of the patch's
-// triangles and its cap apex, children (-1 for a leaf), the leaf's triangles
-// and the node's cap triangles in the cap-tree triangle array.
-struct CapNode {
-  float lo[3], hi[3];
-  int32_t left, right;
-  int32_t tri_begin, tri_cnt;
-  int32_t cap_begin, cap_cnt;
+// vertices, children (-1 for a leaf), the leaf's strip segment and the
+// node's cap segment (entries of the cap-tree segment array) with the
+// triangles each holds.
+constexpr int kCapLeaf = 64;  // most triangles of a leaf
+struct __align__(16) CapNode {
+  float lo[3];
+  int32_t left;
+  float hi[3];
+  int32_t right;
+  int32_t leaf_begin, leaf_cnt;  // leaf: strip segment of its triangles
+  int32_t cap_begin, cap_cnt;    // the node's cap: zigzag strip segment
+  int32_t leaf_tris, cap_tris;
+  int32_t pad_[2];
 };
-constexpr int kCapLeaf = 64;  // triangles per leaf patch
-void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_base, int64_t tri_base,
-                    std::vector<CapNode> &nodes, std::vector<float4> &tri, int32_t *root, int64_t *leaf_tris);
+static_assert(sizeof(CapNode) == 64, "CapNode is four 16-byte words");
+void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_base, int64_t seg_base,
+                    std::vector<CapNode> &nodes, std::vector<Entry> &seg, int32_t *root, int64_t *leaf_entries);
 
 // Device status word bits (ctx->d_status[0]); [1] holds detail.
 enum : uint32_t {
@@ -80,8 +86,8 @@ struct CompHost {
   int64_t nv, nt;
   float lo[3], hi[3];
   int64_t entry_off, entry_cnt, tri_off, nstrips;
-  int32_t cap_root;                // cap tree: root node, triangle block, leaf triangles
-  int64_t ctri_off, ctri_leaf;
+  int32_t cap_root;                // cap tree: root node, segment block, leaf entries
+  int64_t cseg_off, cseg_leaf;
   double dop[kDop];  // max over the vertices of d_k . v (unscaled coordinates)
 };
 
@@ -137,6 +143,7 @@ enum Counter {
   CNT_CL_ITER,        // closure passes of the level
   CNT_CL_GREEN,       // tets split along one to three edges
   CNT_CL_GEXTRA,      // children those splits add
+  CNT_LANE_TILES,     // cap trees: (tile, compartment) pairs evaluated by per-lane walks
   CNT_COUNT_ = 32
 };
 
@@ -164,7 +171,7 @@ struct zef_ctx {
   std::vector<zef::Entry> h_entries;
   std::vector<float4> h_tris;         // 3 per triangle (w unused)
   std::vector<zef::CapNode> h_nodes;  // cap trees of all compartments
-  std::vector<float4> h_ctri;         // cap-tree triangles, 4 float4 each
+  std::vector<zef::Entry> h_cseg;     // cap-tree strip segments
 
   bool dirty = true;
   uint64_t gen = 0;   // upload generation: cached graphs keyed on it see every change of the surfaces
@@ -179,8 +186,8 @@ struct zef_ctx {
   int32_t *d_lpt = nullptr;           // LPT rank -> comp index
   float *d_dop = nullptr;             // [C][kDop] hull support bounds (scaled coordinates)
   zef::CapNode *d_nodes = nullptr;    // cap trees (scaled)
-  float4 *d_ctri = nullptr;           // cap-tree triangles (scaled)
-  int64_t d_nodes_cap = 0, d_ctri_cap = 0;
+  zef::Entry *d_cseg = nullptr;       // cap-tree strip segments (scaled)
+  int64_t d_nodes_cap = 0, d_cseg_cap = 0;
   int64_t d_entries_cap = 0, d_tris_cap = 0;
 
   uint32_t *d_status = nullptr;       // [2]

@@ -47,6 +47,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "zef_internal.h"
@@ -287,9 +288,10 @@ struct LabelArgs {
   int fp32_only;
   int coherence;  // tile representatives allowed
   int early;      // priority early exit: a point certainly inside needs no later compartment
+  int lane_walk;  // kernel form 2 (cap trees): 0 = every point walks the tree for itself
   unsigned long long *masks_out;  // nullable: inside bits per point in the caller's order
   const CapNode *nodes;  // cap trees
-  const float4 *ctri;    // cap-tree triangles, 4 float4 each
+  const Entry *cseg;     // cap-tree strip segments
 };
 
 // Classification of one (point, compartment) pair after the FP32 sum:
@@ -630,29 +632,34 @@ __device__ __forceinline__ bool stream_sums(const LabelArgs &a, const DevComp *c
 }
 
 // ------------------------------------------------------------------ cap trees (kernel form 2)
-// For a box of points, the triangles that stand for a compartment's surface:
-// a depth-first walk of its cap tree emits the cap of every node whose box
-// misses the point box (outside that box the cap subtends the node's patch
-// exactly) and the triangles of every leaf whose box meets it.  The result
-// is a list of ranges of the cap-tree triangle array (contiguous leaves
-// merged); more than kMaxRanges ranges fall back to all leaf triangles.
+// For a box of points, the strip segments that stand for a compartment's
+// surface: a depth-first walk of its cap tree emits the cap of every node
+// whose box misses the point box (outside that box the cap subtends the
+// node's patch exactly) and the strips of every leaf whose box meets it.
+// The result is a list of entry ranges of the cap-tree segment array
+// (contiguous segments merged) with *total entries holding *tris triangles;
+// more than kMaxRanges ranges return -1, or with `all_leaves` fall back to
+// every leaf segment.
 constexpr int kMaxRanges = 192;
 
-__device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb, int2 *out, int *total) {
+__device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb, int2 *out, int *total,
+                          int *tris, bool all_leaves) {
   int stack[48];
-  int sp = 0, n = 0, tot = 0;
+  int sp = 0, n = 0, tot = 0, nt = 0;
   stack[sp++] = __ldg(&cp->cap_root);
   while (sp > 0) {
     const CapNode nd = a.nodes[stack[--sp]];
     const bool far = nd.hi[0] < wb[0] || nd.lo[0] > wb[3] || nd.hi[1] < wb[1] || nd.lo[1] > wb[4] ||
                      nd.hi[2] < wb[2] || nd.lo[2] > wb[5];
-    int b, c;
+    int b, c, t;
     if (far) {
       b = nd.cap_begin;
       c = nd.cap_cnt;
+      t = nd.cap_tris;
     } else if (nd.left < 0) {
-      b = nd.tri_begin;
-      c = nd.tri_cnt;
+      b = nd.leaf_begin;
+      c = nd.leaf_cnt;
+      t = nd.leaf_tris;
     } else {
       if (sp + 2 > 48) {  // deeper than any tree of 2^28 triangles: cannot happen
         n = -1;
@@ -664,6 +671,7 @@ __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb
     }
     if (c <= 0) continue;
     tot += c;
+    nt += t;
     if (n > 0 && out[n - 1].x + out[n - 1].y == b) {
       out[n - 1].y += c;
     } else if (n < kMaxRanges) {
@@ -673,18 +681,20 @@ __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb
       break;
     }
   }
-  if (n < 0) {  // every leaf triangle: the compartment's own triangles
-    out[0] = make_int2(__ldg(&cp->ctri_off), __ldg(&cp->ctri_leaf));
+  if (n < 0 && all_leaves) {  // every leaf segment: the compartment's own triangles
+    out[0] = make_int2(__ldg(&cp->cseg_off), __ldg(&cp->cseg_leaf));
     n = 1;
     tot = out[0].y;
+    nt = __ldg(&cp->tri_cnt);
   }
   *total = tot;
+  *tris = nt;
   return n;
 }
 
-// Position of flattened triangle j of a range list; the cursor (range r,
-// first flattened index of r) only moves forward.
-__device__ __forceinline__ int range_tri(const int2 *rng, int &r, int &rb, int j) {
+// Position of flattened entry j of a range list; the cursor (range r, first
+// flattened index of r) only moves forward.
+__device__ __forceinline__ int range_pos(const int2 *rng, int &r, int &rb, int j) {
   while (j >= rb + rng[r].y) {
     rb += rng[r].y;
     ++r;
@@ -692,9 +702,21 @@ __device__ __forceinline__ int range_tri(const int2 *rng, int &r, int &rb, int j
   return rng[r].x + (j - rb);
 }
 
-// Van Oosterom-Strackee half angle of a stored triangle (A, B, C, n) seen
-// from r: N = R_A . n, D = r_A r_B r_C + (R_A . R_B) r_C + (R_A . R_C) r_B +
-// (R_B . R_C) r_A; bad = min(bad, max(|N|, D) - kappa |n| r_A).
+// The triangle closed by segment entry `pos` (its window: the two entries
+// before it, which lie in the same segment), with the stored oriented
+// normal and kappa |n| in nn.w; false for a window that is not a triangle.
+__device__ __forceinline__ bool seg_tri(const Entry *E, int pos, float4 &A, float4 &B, float4 &C, float4 &nn) {
+  C = E[pos].v;
+  if (fabsf(C.w) != 1.f) return false;
+  A = E[pos - 2].v;
+  B = E[pos - 1].v;
+  nn = E[pos].n;
+  return true;
+}
+
+// Van Oosterom-Strackee half angle of a triangle (A, B, C) with oriented
+// normal n seen from r: N = R_A . n, D = r_A r_B r_C + (R_A . R_B) r_C +
+// (R_A . R_C) r_B + (R_B . R_C) r_A; bad = min(bad, max(|N|, D) - kappa |n| r_A).
 __device__ __forceinline__ void tri_nd(float px, float py, float pz, float4 A, float4 B, float4 C, float4 nn,
                                        float &N, float &D, float &bad) {
   const float ax = A.x - px, ay = A.y - py, az = A.z - pz;
@@ -709,43 +731,51 @@ __device__ __forceinline__ void tri_nd(float px, float py, float pz, float4 A, f
   const float dac = fmaf(ax, cx, fmaf(ay, cy, az * cz));
   const float dbc = fmaf(bx, cx, fmaf(by, cy, bz * cz));
   D = fmaf(ra * rb, rc, fmaf(dab, rc, fmaf(dac, rb, dbc * ra)));
-  bad = fminf(bad, fmaf(-A.w, ra, fmaxf(fabsf(N), D)));
+  bad = fminf(bad, fmaf(-nn.w, ra, fmaxf(fabsf(N), D)));
 }
 
-// rep_pass over a range list (flattened triangles from 0)
+// rep_pass over a range list (one entry per lane; *scanned receives the
+// triangles evaluated)
 __device__ __forceinline__ bool rep_pass_caps(const LabelArgs &a, const int2 *rng, int total, const float *wb,
-                                              float rx, float ry, float rz, int lane, int *k, int *t_hit) {
+                                              float rx, float ry, float rz, int lane, int *k, int *t_hit,
+                                              int *scanned) {
   float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
   if (wb) {
     lx = wb[0]; ly = wb[1]; lz = wb[2]; hx = wb[3]; hy = wb[4]; hz = wb[5];
   }
   *t_hit = -1;
+  int ntri = 0;
   float sum = 0.f, comp = 0.f, bad = __int_as_float(0x7f800000);
   int r = 0, rb = 0;
   for (int t0 = 0; t0 < total; t0 += 32) {
     const int j = t0 + lane;
-    bool ov = false;
+    bool ov = false, is_tri = false;
     float term = 0.f;
     if (j < total) {
-      const float4 *T = a.ctri + 4 * (int64_t)range_tri(rng, r, rb, j);
-      const float4 A = T[0], B = T[1], C = T[2], nn = T[3];
-      if (wb)
-        ov = !(fmaxf(A.x, fmaxf(B.x, C.x)) < lx || fminf(A.x, fminf(B.x, C.x)) > hx ||
-               fmaxf(A.y, fmaxf(B.y, C.y)) < ly || fminf(A.y, fminf(B.y, C.y)) > hy ||
-               fmaxf(A.z, fmaxf(B.z, C.z)) < lz || fminf(A.z, fminf(B.z, C.z)) > hz);
-      float N, D;
-      tri_nd(rx, ry, rz, A, B, C, nn, N, D, bad);
-      term = half_angle(N, D);
+      float4 A, B, C, nn;
+      is_tri = seg_tri(a.cseg, range_pos(rng, r, rb, j), A, B, C, nn);
+      if (is_tri) {
+        if (wb)
+          ov = !(fmaxf(A.x, fmaxf(B.x, C.x)) < lx || fminf(A.x, fminf(B.x, C.x)) > hx ||
+                 fmaxf(A.y, fmaxf(B.y, C.y)) < ly || fminf(A.y, fminf(B.y, C.y)) > hy ||
+                 fmaxf(A.z, fmaxf(B.z, C.z)) < lz || fminf(A.z, fminf(B.z, C.z)) > hz);
+        float N, D;
+        tri_nd(rx, ry, rz, A, B, C, nn, N, D, bad);
+        term = half_angle(N, D);
+      }
     }
     if (wb && __any_sync(0xffffffffu, ov)) {
       *t_hit = t0;
+      *scanned = ntri;
       return false;
     }
+    ntri += __popc(__ballot_sync(0xffffffffu, is_tri));
     const float y = term - comp;
     const float tt = sum + y;
     comp = (tt - sum) - y;
     sum = tt;
   }
+  *scanned = ntri;
   return rep_certain(a, sum, -comp, bad, k);
 }
 
@@ -757,9 +787,8 @@ __device__ __forceinline__ uint32_t touched_groups_caps(const LabelArgs &a, cons
   int r = 0, rb = 0;
   for (int t0 = t_begin; t0 < total; t0 += 32) {
     const int j = t0 + lane;
-    if (j < total) {
-      const float4 *T = a.ctri + 4 * (int64_t)range_tri(rng, r, rb, j);
-      const float4 A = T[0], B = T[1], C = T[2];
+    float4 A, B, C, nn;
+    if (j < total && seg_tri(a.cseg, range_pos(rng, r, rb, j), A, B, C, nn)) {
       const float ux = fmaxf(A.x, fmaxf(B.x, C.x)), lx = fminf(A.x, fminf(B.x, C.x));
       const float uy = fmaxf(A.y, fmaxf(B.y, C.y)), ly = fminf(A.y, fminf(B.y, C.y));
       const float uz = fmaxf(A.z, fmaxf(B.z, C.z)), lz = fminf(A.z, fminf(B.z, C.z));
@@ -788,8 +817,8 @@ __device__ __forceinline__ uint32_t group_reps_caps(const LabelArgs &a, const in
   }
   int r = 0, rb = 0;
   for (int j = lane; j < total; j += 32) {
-    const float4 *T = a.ctri + 4 * (int64_t)range_tri(rng, r, rb, j);
-    const float4 A = T[0], B = T[1], C = T[2], nn = T[3];
+    float4 A, B, C, nn;
+    if (!seg_tri(a.cseg, range_pos(rng, r, rb, j), A, B, C, nn)) continue;
 #pragma unroll
     for (int g = 0; g < NG; ++g)
       if ((u >> g) & 1u) {
@@ -808,22 +837,23 @@ __device__ __forceinline__ uint32_t group_reps_caps(const LabelArgs &a, const in
   return certain;
 }
 
-// Point-by-point sums over a range list: chunks of kCapChunk triangles (4 KB)
-// gathered into the warp's double buffer by one or more bulk copies on one
-// mbarrier; every lane multiplies the (D + i N) factors of four consecutive
-// triangles with wrap counting (missing ones are the identity) and takes one
-// atan2 per four, the group sums Kahan-compensated every 16 triangles.
-constexpr int kCapChunk = 64;
-
+// Point-by-point sums over a range list of strip segments: chunks of
+// kWChunk entries (4 KB) gathered into the warp's double buffer by one or
+// more bulk copies on one mbarrier; every lane steps its points' windows
+// through the entries, multiplies the (D + i N) factors of four consecutive
+// windows with wrap counting and takes one atan2 per four, the group sums
+// Kahan-compensated every kGroup entries.  A segment opens with a reset
+// entry at a multiple of four (every segment holds whole groups of four),
+// which restarts the windows at its vertex.
 template <int NA>
-__device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 *rng, int total, float4 *wbuf,
+__device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 *rng, int total, Entry *wbuf,
                                                  uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane,
                                                  PState (&st)[NA]) {
-  const int nchunks = (total + kCapChunk - 1) / kCapChunk;
+  const int nchunks = (total + kWChunk - 1) / kWChunk;
   int fr = 0, fb = 0;  // lane 0's fill cursor over the ranges
   auto fill = [&](int ch, int b) {
-    const int j0 = ch * kCapChunk, j1 = min(total, j0 + kCapChunk);
-    tma_expect(&bar[b], (uint32_t)(j1 - j0) * 64u);
+    const int j0 = ch * kWChunk, j1 = min(total, j0 + kWChunk);
+    tma_expect(&bar[b], (uint32_t)(j1 - j0) * (uint32_t)sizeof(Entry));
     int j = j0;
     while (j < j1) {
       while (j >= fb + rng[fr].y) {
@@ -831,8 +861,8 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
         ++fr;
       }
       const int take = min(j1 - j, fb + rng[fr].y - j);
-      tma_copy_1d(wbuf + b * 4 * kCapChunk + 4 * (j - j0), a.ctri + 4 * (int64_t)(rng[fr].x + (j - fb)),
-                  (uint32_t)take * 64u, &bar[b]);
+      tma_copy_1d(wbuf + b * kWChunk + (j - j0), a.cseg + (rng[fr].x + (j - fb)),
+                  (uint32_t)take * (uint32_t)sizeof(Entry), &bar[b]);
       j += take;
     }
   };
@@ -851,35 +881,30 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
     const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
     if (__any_sync(0xffffffffu, !ok)) return false;
     if (b) ph1 ^= 1; else ph0 ^= 1;
-    const float4 *E = wbuf + b * 4 * kCapChunk;
-    const int cnt = min(kCapChunk, total - ch * kCapChunk);
+    const Entry *E = wbuf + b * kWChunk;
+    const int cnt = min(kWChunk, total - ch * kWChunk);  // a multiple of four
     for (int g = 0; g < cnt; g += kGroup) {
 #pragma unroll 1
       for (int j = g; j < min(cnt, g + kGroup); j += 4) {
-        float R[NA], I[NA];
+        const Entry *e = E + j;
+        const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
+        const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
+        if (v0.w == 2.f) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (j + k < cnt) {
-            const float4 *T = E + 4 * (j + k);
-            const float4 A = T[0], B = T[1], C = T[2], nn = T[3];
-#pragma unroll
-            for (int q = 0; q < NA; ++q) {
-              float N, D;
-              tri_nd(st[q].px, st[q].py, st[q].pz, A, B, C, nn, N, D, st[q].bad);
-              if (k == 0) {
-                R[q] = D;
-                I[q] = N;
-              } else {
-                float cr, ci;
-                cmul_wrap(R[q], I[q], D, N, cr, ci, st[q].kp, st[q].kn);
-                R[q] = cr;
-                I[q] = ci;
-              }
-            }
-          }
+          for (int q = 0; q < NA; ++q) window_init(st[q], v0);
         }
 #pragma unroll
-        for (int q = 0; q < NA; ++q) st[q].grp += half_angle(I[q], R[q]);
+        for (int q = 0; q < NA; ++q) {
+          float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+          geom_step(st[q], v0, n0, N0, D0);
+          geom_step(st[q], v1, n1, N1, D1);
+          cmul_wrap(D0, N0, D1, N1, r01, i01, st[q].kp, st[q].kn);
+          geom_step(st[q], v2, n2, N0, D0);
+          geom_step(st[q], v3, n3, N1, D1);
+          cmul_wrap(D0, N0, D1, N1, r23, i23, st[q].kp, st[q].kn);
+          cmul_wrap(r01, i01, r23, i23, R, I, st[q].kp, st[q].kn);
+          st[q].grp += half_angle(I, R);
+        }
       }
 #pragma unroll
       for (int q = 0; q < NA; ++q) kahan_flush(st[q]);
@@ -888,6 +913,115 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
     if (lane == 0 && ch + 2 < nchunks) fill(ch + 2, b);
   }
   return true;
+}
+
+// Per-lane evaluation, for a tile whose shared range list is long (its box
+// covers far more of the surface than any of its points needs, as when its
+// Morton-consecutive points straddle a jump of the curve): every lane walks
+// the cap tree for each of its own points in `todo` and streams that walk's
+// segments from global memory four entries at a time, with the same
+// products, wrap counting and compensation as the shared stream.  A node is
+// far from a point when the point lies outside the node's box grown by a
+// quarter of the box's longest side on every side (exact outside the box;
+// the margin keeps the cap's triangles at a distance from the point that is
+// a fixed fraction of their size, as the tile's own extent does for the
+// shared lists).  Returns the bits q of the points certainly inside; *pairs
+// receives the triangles evaluated.
+constexpr int kLaneWalkFloor = 2048;  // shared lists up to this long are always kept
+constexpr int kLaneWalkRatio = 3;     // longer ones go per lane when > ratio x the longest own walk
+
+__device__ __forceinline__ bool lane_far(const CapNode &nd, float x, float y, float z) {
+  const float m = 0.25f * fmaxf(nd.hi[0] - nd.lo[0], fmaxf(nd.hi[1] - nd.lo[1], nd.hi[2] - nd.lo[2]));
+  return nd.hi[0] + m < x || nd.lo[0] - m > x || nd.hi[1] + m < y || nd.lo[1] - m > y || nd.hi[2] + m < z ||
+         nd.lo[2] - m > z;
+}
+
+// Entries of a point's own walk (the same walk as lane_walk_caps).
+__device__ __noinline__ int lane_walk_entries(const LabelArgs &a, int root, float x, float y, float z) {
+  int stack[48];
+  int sp = 0, tot = 0;
+  stack[sp++] = root;
+  while (sp > 0) {
+    const CapNode nd = a.nodes[stack[--sp]];
+    if (lane_far(nd, x, y, z)) {
+      tot += nd.cap_cnt;
+    } else if (nd.left < 0) {
+      tot += nd.leaf_cnt;
+    } else if (sp + 2 <= 48) {
+      stack[sp++] = nd.right;
+      stack[sp++] = nd.left;
+    } else {
+      return INT_MAX;
+    }
+  }
+  return tot;
+}
+
+template <int P>
+__device__ __noinline__ uint32_t lane_walk_caps(const LabelArgs &a, const DevComp *cp, const float *thr, int base,
+                                                uint32_t todo, int lane, unsigned long long *pairs) {
+  const DevComp c = *cp;
+  uint32_t in = 0;
+  unsigned long long np = 0;
+  for (int q = 0; q < P; ++q) {
+    if (!((todo >> q) & 1u)) continue;
+    const int i = base + 32 * q + lane;
+    const float4 p = a.spts[i];
+    PState st;
+    st.px = p.x;
+    st.py = p.y;
+    st.pz = p.z;
+    st.grp = st.sum = st.comp = 0.f;
+    st.bad = __int_as_float(0x7f800000);
+    st.kp = st.kn = 0u;
+    int stack[48];
+    int sp = 0, b = 0, e = 0, g = 0;
+    stack[sp++] = c.cap_root;
+    for (;;) {
+      while (b >= e && sp > 0) {
+        const CapNode nd = a.nodes[stack[--sp]];
+        if (lane_far(nd, p.x, p.y, p.z)) {
+          b = nd.cap_begin;
+          e = b + nd.cap_cnt;
+          np += (unsigned long long)nd.cap_tris;
+        } else if (nd.left < 0) {
+          b = nd.leaf_begin;
+          e = b + nd.leaf_cnt;
+          np += (unsigned long long)nd.leaf_tris;
+        } else if (sp + 2 <= 48) {
+          stack[sp++] = nd.right;
+          stack[sp++] = nd.left;
+        } else {  // deeper than any tree of 2^28 triangles: cannot happen; left to the FP64 pass
+          st.bad = -1.f;
+          sp = 0;
+        }
+      }
+      if (b >= e) break;
+      const Entry *E = a.cseg + b;
+      const float4 v0 = __ldg(&E[0].v), n0 = __ldg(&E[0].n), v1 = __ldg(&E[1].v), n1 = __ldg(&E[1].n);
+      const float4 v2 = __ldg(&E[2].v), n2 = __ldg(&E[2].n), v3 = __ldg(&E[3].v), n3 = __ldg(&E[3].n);
+      if (v0.w == 2.f) window_init(st, v0);
+      float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+      geom_step(st, v0, n0, N0, D0);
+      geom_step(st, v1, n1, N1, D1);
+      cmul_wrap(D0, N0, D1, N1, r01, i01, st.kp, st.kn);
+      geom_step(st, v2, n2, N0, D0);
+      geom_step(st, v3, n3, N1, D1);
+      cmul_wrap(D0, N0, D1, N1, r23, i23, st.kp, st.kn);
+      cmul_wrap(r01, i01, r23, i23, R, I, st.kp, st.kn);
+      st.grp += half_angle(I, R);
+      b += 4;
+      if (++g == kGroup / 4) {
+        kahan_flush(st);
+        g = 0;
+      }
+    }
+    kahan_flush(st);
+    if (classify_store(a, c, thr, i, p.x, p.y, p.z, st.sum - st.comp, (int)st.kp - (int)st.kn, st.bad))
+      in |= 1u << q;
+  }
+  *pairs = np;
+  return in;
 }
 
 // Point-by-point evaluation of the groups in `act` (m of them), packed two
@@ -900,7 +1034,7 @@ template <int NA, int V, int P>
 __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, const float *thr, Entry *wbuf,
                                             uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane, int base, int n,
                                             uint32_t act, uint32_t list, int m, uint32_t &done, const int2 *rng,
-                                            int rtotal) {
+                                            int rtotal, int rtris) {
   PState st[NA];
   int idx[NA];
   const int half = lane >> 4;
@@ -917,7 +1051,7 @@ __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, 
     idx[j] = (valid && finite3(p.x, p.y, p.z)) ? i : -1;
   }
   if constexpr (V == 2) {
-    if (!stream_sums_caps<NA>(a, rng, rtotal, reinterpret_cast<float4 *>(wbuf), bar, ph0, ph1, lane, st))
+    if (!stream_sums_caps<NA>(a, rng, rtotal, wbuf, bar, ph0, ph1, lane, st))
       return false;
   } else {
     if (!stream_sums<NA, V>(a, cp, wbuf, bar, ph0, ph1, lane, st)) return false;
@@ -950,7 +1084,7 @@ __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, 
   }
   if (lane == 0)
     atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL),
-              (unsigned long long)evaluated * (V == 2 ? rtotal : c.tri_cnt));
+              (unsigned long long)evaluated * (V == 2 ? rtris : c.tri_cnt));
   return true;
 }
 
@@ -974,7 +1108,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
   __shared__ float s_rep[NW][NG][3];
   constexpr int RN = V == 2 ? kMaxRanges : 1;
   __shared__ int2 s_rng[NW][RN];   // form 2: the tile's range list of the compartment
-  __shared__ int s_rtot[NW];
+  __shared__ int s_rtot[NW][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, half = lane >> 4;
   Entry *wbuf = reinterpret_cast<Entry *>(smem_raw) + wid * 2 * kWChunk;
   uint64_t *bar = bars[wid];
@@ -1055,17 +1189,49 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         if (early) break;  // every point decided: no later compartment matters
         continue;          // no usable point in the tile
       }
-      int rtotal = 0;  // form 2: triangles standing for the surface near this tile
+      // form 2: the strip entries (and their triangles) standing for the
+      // surface near this tile
+      int rtotal = 0, rtris = 0;
       if constexpr (V == 2) {
         if (lane == 0) {
-          int tot = 0;
-          cap_ranges(a, cp, s_wbox[wid], s_rng[wid], &tot);
-          s_rtot[wid] = tot;
+          int tot = 0, nt = 0;
+          const int nr = cap_ranges(a, cp, s_wbox[wid], s_rng[wid], &tot, &nt, false);
+          s_rtot[wid][0] = nr < 0 ? -1 : tot;
+          s_rtot[wid][1] = nt;
         }
         __syncwarp();
-        rtotal = s_rtot[wid];
+        rtotal = s_rtot[wid][0];
+        rtris = s_rtot[wid][1];
+        uint32_t todo = 0;
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+          if (((usable >> q) & 1u) && !(early && ((done >> q) & 1u))) todo |= 1u << q;
+        bool per_lane = rtotal < 0 || !a.lane_walk;
+        if (!per_lane && rtotal > kLaneWalkFloor) {
+          // the longest of the points' own walks decides
+          int own = 0;
+#pragma unroll
+          for (int q = 0; q < P; ++q)
+            if ((todo >> q) & 1u) {
+              const float4 p = a.spts[base + 32 * q + lane];
+              own = max(own, lane_walk_entries(a, __ldg(&cp->cap_root), p.x, p.y, p.z));
+            }
+          own = __reduce_max_sync(0xffffffffu, own);
+          per_lane = (long long)rtotal > (long long)kLaneWalkRatio * own;
+        }
+        if (per_lane) {
+          unsigned long long pairs = 0;
+          done |= lane_walk_caps<P>(a, cp, thr, base, todo, lane, &pairs);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+          if (lane == 0) {
+            atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), pairs);
+            atomicAdd((unsigned long long *)(a.counters + CNT_LANE_TILES), 1ull);
+          }
+          continue;
+        }
       }
-      const unsigned long long surf = V == 2 ? (unsigned long long)rtotal : (unsigned long long)__ldg(&cp->tri_cnt);
+      const unsigned long long surf = V == 2 ? (unsigned long long)rtris : (unsigned long long)__ldg(&cp->tri_cnt);
       uint32_t coh = 0;  // groups whose points take a representative's winding number
       int kg[NG];
 #pragma unroll
@@ -1086,13 +1252,15 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         }
         const float4 rp = a.spts[first];
         const float rx = rp.x, ry = rp.y, rz = rp.z;
-        int k_t = 0, t_hit = -1;
+        int k_t = 0, t_hit = -1, scanned = 0;
         unsigned long long reps = 0;
         bool cert;
-        if constexpr (V == 2)
-          cert = rep_pass_caps(a, s_rng[wid], rtotal, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit);
-        else
+        if constexpr (V == 2) {
+          cert = rep_pass_caps(a, s_rng[wid], rtotal, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit, &scanned);
+        } else {
           cert = rep_pass(a, cp, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit);
+          scanned = t_hit;
+        }
         if (cert) {
           coh = need;
 #pragma unroll
@@ -1101,7 +1269,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         } else if (t_hit < 0) {
           reps += surf;  // completed, but the representative is uncertain
         } else {
-          reps += t_hit;
+          reps += scanned;
           uint32_t touched;
           if constexpr (V == 2)
             touched = touched_groups_caps<NG>(a, s_rng[wid], rtotal, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
@@ -1175,10 +1343,10 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         if ((act >> g) & 1u) list |= (uint32_t)g << (4 * m++);
       bool ok = true;
       switch ((m + 1) >> 1) {
-        case 1: ok = eval_groups<1, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
-        case 2: ok = eval_groups<(P >= 2 ? 2 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
-        case 3: ok = eval_groups<(P >= 3 ? 3 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
-        default: ok = eval_groups<P, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal); break;
+        case 1: ok = eval_groups<1, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
+        case 2: ok = eval_groups<(P >= 2 ? 2 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
+        case 3: ok = eval_groups<(P >= 3 ? 3 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
+        default: ok = eval_groups<P, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
       }
       if (!ok) {
         timed_out = true;
@@ -1388,9 +1556,11 @@ __device__ void strip_half_angle64(const Entry *E, int s, int e, double px, doub
 // FP64 re-evaluation over the cap tree: one block per uncertain pair, the
 // point's own range list (the tree walked for the point's zero-size box, so
 // leaves near the point and caps of every farther node), threads split the
-// triangles, plain FP64 Van Oosterom-Strackee terms with the exact triple
-// product, fixed-order block reduction.  Outside a node's box its cap
-// subtends its patch exactly, so the sum is Omega up to FP64 rounding.
+// segment entries, and every entry that closes a triangle window adds the
+// plain FP64 Van Oosterom-Strackee term of that triangle in its own
+// orientation (triple product from the vertices), fixed-order block
+// reduction.  Outside a node's box its cap subtends its patch exactly, so
+// the sum is Omega up to FP64 rounding.
 __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
   __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
   __shared__ int64_t s_group;
@@ -1399,7 +1569,7 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
   __shared__ unsigned long long s_mask[kRescueT];
   __shared__ double s_red[kRescueT / 32];
   __shared__ int2 s_rng[kMaxRanges];
-  __shared__ int s_nr, s_tot;
+  __shared__ int s_nr, s_tot, s_tris;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
   const int64_t n = a.counters[CNT_N];
@@ -1433,17 +1603,23 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
         const DevComp *cp = a.comps + s_rowcomp[row];
         if (tid == 0) {
           const float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
-          int tot = 0;
-          s_nr = cap_ranges(a, cp, box, s_rng, &tot);
+          int tot = 0, nt = 0;
+          s_nr = cap_ranges(a, cp, box, s_rng, &tot, &nt, true);
           s_tot = tot;
+          s_tris = nt;
         }
         __syncthreads();
         const int total = s_tot;
         double part = 0.0;
         int r = 0, rb = 0;
         for (int j = tid; j < total; j += kRescueT) {
-          const float4 *T = a.ctri + 4 * (int64_t)range_tri(s_rng, r, rb, j);
-          const float4 A = T[0], B = T[1], C = T[2];
+          float4 A, B, C, nn;
+          if (!seg_tri(a.cseg, range_pos(s_rng, r, rb, j), A, B, C, nn)) continue;
+          if (C.w < 0.f) {  // the window runs against the triangle's orientation
+            const float4 t = A;
+            A = B;
+            B = t;
+          }
           const double x1 = (double)A.x - px, y1 = (double)A.y - py, z1 = (double)A.z - pz;
           const double x2 = (double)B.x - px, y2 = (double)B.y - py, z2 = (double)B.z - pz;
           const double x3 = (double)C.x - px, y3 = (double)C.y - py, z3 = (double)C.z - pz;
@@ -1468,7 +1644,7 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
         if (tid == 0) {
           if (a.omega) a.omega[(int64_t)row * a.omega_ld + a.perm[i]] = (float)om;
           atomicAdd((unsigned long long *)(a.counters + CNT_UNC), 1ull);
-          atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)total);
+          atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)s_tris);
         }
       }
       if (tid == 0 && set_bits) atomicOr(a.in_mask + i, set_bits);
@@ -1648,6 +1824,7 @@ __global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
     cnt[CNT_PAIRS_RESCUE] = 0;
     cnt[CNT_COHERENT] = 0;
     cnt[CNT_REP_PAIRS] = 0;
+    cnt[CNT_LANE_TILES] = 0;
     int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
     for (int k = 0; k < 3; ++k) {
       box[k] = INT32_MAX;
@@ -2253,9 +2430,10 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.ncomp = C;
   a.fp32_only = plan.opts.precision == ZEF_FP32_ONLY;
   a.coherence = !(plan.opts.flags & ZEF_NO_TILE_COHERENCE);
+  a.lane_walk = (plan.opts.flags & ZEF_POINT_WALK) ? 0 : 1;
   a.early = plan.omega == nullptr && !plan.full_masks;
   a.nodes = ctx->d_nodes;
-  a.ctri = ctx->d_ctri;
+  a.cseg = ctx->d_cseg;
   a.masks_out = plan.masks;
   if (plan.timed) cudaEventRecord(ctx->ev[1], s);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {

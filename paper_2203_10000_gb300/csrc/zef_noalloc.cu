@@ -94,6 +94,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
+  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -175,6 +176,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
     stats->tiles = h[CNT_TILES];
     stats->coherent_pairs = h[CNT_COHERENT];
     stats->representative_pairs = h[CNT_REP_PAIRS];
+    stats->lane_walk_items = h[CNT_LANE_TILES];
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;

@@ -34,6 +34,7 @@ ZEF_FP32_RESCUE = 0
 ZEF_FP64_PLAIN = 1
 ZEF_FP32_ONLY = 2
 ZEF_NO_TILE_COHERENCE = 1
+ZEF_POINT_WALK = 2
 MAX_COMPARTMENTS = 64
 
 STATUS_NAMES = {0: "ZEF_OK", 1: "ZEF_ERR_INVALID_ARG", 2: "ZEF_ERR_SURFACE_NOT_CLOSED",
@@ -61,7 +62,8 @@ class LabelStats(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
                 ("ms_total", ctypes.c_float), ("ms_label", ctypes.c_float),
                 ("ms_rescue", ctypes.c_float), ("reserved", ctypes.c_float),
-                ("coherent_pairs", ctypes.c_int64), ("representative_pairs", ctypes.c_int64)]
+                ("coherent_pairs", ctypes.c_int64), ("representative_pairs", ctypes.c_int64),
+                ("lane_walk_items", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -184,10 +186,10 @@ def _contig(x, dtype_np, dtype_name):
 
 
 def make_opts(margin=0.0, winding_tol=0.0, precision=ZEF_FP32_RESCUE, block_threads=0,
-              points_per_thread=0, kernel=0, coherence=True) -> LabelOpts:
+              points_per_thread=0, kernel=0, coherence=True, point_walk=False) -> LabelOpts:
     o = LabelOpts()
     o.kernel = kernel
-    o.flags = 0 if coherence else ZEF_NO_TILE_COHERENCE
+    o.flags = (0 if coherence else ZEF_NO_TILE_COHERENCE) | (ZEF_POINT_WALK if point_walk else 0)
     o.margin = margin
     o.winding_tol = winding_tol
     o.precision = precision
@@ -284,17 +286,17 @@ class Context:
         return int(_lib.zef_debug_wait_probe(self._h, int(limit_ns)))
 
     def cap_tree(self, index: int):
-        """(boxes float32 (n, 6), links int32 (n, 6), triangles float32 (m, 16))
+        """(boxes float32 (n, 6), links int32 (n, 8), entries float32 (m, 8))
         of compartment `index`'s cap tree (diagnostics)."""
-        nn, nt = _I64(0), _I64(0)
-        self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(nt),
+        nn, ne = _I64(0), _I64(0)
+        self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(ne),
                                             None, None, None))
         boxes = np.empty((nn.value, 6), np.float32)
-        links = np.empty((nn.value, 6), np.int32)
-        tris = np.empty((nt.value, 16), np.float32)
-        self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(nt),
-                                            boxes.ctypes.data, links.ctypes.data, tris.ctypes.data))
-        return boxes, links, tris
+        links = np.empty((nn.value, 8), np.int32)
+        ent = np.empty((ne.value, 8), np.float32)
+        self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(ne),
+                                            boxes.ctypes.data, links.ctypes.data, ent.ctypes.data))
+        return boxes, links, ent
 
     def fma_rate(self, fp64: bool = False) -> float:
         """Measured FMA throughput of the device in TFLOP/s (diagnostics)."""

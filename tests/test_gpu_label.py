@@ -173,6 +173,29 @@ def test_kernel_forms_match_oracle(zef, oracle_mod, kernel):
     assert_parity(lab, om, olab, oom)
 
 
+def test_point_walk_matches_shared_lists(zef, oracle_mod):
+    """Kernel form 0 with every point walking the cap tree for itself (the
+    point as a zero-size box) instead of sharing its tile's list: the same
+    arithmetic over the point's own leaves and caps, so the labels equal the
+    shared-list evaluation and the oracle."""
+    w = zs.config1(npts_limit=0)
+    g = zs.lattice_centroids(40, 5.0, (-100.0, -100.0, -100.0))   # 320,000 centroids
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    lab_s, om_s, st_s = gpu_label(ctx, g, opts=zef.make_opts(coherence=False))
+    lab_p, om_p, st_p = gpu_label(ctx, g, opts=zef.make_opts(coherence=False, point_walk=True))
+    assert st_p["lane_walk_items"] > 0.5 * st_p["tiles"]
+    assert np.array_equal(lab_s, lab_p)
+    assert np.abs(om_s.astype(np.float64) - om_p).max() <= 2 * OMEGA_TOL
+    idx = zs.sample_rows(g, 3000, seed=9)
+    olab, oom = oracle_mod.label_points(g[idx], w.surfaces, w.priority)
+    assert_parity(lab_p[idx], om_p[:, idx], olab, oom)
+    # the flag is validated
+    o = zef.make_opts()
+    o.flags = 4
+    with pytest.raises(zef.ZefError):
+        ctx.label_points(torch.from_numpy(g[:100]).cuda(), opts=o)
+
+
 def test_autotuned_shape_matches_fixed_shape(zef, oracle_mod):
     """With no shape given the library times its candidate shapes on a
     sample of the call's points and caches the winner; the per-point
@@ -376,3 +399,5 @@ def test_config1_full_size_sampled(zef, oracle_mod, kernel):
     assert_parity(lab[idx], om[:, idx], olab, oom)
     assert 0 < st["pairs_evaluated"] < st["pairs_nominal"]
     assert st["uncertain_pairs"] < 0.001 * st["points"]
+    if kernel == 0:  # tiles across a jump of the Morton order walk per point
+        assert st["lane_walk_items"] >= 1

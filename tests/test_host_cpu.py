@@ -182,18 +182,53 @@ def test_strip_efficiency_head_surfaces(zef):
         assert n_ent < 1.10 * s.ntris, (s.name, n_ent, s.ntris, n_strips)
 
 
-def _tree_omega(oracle_mod, p, tri16):
-    v = tri16[:, [0, 1, 2, 4, 5, 6, 8, 9, 10]].reshape(-1, 3).astype(np.float64)
+def _seg_triangles(e):
+    """Triangles (m, 3, 3) of a strip segment (entries (k, 8)), each with its
+    own orientation: entry j with weight +-1 closes the window (x[j-2],
+    x[j-1], x[j]), reversed when the weight is -1."""
+    x = e[:, :3].astype(np.float64)
+    out = []
+    for j in range(e.shape[0]):
+        if abs(e[j, 3]) == 1.0:
+            a, b = (j - 2, j - 1) if e[j, 3] > 0 else (j - 1, j - 2)
+            out.append(np.stack([x[a], x[b], x[j]]))
+    return np.array(out).reshape(-1, 3, 3)
+
+
+def _tri_omega(oracle_mod, p, tri):
+    v = tri.reshape(-1, 3)
     t = np.arange(v.shape[0], dtype=np.int32).reshape(-1, 3)
     return oracle_mod.solid_angle(p, v, t) if t.size else np.zeros(p.shape[0])
+
+
+def _strip_omega(p, e):
+    """Omega of a strip segment evaluated window by window in FP64, as the
+    kernel does: a reset entry (weight 2) restarts the window at its vertex,
+    every entry's window (a, b, c) adds 2 atan2(N, D) with N = n . (c - p)."""
+    om = np.zeros(p.shape[0])
+    x = e[:, :3].astype(np.float64)
+    n = e[:, 4:7].astype(np.float64)
+    for q, pt in enumerate(p):
+        a = b = None
+        for j in range(e.shape[0]):
+            c = x[j] - pt
+            if e[j, 3] == 2.0:
+                a = b = c
+            N = n[j] @ c
+            ra, rb, rc = np.linalg.norm(a), np.linalg.norm(b), np.linalg.norm(c)
+            D = ra * rb * rc + (a @ b) * rc + (a @ c) * rb + (b @ c) * ra
+            om[q] += 2.0 * np.arctan2(N, D)
+            a, b = b, c
+    return om
 
 
 @pytest.mark.parametrize("which", ["sphere", "torus", "ellipsoid"])
 def test_cap_tree_identity(zef, oracle_mod, which):
     """Every node of the library's cap tree: outside the node's box its
-    caps' solid angle equals that of its leaf triangles (FP64 oracle), the
-    leaves cover every triangle once, and the root (the closed surface) has
-    no cap."""
+    cap's solid angle equals that of its leaves' triangles (FP64 oracle),
+    the leaf strips hold every triangle once with its orientation, every
+    window that is not a triangle repeats a vertex with a zero normal, and
+    the root (the closed surface) has no cap."""
     if which == "sphere":
         s = zs.config0().surfaces[0]
         v, t = s.verts, s.tris
@@ -203,16 +238,58 @@ def test_cap_tree_identity(zef, oracle_mod, which):
         v, t = zs.perturbed_ellipsoid(16, (9.0, 7.0, 5.0), amp=1.0, seed=3)
     ctx = _host_ctx(zef)
     ctx.add_compartment(1, v, t)
-    boxes, links, tris = ctx.cap_tree(0)
-    assert links[0, 5] == 0                                    # root: closed, no cap
-    leaves = links[links[:, 0] < 0]
-    assert leaves[:, 3].sum() == t.shape[0] and leaves[:, 3].max() <= 64
+    boxes, links, ent = ctx.cap_tree(0)
+    assert links[0, 5] == 0 and links[0, 7] == 0                 # root: closed, no cap
+    leaf = links[:, 0] < 0
+    assert links[leaf, 6].sum() == t.shape[0] and links[leaf, 6].max() <= 64
+
+    def seg(k, cap):
+        b, c = (links[k, 4], links[k, 5]) if cap else (links[k, 2], links[k, 3])
+        return ent[b:b + c]
+
+    # segment format: reset first, whole groups of four, identity windows
+    for k in range(len(boxes)):
+        for cap in ([False, True] if leaf[k] else [True]):
+            e = seg(k, cap)
+            if e.shape[0] == 0:
+                continue
+            assert e.shape[0] % 4 == 0 and e[0, 3] == 2.0 and not np.any(e[1:, 3] == 2.0)
+            for j in range(e.shape[0]):
+                if abs(e[j, 3]) == 1.0:
+                    continue
+                assert np.all(e[j, 4:8] == 0)
+                if j >= 1:
+                    w = [e[max(j - 2, 0), :3], e[j - 1, :3], e[j, :3]]
+                    assert any(np.array_equal(w[u], w[w2]) for u in range(3) for w2 in range(u + 1, 3))
+            tri = _seg_triangles(e)
+            assert tri.shape[0] == (links[k, 7] if cap else links[k, 6])
+            nn = np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0])
+            tw = e[np.abs(e[:, 3]) == 1.0]
+            np.testing.assert_allclose(tw[:, 4:7], nn, rtol=1e-5, atol=1e-6 * max(np.abs(nn).max(), 1e-30))
+            np.testing.assert_allclose(tw[:, 7], np.linalg.norm(nn, axis=1) / 8192.0, rtol=1e-5)
+    # the leaves hold every oriented triangle once
+    index = {tuple(p): i for i, p in enumerate(v.astype(np.float32).tolist())}
+    got = []
+    for k in np.nonzero(leaf)[0]:
+        for tr in _seg_triangles(seg(k, False)):
+            ids = [index[tuple(np.float32(q).tolist())] for q in tr]
+            r = int(np.argmin(ids))
+            got.append(tuple(ids[r:] + ids[:r]))
+    want = []
+    for f in t.tolist():
+        r = int(np.argmin(f))
+        want.append(tuple(f[r:] + f[:r]))
+    assert sorted(got) == sorted(want)
+    # entries per triangle (strip overhead): caps are single zigzag strips
+    assert links[leaf, 3].sum() <= 2.0 * t.shape[0]
+    assert links[:, 5].sum() <= 1.2 * links[:, 7].sum() + 8 * len(boxes)
+
     rng = np.random.default_rng(7)
     checked = 0
 
     def leaf_tris(k):
-        if links[k, 0] < 0:
-            return [tris[links[k, 2]:links[k, 2] + links[k, 3]]]
+        if leaf[k]:
+            return [_seg_triangles(seg(k, False))]
         return leaf_tris(links[k, 0]) + leaf_tris(links[k, 1])
 
     for k in rng.choice(len(boxes), size=min(40, len(boxes)), replace=False):
@@ -225,13 +302,15 @@ def test_cap_tree_identity(zef, oracle_mod, which):
                               lo - rng.uniform(0.01, 3.0, (8, 3)) * ext.max()])
         outside = np.any((pts < lo) | (pts > hi), axis=1)
         pts = pts[outside]
-        patch = np.concatenate(leaf_tris(k))
-        cap = tris[links[k, 4]:links[k, 4] + links[k, 5]]
-        a = _tree_omega(oracle_mod, pts, patch)
-        b = _tree_omega(oracle_mod, pts, cap)
+        a = _tri_omega(oracle_mod, pts, np.concatenate(leaf_tris(k)))
+        b = _tri_omega(oracle_mod, pts, _seg_triangles(seg(k, True)))
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-9)
+        if checked < 4:
+            # the window-by-window evaluation of the strips; N uses the stored
+            # float32 normals (relative rounding 2^-24 per component), hence
+            # the wider tolerance against the exact triple products
+            np.testing.assert_allclose(_strip_omega(pts[:3], seg(k, True)), b[:3], rtol=0, atol=1e-6)
+            if leaf[k]:
+                np.testing.assert_allclose(_strip_omega(pts[:3], seg(k, False)), a[:3], rtol=0, atol=1e-6)
         checked += 1
     assert checked >= 10
-    # normals and kappa terms as documented
-    n = np.cross(tris[:, 4:7].astype(np.float64) - tris[:, 0:3], tris[:, 8:11].astype(np.float64) - tris[:, 0:3])
-    np.testing.assert_allclose(tris[:, 12:15], n, rtol=1e-5, atol=1e-6 * np.abs(n).max())
