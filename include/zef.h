@@ -289,7 +289,7 @@ zef_status zef_label_elements(zef_ctx *ctx, const float *nodes, int64_t n_nodes,
              omega must be DEVICE pointers (ZEF_ERR_INVALID_ARG otherwise)
      n       0 <= n <= ZEF_NOALLOC_MAX_POINTS, else ZEF_ERR_INVALID_ARG
    All scratch comes from one fixed-size array compiled into the library
-   (about 10.7 MB, held on every GPU that loads the library until the process
+   (about 11 MB, held on every GPU that loads the library until the process
    exits).  The compartments must already be registered (ZEF_ERR_NOT_READY
    otherwise).  The first call on a device looks up the array's device
    address (cudaGetSymbolAddress) and caches it: make that first call before

@@ -96,7 +96,7 @@ struct LabelBuffers {
   int64_t cap_points = 0;   // points the buffers hold
   int64_t cap_tiles = 0;
   int64_t cap_items = 0;
-  int64_t cap_unc = 0;
+  int64_t cap_unc = 0;      // capacity of unc_list (0: no list)
   float4 *spts = nullptr;       // sorted points (x, y, z, unused)
   int32_t *perm = nullptr;      // sorted position -> original index
   uint32_t *keys = nullptr;     // binning key per original point
@@ -107,7 +107,7 @@ struct LabelBuffers {
   uint32_t *flags = nullptr;    // [C * tiles] work-list flags, scanned in place
   uint32_t *block_sums = nullptr;
   int2 *items = nullptr;        // (tile, comp)
-  int2 *unc_list = nullptr;     // (sorted point, comp)
+  int2 *unc_list = nullptr;     // uncertain (sorted point, priority row) pairs
   int64_t *counters = nullptr;  // device counters, see Counter enum
   int32_t *labels_tmp = nullptr;
   float *pts_tmp = nullptr;     // staging for host inputs
@@ -115,6 +115,8 @@ struct LabelBuffers {
   int64_t cap_omega = 0;
   float *tune_pts = nullptr;    // autotuner sample (2^20 points)
 };
+
+constexpr int64_t kUncListCap = 1 << 15;  // uncertain-pair list of the cap-tree re-evaluation
 
 enum Counter {
   CNT_N = 0,          // points of this call
@@ -144,6 +146,7 @@ enum Counter {
   CNT_CL_GREEN,       // tets split along one to three edges
   CNT_CL_GEXTRA,      // children those splits add
   CNT_LANE_TILES,     // cap trees: (tile, compartment) pairs evaluated by per-lane walks
+  CNT_UNC_LIST,       // uncertain pairs appended to the pair list (may exceed its capacity)
   CNT_COUNT_ = 32
 };
 

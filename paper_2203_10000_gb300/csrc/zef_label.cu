@@ -292,6 +292,8 @@ struct LabelArgs {
   unsigned long long *masks_out;  // nullable: inside bits per point in the caller's order
   const CapNode *nodes;  // cap trees
   const Entry *cseg;     // cap-tree strip segments
+  int2 *unc_list;        // uncertain (sorted point, row) pairs of the cap-tree re-evaluation
+  int64_t unc_cap;
 };
 
 // Classification of one (point, compartment) pair after the FP32 sum:
@@ -1553,14 +1555,167 @@ __device__ void strip_half_angle64(const Entry *E, int s, int e, double px, doub
   *wraps = K;
 }
 
-// FP64 re-evaluation over the cap tree: one block per uncertain pair, the
+// FP64 strip evaluation of one group of four cap-tree segment entries
+// (positions pos .. pos + 3, a multiple of four: a group never straddles two
+// segments) seen from p: the window enters the group as (E[pos-2], E[pos-1])
+// (both in the same segment, since a segment starts at a multiple of four
+// with its reset entry) or restarts at a reset entry; every window that is a
+// triangle contributes the factor D + iN with N = w R_a . (R_b x R_c) (w the
+// entry's orientation sign, the exact triple product of the stored
+// vertices) and D = r_a r_b r_c + (R_a . R_b) r_c + (R_a . R_c) r_b +
+// (R_b . R_c) r_a (Sec. 2.1.3), and the group returns the argument of the
+// product with the 2 pi wraps of the partial products counted in *K exactly
+// as the FP32 kernel does.
+__device__ __forceinline__ bool sign64(double x) { return __double_as_longlong(x) < 0; }
+
+__device__ double group64(const Entry *E, int pos, double px, double py, double pz, int *K) {
+  double a[3], b[3], ra, rb;
+  const float4 v0 = E[pos].v;
+  if (v0.w == 2.f) {
+    a[0] = b[0] = (double)v0.x - px;
+    a[1] = b[1] = (double)v0.y - py;
+    a[2] = b[2] = (double)v0.z - pz;
+    ra = rb = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  } else {
+    const float4 u = E[pos - 2].v, w = E[pos - 1].v;
+    a[0] = (double)u.x - px; a[1] = (double)u.y - py; a[2] = (double)u.z - pz;
+    b[0] = (double)w.x - px; b[1] = (double)w.y - py; b[2] = (double)w.z - pz;
+    ra = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    rb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  }
+  double R = 1.0, I = 0.0;
+  bool have = false;
+  int k = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 v = E[pos + q].v;
+    const double c[3] = {(double)v.x - px, (double)v.y - py, (double)v.z - pz};
+    const double rc = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    if (fabsf(v.w) == 1.f) {
+      const double N = (double)v.w * (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
+                                      a[2] * (b[0] * c[1] - b[1] * c[0]));
+      const double dab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+      const double dac = a[0] * c[0] + a[1] * c[1] + a[2] * c[2];
+      const double dbc = b[0] * c[0] + b[1] * c[1] + b[2] * c[2];
+      const double D = ra * rb * rc + dab * rc + dac * rb + dbc * ra;
+      if (!have) {
+        R = D;
+        I = N;
+        have = true;
+      } else {
+        const double cr = R * D - I * N, ci = R * N + I * D;
+        k += (!sign64(I) && !sign64(N) && sign64(ci)) ? 1 : 0;
+        k -= (sign64(I) && sign64(N) && !sign64(ci)) ? 1 : 0;
+        R = cr;
+        I = ci;
+      }
+    }
+    a[0] = b[0]; a[1] = b[1]; a[2] = b[2];
+    b[0] = c[0]; b[1] = c[1]; b[2] = c[2];
+    ra = rb;
+    rb = rc;
+  }
+  *K += k;
+  return have ? atan2(I, R) : 0.0;
+}
+
+// FP64 half-angle sum over a range list, the block's threads splitting the
+// groups of four (fixed assignment and reduction order: deterministic);
+// every thread of the block returns the block's total, Omega / 2.
+__device__ double block_sum64(const LabelArgs &a, const int2 *rng, int total, double px, double py, double pz,
+                              double *s_red, int *s_kred) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double part = 0.0;
+  int K = 0;
+  int r = 0, rb = 0;
+  for (int j = 4 * tid; j < total; j += 4 * kRescueT) part += group64(a.cseg, range_pos(rng, r, rb, j), px, py, pz, &K);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+    K += __shfl_xor_sync(0xffffffffu, K, o);
+  }
+  if (lane == 0) {
+    s_red[wid] = part;
+    s_kred[wid] = K;
+  }
+  __syncthreads();
+  double half = 0.0;
+  int kt = 0;
+#pragma unroll
+  for (int w = 0; w < kRescueT / 32; ++w) {
+    half += s_red[w];
+    kt += s_kred[w];
+  }
+  __syncthreads();
+  return half + 6.283185307179586476925 * (double)kt;
+}
+
+// Result of one FP64 re-evaluated pair: Omega, the inside bit, counters.
+__device__ __forceinline__ void store64(const LabelArgs &a, int row, int64_t i, double half, int tris) {
+  const double om = 2.0 * half;
+  if (om > 6.283185307179586476925) atomicOr(a.in_mask + i, 1ull << row);
+  if (a.omega) a.omega[(int64_t)row * a.omega_ld + a.perm[i]] = (float)om;
+  atomicAdd((unsigned long long *)(a.counters + CNT_UNC), 1ull);
+  atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)tris);
+}
+
+// Uncertain (point, row) pairs of the FP32 kernel into the pair list.
+__global__ void __launch_bounds__(256) k_unc_list(LabelArgs a) {
+  const int64_t n = a.counters[CNT_N];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long m = a.unc_mask[i];
+    while (m) {
+      const int row = __ffsll((long long)m) - 1;
+      m &= m - 1;
+      const unsigned long long slot = atomicAdd((unsigned long long *)(a.counters + CNT_UNC_LIST), 1ull);
+      if ((int64_t)slot < a.unc_cap) a.unc_list[slot] = make_int2((int)i, row);
+    }
+  }
+}
+
+// FP64 re-evaluation over the cap tree, one block per listed pair: the
 // point's own range list (the tree walked for the point's zero-size box, so
-// leaves near the point and caps of every farther node), threads split the
-// segment entries, and every entry that closes a triangle window adds the
-// plain FP64 Van Oosterom-Strackee term of that triangle in its own
-// orientation (triple product from the vertices), fixed-order block
-// reduction.  Outside a node's box its cap subtends its patch exactly, so
-// the sum is Omega up to FP64 rounding.
+// leaves near the point and caps of every farther node), group64 over it.
+// Outside a node's box its cap subtends its patch exactly, so the sum is
+// Omega up to FP64 rounding.  Runs only when the list held every pair.
+__global__ void __launch_bounds__(kRescueT) k_rescue64_list(LabelArgs a) {
+  __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
+  __shared__ int64_t s_pair;
+  __shared__ double s_red[kRescueT / 32];
+  __shared__ int s_kred[kRescueT / 32];
+  __shared__ int2 s_rng[kMaxRanges];
+  __shared__ int s_tot, s_tris;
+  const int64_t npairs = a.counters[CNT_UNC_LIST];
+  if (npairs > a.unc_cap) return;  // k_rescue64_caps takes them all
+  const int tid = threadIdx.x;
+  for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
+  for (;;) {
+    if (tid == 0) {
+      const int64_t pr = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_UNC_WORK), 1ull);
+      s_pair = pr;
+      if (pr < npairs) {
+        const int2 e = a.unc_list[pr];
+        const float4 p = a.spts[e.x];
+        const float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
+        int tot = 0, nt = 0;
+        cap_ranges(a, a.comps + s_rowcomp[e.y], box, s_rng, &tot, &nt, true);
+        s_tot = tot;
+        s_tris = nt;
+      }
+    }
+    __syncthreads();
+    if (s_pair >= npairs) break;
+    const int2 e = a.unc_list[s_pair];
+    const float4 p = a.spts[e.x];
+    const double half = block_sum64(a, s_rng, s_tot, p.x, p.y, p.z, s_red, s_kred);
+    if (tid == 0) store64(a, e.y, e.x, half, s_tris);
+    __syncthreads();
+  }
+}
+
+// The same re-evaluation by point groups (every uncertain pair of a group of
+// kRescueT sorted points in turn), for calls whose uncertain pairs overflow
+// the pair list.
 __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
   __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
   __shared__ int64_t s_group;
@@ -1568,9 +1723,11 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
   __shared__ int s_list[kRescueT];
   __shared__ unsigned long long s_mask[kRescueT];
   __shared__ double s_red[kRescueT / 32];
+  __shared__ int s_kred[kRescueT / 32];
   __shared__ int2 s_rng[kMaxRanges];
-  __shared__ int s_nr, s_tot, s_tris;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  __shared__ int s_tot, s_tris;
+  if (a.counters[CNT_UNC_LIST] <= a.unc_cap) return;  // k_rescue64_list took them
+  const int tid = threadIdx.x;
   for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
   const int64_t n = a.counters[CNT_N];
   const int64_t ngroups = (n + kRescueT - 1) / kRescueT;
@@ -1595,59 +1752,20 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
       const int64_t i = g * kRescueT + s_list[e];
       unsigned long long mm = s_mask[e];
       const float4 p = a.spts[i];
-      const double px = p.x, py = p.y, pz = p.z;
-      unsigned long long set_bits = 0ull;
       while (mm) {
         const int row = __ffsll((long long)mm) - 1;
         mm &= mm - 1;
-        const DevComp *cp = a.comps + s_rowcomp[row];
         if (tid == 0) {
           const float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
           int tot = 0, nt = 0;
-          s_nr = cap_ranges(a, cp, box, s_rng, &tot, &nt, true);
+          cap_ranges(a, a.comps + s_rowcomp[row], box, s_rng, &tot, &nt, true);
           s_tot = tot;
           s_tris = nt;
         }
         __syncthreads();
-        const int total = s_tot;
-        double part = 0.0;
-        int r = 0, rb = 0;
-        for (int j = tid; j < total; j += kRescueT) {
-          float4 A, B, C, nn;
-          if (!seg_tri(a.cseg, range_pos(s_rng, r, rb, j), A, B, C, nn)) continue;
-          if (C.w < 0.f) {  // the window runs against the triangle's orientation
-            const float4 t = A;
-            A = B;
-            B = t;
-          }
-          const double x1 = (double)A.x - px, y1 = (double)A.y - py, z1 = (double)A.z - pz;
-          const double x2 = (double)B.x - px, y2 = (double)B.y - py, z2 = (double)B.z - pz;
-          const double x3 = (double)C.x - px, y3 = (double)C.y - py, z3 = (double)C.z - pz;
-          const double r1 = sqrt(x1 * x1 + y1 * y1 + z1 * z1);
-          const double r2 = sqrt(x2 * x2 + y2 * y2 + z2 * z2);
-          const double r3 = sqrt(x3 * x3 + y3 * y3 + z3 * z3);
-          const double N = x1 * (y2 * z3 - z2 * y3) + y1 * (z2 * x3 - x2 * z3) + z1 * (x2 * y3 - y2 * x3);
-          const double D = r1 * r2 * r3 + (x1 * x2 + y1 * y2 + z1 * z2) * r3 + (x1 * x3 + y1 * y3 + z1 * z3) * r2 +
-                           (x2 * x3 + y2 * y3 + z2 * z3) * r1;
-          part += atan2(N, D);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        if (lane == 0) s_red[wid] = part;
-        __syncthreads();
-        double half = 0.0;
-#pragma unroll
-        for (int w = 0; w < kRescueT / 32; ++w) half += s_red[w];
-        __syncthreads();
-        const double om = 2.0 * half;
-        if (om > 6.283185307179586476925) set_bits |= 1ull << row;
-        if (tid == 0) {
-          if (a.omega) a.omega[(int64_t)row * a.omega_ld + a.perm[i]] = (float)om;
-          atomicAdd((unsigned long long *)(a.counters + CNT_UNC), 1ull);
-          atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)s_tris);
-        }
+        const double half = block_sum64(a, s_rng, s_tot, p.x, p.y, p.z, s_red, s_kred);
+        if (tid == 0) store64(a, row, i, half, s_tris);
       }
-      if (tid == 0 && set_bits) atomicOr(a.in_mask + i, set_bits);
     }
     __syncthreads();
   }
@@ -1825,6 +1943,7 @@ __global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
     cnt[CNT_COHERENT] = 0;
     cnt[CNT_REP_PAIRS] = 0;
     cnt[CNT_LANE_TILES] = 0;
+    cnt[CNT_UNC_LIST] = 0;
     int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
     for (int k = 0; k < 3; ++k) {
       box[k] = INT32_MAX;
@@ -2361,6 +2480,11 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap) {
     cudaError_t e = cudaMalloc(&b.hist, (size_t)kBuckets * sizeof(uint32_t));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(hist)");
   }
+  if (!b.unc_list) {
+    cudaError_t e = cudaMalloc(&b.unc_list, (size_t)kUncListCap * sizeof(int2));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(uncertain pairs)");
+    b.cap_unc = kUncListCap;
+  }
   if (!b.counters) {
     cudaError_t e = cudaMalloc(&b.counters, CNT_COUNT_ * sizeof(int64_t));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(counters)");
@@ -2434,6 +2558,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.early = plan.omega == nullptr && !plan.full_masks;
   a.nodes = ctx->d_nodes;
   a.cseg = ctx->d_cseg;
+  a.unc_list = b.unc_list;
+  a.unc_cap = b.unc_list ? b.cap_unc : 0;
   a.masks_out = plan.masks;
   if (plan.timed) cudaEventRecord(ctx->ev[1], s);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
@@ -2447,8 +2573,14 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   if (plan.timed) cudaEventRecord(ctx->ev[2], s);
   if (plan.timed) cudaEventRecord(ctx->ev[3], s);
   if (plan.opts.precision == ZEF_FP32_RESCUE) {
-    if (plan.shape.variant == 2) k_rescue64_caps<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
-    else k_rescue64<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+    if (plan.shape.variant == 2) {
+      // the pair list when it holds every uncertain pair, else by point groups
+      k_unc_list<<<g, 256, 0, s>>>(a);
+      k_rescue64_list<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+      k_rescue64_caps<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+    } else {
+      k_rescue64<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+    }
   }
   if (plan.timed) cudaEventRecord(ctx->ev[4], s);
   k_resolve<<<g, 256, 0, s>>>(a, plan.pts, plan.labels, ctx->d_row_ids);

@@ -44,7 +44,8 @@ constexpr size_t kOffHist = align256(kOffBox + kMaxTiles * 6 * sizeof(float));
 constexpr size_t kOffFlags = align256(kOffHist + kBuckets * sizeof(uint32_t));
 constexpr size_t kOffSums = align256(kOffFlags + kMaxFlags * sizeof(uint32_t));
 constexpr size_t kOffItems = align256(kOffSums + kMaxBlockSums * sizeof(uint32_t));
-constexpr size_t kOffCnt = align256(kOffItems + kMaxFlags * sizeof(int2));
+constexpr size_t kOffUncList = align256(kOffItems + kMaxFlags * sizeof(int2));
+constexpr size_t kOffCnt = align256(kOffUncList + kUncListCap * sizeof(int2));
 constexpr size_t kScratchBytes = align256(kOffCnt + CNT_COUNT_ * sizeof(int64_t));
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -132,6 +133,8 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
   view.flags = reinterpret_cast<uint32_t *>(s + kOffFlags);
   view.block_sums = reinterpret_cast<uint32_t *>(s + kOffSums);
   view.items = reinterpret_cast<int2 *>(s + kOffItems);
+  view.unc_list = reinterpret_cast<int2 *>(s + kOffUncList);
+  view.cap_unc = kUncListCap;
   view.counters = reinterpret_cast<int64_t *>(s + kOffCnt);
 
   LabelPlan plan;
