@@ -118,7 +118,7 @@ typedef struct zef_label_opts {
 #define ZEF_NO_TILE_COHERENCE 1u
 /* Kernel form 0: by default the points of a tile share one list of leaf and
    cap segments (the tree walked for the tile's box), except where that list
-   is longer than 2048 entries and more than three times the longest of the
+   is longer than 4096 entries and more than three times the longest of the
    points' own walks (a tile whose box spans much of a surface): there every
    point walks the tree for itself.  This flag makes every point walk the
    tree for itself. */

@@ -929,7 +929,7 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
 // a fixed fraction of their size, as the tile's own extent does for the
 // shared lists).  Returns the bits q of the points certainly inside; *pairs
 // receives the triangles evaluated.
-constexpr int kLaneWalkFloor = 2048;  // shared lists up to this long are always kept
+constexpr int kLaneWalkFloor = 4096;  // shared lists up to this long are always kept
 constexpr int kLaneWalkRatio = 3;     // longer ones go per lane when > ratio x the longest own walk
 
 __device__ __forceinline__ bool lane_far(const CapNode &nd, float x, float y, float z) {
@@ -1210,14 +1210,14 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
           if (((usable >> q) & 1u) && !(early && ((done >> q) & 1u))) todo |= 1u << q;
         bool per_lane = rtotal < 0 || !a.lane_walk;
         if (!per_lane && rtotal > kLaneWalkFloor) {
-          // the longest of the points' own walks decides
+          // the longest own walk of one point per lane (the lanes walk in
+          // parallel) decides
           int own = 0;
-#pragma unroll
-          for (int q = 0; q < P; ++q)
-            if ((todo >> q) & 1u) {
-              const float4 p = a.spts[base + 32 * q + lane];
-              own = max(own, lane_walk_entries(a, __ldg(&cp->cap_root), p.x, p.y, p.z));
-            }
+          if (todo) {
+            const int q = __ffs(todo) - 1;
+            const float4 p = a.spts[base + 32 * q + lane];
+            own = lane_walk_entries(a, __ldg(&cp->cap_root), p.x, p.y, p.z);
+          }
           own = __reduce_max_sync(0xffffffffu, own);
           per_lane = (long long)rtotal > (long long)kLaneWalkRatio * own;
         }
