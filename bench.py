@@ -385,7 +385,8 @@ def run_ours(args):
             rec = json.load(open(tpath)).get(f"config{args.config}")
             src = os.path.join(ROOT, "paper_2203_10000_gb300", "csrc", "zef_label.cu")
             sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-            shape = f"k_label32<{st['block_threads']},{st['points_per_thread']},{args.kernel}>"
+            variant = 2 if args.kernel == 0 else args.kernel - 1  # template argument of the form
+            shape = f"k_label32<{st['block_threads']},{st['points_per_thread']},{variant}>"
             if rec and rec["source_sha256_prefix"] == sha and rec["kernel"] == shape:
                 traffic = rec["bytes_per_launch"]
         except Exception:
