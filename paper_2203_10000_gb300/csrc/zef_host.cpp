@@ -224,6 +224,7 @@ void zef_destroy(zef_ctx *ctx) {
   fr(ctx->d_tris);
   fr(ctx->d_nodes);
   fr(ctx->d_cseg);
+  fr(ctx->d_ctidx);
   fr(ctx->d_comps);
   fr(ctx->d_row_ids);
   fr(ctx->d_lpt);
@@ -461,7 +462,8 @@ zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int
   {
     const int64_t node_base = (int64_t)ctx->h_nodes.size(), seg_base = (int64_t)ctx->h_cseg.size();
     int64_t leaf = 0;
-    build_cap_tree(V.data(), T.data(), nt, node_base, seg_base, ctx->h_nodes, ctx->h_cseg, &ch.cap_root, &leaf);
+    build_cap_tree(V.data(), T.data(), nt, node_base, seg_base, (int64_t)ctx->h_ctidx.size(), ctx->h_nodes,
+                   ctx->h_cseg, ctx->h_ctidx, &ch.cap_root, &leaf);
     ch.cseg_off = seg_base;
     ch.cseg_leaf = leaf;
     if ((int64_t)ctx->h_nodes.size() > INT32_MAX || (int64_t)ctx->h_cseg.size() > INT32_MAX)
@@ -886,6 +888,16 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
     ctx->d_cseg_cap = (int64_t)gs.size();
   }
   if (!gs.empty()) CK(cudaMemcpy(ctx->d_cseg, gs.data(), gs.size() * sizeof(Entry), cudaMemcpyHostToDevice), "upload cap segments");
+  if (ctx->d_ctidx_cap < (int64_t)ctx->h_ctidx.size()) {
+    if (ctx->d_ctidx) cudaFree(ctx->d_ctidx);
+    ctx->d_ctidx = nullptr;
+    CK(cudaMalloc(&ctx->d_ctidx, std::max<size_t>(ctx->h_ctidx.size(), 1) * sizeof(int32_t)),
+       "cudaMalloc(cap-tree triangle order)");
+    ctx->d_ctidx_cap = (int64_t)ctx->h_ctidx.size();
+  }
+  if (!ctx->h_ctidx.empty())
+    CK(cudaMemcpy(ctx->d_ctidx, ctx->h_ctidx.data(), ctx->h_ctidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice),
+       "upload cap-tree triangle order");
   std::vector<DevComp> dc(C);
   std::vector<int32_t> rows(C), lpt(C);
   for (int i = 0; i < C; ++i) {

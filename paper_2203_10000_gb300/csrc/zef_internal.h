@@ -53,11 +53,13 @@ struct __align__(16) CapNode {
   int32_t leaf_begin, leaf_cnt;  // leaf: strip segment of its triangles
   int32_t cap_begin, cap_cnt;    // the node's cap: zigzag strip segment
   int32_t leaf_tris, cap_tris;
-  int32_t pad_[2];
+  int32_t tri_begin;             // leaf: first of its triangles in the tree-ordered index array
+  int32_t pad_;
 };
 static_assert(sizeof(CapNode) == 64, "CapNode is four 16-byte words");
 void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_base, int64_t seg_base,
-                    std::vector<CapNode> &nodes, std::vector<Entry> &seg, int32_t *root, int64_t *leaf_entries);
+                    int64_t tidx_base, std::vector<CapNode> &nodes, std::vector<Entry> &seg,
+                    std::vector<int32_t> &tidx, int32_t *root, int64_t *leaf_entries);
 
 // Device status word bits (ctx->d_status[0]); [1] holds detail.
 enum : uint32_t {
@@ -175,6 +177,7 @@ struct zef_ctx {
   std::vector<float4> h_tris;         // 3 per triangle (w unused)
   std::vector<zef::CapNode> h_nodes;  // cap trees of all compartments
   std::vector<zef::Entry> h_cseg;     // cap-tree strip segments
+  std::vector<int32_t> h_ctidx;       // cap-tree leaves' triangles (compartment-local indices), tree order
 
   bool dirty = true;
   uint64_t gen = 0;   // upload generation: cached graphs keyed on it see every change of the surfaces
@@ -190,6 +193,8 @@ struct zef_ctx {
   float *d_dop = nullptr;             // [C][kDop] hull support bounds (scaled coordinates)
   zef::CapNode *d_nodes = nullptr;    // cap trees (scaled)
   zef::Entry *d_cseg = nullptr;       // cap-tree strip segments (scaled)
+  int32_t *d_ctidx = nullptr;         // cap-tree leaves' triangles
+  int64_t d_ctidx_cap = 0;
   int64_t d_nodes_cap = 0, d_cseg_cap = 0;
   int64_t d_entries_cap = 0, d_tris_cap = 0;
 

@@ -1975,14 +1975,23 @@ __global__ void __launch_bounds__(256) k_bbox(const float *pts, int64_t *cnt, un
       hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
     }
   }
-  if ((threadIdx.x & 31) == 0) {
-    int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
+  // block reduction, then one atomic per block and bound (six addresses
+  // shared by the whole grid: per-warp atomics serialised on them)
+  __shared__ float red[6][8];
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
     for (int k = 0; k < 3; ++k) {
-      if (lo[k] <= hi[k]) {
-        atomicMin(box + k, f2o(lo[k]));
-        atomicMax(box + 3 + k, f2o(hi[k]));
-      }
+      red[k][wid] = lo[k];
+      red[3 + k][wid] = hi[k];
     }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    float v = red[k][0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = k < 3 ? fminf(v, red[k][q]) : fmaxf(v, red[k][q]);
+    int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
+    if (k < 3 && v != INFINITY) atomicMin(box + k, f2o(v));
+    if (k >= 3 && v != -INFINITY) atomicMax(box + k, f2o(v));
   }
 }
 
@@ -2041,40 +2050,31 @@ __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt,
   }
 }
 
+// Bounding box of every tile of `tile` (= 32 P) consecutive sorted points:
+// one warp per tile, P points per lane, shuffle reductions.
 __global__ void __launch_bounds__(256) k_tile_box(const float4 *spts, int64_t *cnt, float *tile_box, int tile) {
   const int64_t n = cnt[CNT_N];
   const int64_t ntiles = cnt[CNT_TILES];
-  __shared__ float red[6][8];
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += warps) {
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const int64_t b = t * tile;
     const int64_t e = min(b + tile, n);
-    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+    for (int64_t i = b + lane; i < e; i += 32) {
       const float4 p = spts[i];
       if (finite3(p.x, p.y, p.z)) {
         lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
         hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
       }
     }
+#pragma unroll
     for (int k = 0; k < 3; ++k)
       for (int o = 16; o > 0; o >>= 1) {
         lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
         hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
       }
-    const int wid = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-      for (int k = 0; k < 3; ++k) {
-        red[k][wid] = lo[k];
-        red[3 + k][wid] = hi[k];
-      }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-      const int k = threadIdx.x;
-      float v = red[k][0];
-      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = k < 3 ? fminf(v, red[k][q]) : fmaxf(v, red[k][q]);
-      tile_box[t * 6 + k] = v;
-    }
-    __syncthreads();
+    if (lane < 6) tile_box[t * 6 + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
   }
 }
 
@@ -2516,7 +2516,7 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   if (st) return st;
   k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm, ctx->scale);
   const int64_t tiles_cap = (ncap + tile - 1) / tile;
-  k_tile_box<<<grid_for(ctx, tiles_cap * 256, 256), 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
+  k_tile_box<<<grid_for(ctx, tiles_cap * 32, 256), 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
     // (tile, compartment) items for the plain FP64 kernel
     k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,

@@ -271,16 +271,26 @@ __global__ void __launch_bounds__(256) k_in_flag(Adj g, const unsigned long long
 // order) the nearest intersection with the compartment's triangles
 // (Moller-Trumbore in FP32 on the scaled coordinates, inclusive by a
 // relative 2^-20 so that an edge through a shared triangle edge still hits),
-// then the averaged move.
+// then the averaged move.  The candidates are the
+// triangles of the cap-tree leaves whose box meets the edge's box grown by
+// 2^-10 (lane 0 walks the tree; a triangle the edge meets lies in such a
+// leaf, so the minimum is the one over all triangles); more than kInLeaves
+// such leaves fall back to every triangle.
+constexpr int kInLeaves = 32;
+
 __global__ void __launch_bounds__(256) k_in_move(Adj g, const float *x, float *out, const unsigned long long *mask,
                                                  int row, const uint32_t *pos, const float4 *tris, int tri_cnt,
-                                                 float scale, float zeta) {
-  const int lane = threadIdx.x & 31;
+                                                 const CapNode *nodes, int root, const int32_t *ctidx, float scale,
+                                                 float zeta) {
+  __shared__ int2 s_leaf[8][kInLeaves];  // per warp: (first position in ctidx, triangles)
+  __shared__ int s_nleaf[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t listed = g.words[PP_LISTED];
   const unsigned long long bit = 1ull << row;
   constexpr float kEps = 9.5367431640625e-07f;  // 2^-20
+  constexpr float kBoxMargin = 9.765625e-04f;   // 2^-10
   for (int64_t w = warp; w < listed; w += nwarps) {
     const int32_t i = (int32_t)pos[w];
     const float p0 = x[3 * (int64_t)i] * scale, p1 = x[3 * (int64_t)i + 1] * scale, p2 = x[3 * (int64_t)i + 2] * scale;
@@ -292,24 +302,58 @@ __global__ void __launch_bounds__(256) k_in_move(Adj g, const float *x, float *o
       const float e0 = x[3 * (int64_t)j] - x[3 * (int64_t)i], e1 = x[3 * (int64_t)j + 1] - x[3 * (int64_t)i + 1],
                   e2 = x[3 * (int64_t)j + 2] - x[3 * (int64_t)i + 2];
       const float d0 = e0 * scale, d1 = e1 * scale, d2 = e2 * scale;
-      float tmin = INFINITY;
-      for (int t = lane; t < tri_cnt; t += 32) {
-        const float4 A = tris[3 * t], B = tris[3 * t + 1], C = tris[3 * t + 2];
-        const float ax = B.x - A.x, ay = B.y - A.y, az = B.z - A.z;   // edge 1
-        const float bx = C.x - A.x, by = C.y - A.y, bz = C.z - A.z;   // edge 2
-        const float px = d1 * bz - d2 * by, py = d2 * bx - d0 * bz, pz = d0 * by - d1 * bx;
-        const float det = ax * px + ay * py + az * pz;
-        if (det == 0.f) continue;
-        const float inv = 1.f / det;
-        const float tx = p0 - A.x, ty = p1 - A.y, tz = p2 - A.z;
-        const float u = (tx * px + ty * py + tz * pz) * inv;
-        if (u < -kEps || u > 1.f + kEps) continue;
-        const float qx = ty * az - tz * ay, qy = tz * ax - tx * az, qz = tx * ay - ty * ax;
-        const float v = (d0 * qx + d1 * qy + d2 * qz) * inv;
-        if (v < -kEps || u + v > 1.f + kEps) continue;
-        const float tt = (bx * qx + by * qy + bz * qz) * inv;
-        if (tt >= 0.f && tt <= 1.f + kEps) tmin = fminf(tmin, tt);
+      if (lane == 0) {
+        const float lo0 = fminf(p0, p0 + d0) - kBoxMargin, hi0 = fmaxf(p0, p0 + d0) + kBoxMargin;
+        const float lo1 = fminf(p1, p1 + d1) - kBoxMargin, hi1 = fmaxf(p1, p1 + d1) + kBoxMargin;
+        const float lo2 = fminf(p2, p2 + d2) - kBoxMargin, hi2 = fmaxf(p2, p2 + d2) + kBoxMargin;
+        int stack[48];
+        int sp = 0, nl = 0;
+        stack[sp++] = root;
+        while (sp > 0) {
+          const CapNode nd = nodes[stack[--sp]];
+          if (nd.hi[0] < lo0 || nd.lo[0] > hi0 || nd.hi[1] < lo1 || nd.lo[1] > hi1 || nd.hi[2] < lo2 ||
+              nd.lo[2] > hi2)
+            continue;
+          if (nd.left < 0) {
+            if (nl < kInLeaves) s_leaf[wid][nl] = make_int2(nd.tri_begin, nd.leaf_tris);
+            ++nl;
+          } else if (sp + 2 <= 48) {
+            stack[sp++] = nd.right;
+            stack[sp++] = nd.left;
+          } else {  // deeper than any tree of 2^28 triangles: cannot happen
+            nl = kInLeaves + 1;
+            break;
+          }
+        }
+        s_nleaf[wid] = nl;
       }
+      __syncwarp();
+      const int nl = s_nleaf[wid];
+      const bool all = nl > kInLeaves;
+      const int nsrc = all ? 1 : nl;
+      float tmin = INFINITY;
+      for (int l = 0; l < nsrc; ++l) {
+        const int2 L = all ? make_int2(0, tri_cnt) : s_leaf[wid][l];
+        for (int q = lane; q < L.y; q += 32) {
+          const int t = all ? q : ctidx[L.x + q];
+          const float4 A = tris[3 * t], B = tris[3 * t + 1], C = tris[3 * t + 2];
+          const float ax = B.x - A.x, ay = B.y - A.y, az = B.z - A.z;   // edge 1
+          const float bx = C.x - A.x, by = C.y - A.y, bz = C.z - A.z;   // edge 2
+          const float px = d1 * bz - d2 * by, py = d2 * bx - d0 * bz, pz = d0 * by - d1 * bx;
+          const float det = ax * px + ay * py + az * pz;
+          if (det == 0.f) continue;
+          const float inv = 1.f / det;
+          const float tx = p0 - A.x, ty = p1 - A.y, tz = p2 - A.z;
+          const float u = (tx * px + ty * py + tz * pz) * inv;
+          if (u < -kEps || u > 1.f + kEps) continue;
+          const float qx = ty * az - tz * ay, qy = tz * ax - tx * az, qz = tx * ay - ty * ax;
+          const float v = (d0 * qx + d1 * qy + d2 * qz) * inv;
+          if (v < -kEps || u + v > 1.f + kEps) continue;
+          const float tt = (bx * qx + by * qy + bz * qz) * inv;
+          if (tt >= 0.f && tt <= 1.f + kEps) tmin = fminf(tmin, tt);
+        }
+      }
+      __syncwarp();  // lane 0 rewrites the leaf list for the next edge
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
       if (tmin < INFINITY) {
@@ -528,7 +572,8 @@ zef_status inflate_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tet
   const CompHost &c = ctx->comps[(size_t)ci];
   // one warp per listed node; the grid covers the node count at most
   k_in_move<<<grid_blocks(ctx, n * 32, 256), 256, 0, s>>>(g, x, out, mask, row, list, ctx->d_tris + c.tri_off * 3,
-                                                          (int)c.nt, ctx->scale, zeta);
+                                                          (int)c.nt, ctx->d_nodes, c.cap_root, ctx->d_ctidx,
+                                                          ctx->scale, zeta);
   CK(cudaGetLastError(), "k_in_move");
   int64_t words[PP_WORDS];
   CK(cudaMemcpyAsync(x, out, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, s), "write positions");

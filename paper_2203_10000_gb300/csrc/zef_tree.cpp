@@ -317,6 +317,7 @@ struct Builder {
       cancel_into(boundary, edges);
       std::vector<int64_t> mine(idx.begin() + b, idx.begin() + e);
       SegWriter sw{V, &leaf_seg};
+      node.tri_begin = (int32_t)b;
       node.leaf_begin = (int32_t)leaf_seg.size();
       leaf_strips(T, mine, sw);
       node.leaf_cnt = (int32_t)leaf_seg.size() - node.leaf_begin;
@@ -362,10 +363,13 @@ struct Builder {
 }  // namespace
 
 // Builds the cap tree of one closed surface: appends its nodes (indices from
-// node_base) and its segment block (entries from seg_base: the leaves'
-// segments, leaf_entries of them, then the caps').
+// node_base), its segment block (entries from seg_base: the leaves'
+// segments, leaf_entries of them, then the caps') and its triangle indices
+// in leaf order (positions from tidx_base; a leaf's triangles are
+// tidx[tri_begin .. tri_begin + leaf_tris)).
 void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_base, int64_t seg_base,
-                    std::vector<CapNode> &nodes, std::vector<Entry> &seg, int32_t *root, int64_t *leaf_entries) {
+                    int64_t tidx_base, std::vector<CapNode> &nodes, std::vector<Entry> &seg,
+                    std::vector<int32_t> &tidx, int32_t *root, int64_t *leaf_entries) {
   Builder bd;
   bd.V = V;
   bd.T = T;
@@ -389,7 +393,9 @@ void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_b
     }
     n.leaf_begin += (int32_t)seg_base;
     n.cap_begin += (int32_t)(seg_base + nleaf);
+    n.tri_begin += (int32_t)tidx_base;
   }
+  for (int64_t t : bd.idx) tidx.push_back((int32_t)t);
   *root = (int32_t)node_base;
   *leaf_entries = nleaf;
   nodes.insert(nodes.end(), local.begin(), local.end());
