@@ -267,6 +267,47 @@ def test_empty_and_tiny_inputs(zef, oracle_mod):
         assert_parity(lab, om, olab, oom)
 
 
+def _pinched_spheres(freq, radius, cid):
+    """Two geodesic spheres that share one vertex (the second is the first
+    reflected through its vertex of largest x, orientation restored): a
+    closed, oriented surface whose patches have boundary loops through the
+    shared vertex twice."""
+    u, t = zs.geodesic_sphere(freq)
+    va = u * radius
+    k = int(np.argmax(va[:, 0]))
+    P = va[k]
+    vb = 2.0 * P - va
+    nb = va.shape[0]
+    tb = t[:, [0, 2, 1]] + nb
+    tb = np.where(tb == k + nb, k, tb)
+    v = np.concatenate([va, vb]).astype(np.float32)
+    return zs.Surface(cid, "pinched", v, np.concatenate([t, tb]).astype(np.int32))
+
+
+@pytest.mark.parametrize("kernel,walk", [(0, False), (0, True), (1, False)])
+def test_small_and_pinched_surfaces(zef, oracle_mod, kernel, walk):
+    """Surfaces of a single cap-tree leaf (a tetrahedron, a 12-triangle box:
+    no caps at all), of a few leaves (a 108-triangle box), and a pinched one
+    (two spheres sharing a vertex) against the oracle."""
+    tet_v = np.array([[0, 0, 0], [10, 0, 0], [0, 10, 0], [0, 0, 10]], np.float32) + np.float32(-30.0)
+    tet_t = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], np.int32)
+    surfs = [zs.Surface(4, "tet", tet_v, tet_t),
+             zs.Surface(3, "box1", *zs.box_surface((5.0, -20.0, -20.0), (17.0, -8.0, -9.0), 1)),
+             zs.Surface(2, "box3", *zs.box_surface((-12.0, 6.0, 4.0), (3.0, 19.0, 16.0), 3)),
+             _pinched_spheres(3, 9.0, 1)]
+    prio = [4, 3, 2, 1]
+    rng = np.random.default_rng(31)
+    pts = rng.uniform(-32.0, 32.0, size=(40000, 3)).astype(np.float32)
+    pts = np.concatenate([pts, surfs[3].verts[rng.integers(0, len(surfs[3].verts), 2000)] *
+                          np.float32(0.97)]).astype(np.float32)
+    ctx = make_ctx(zef, surfs, prio)
+    lab, om, st = gpu_label(ctx, pts, opts=zef.make_opts(kernel=kernel, point_walk=walk))
+    olab, oom = oracle_mod.label_points(pts, surfs, prio)
+    off_surface(oom)
+    assert_parity(lab, om, olab, oom)
+    assert np.count_nonzero(lab == 1) > 1000 and np.count_nonzero(lab == 4) > 10
+
+
 def test_nonfinite_points(zef, oracle_mod):
     w = zs.config0()
     pts = w.points[:3000].copy()

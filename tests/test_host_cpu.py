@@ -222,7 +222,7 @@ def _strip_omega(p, e):
     return om
 
 
-@pytest.mark.parametrize("which", ["sphere", "torus", "ellipsoid"])
+@pytest.mark.parametrize("which", ["sphere", "torus", "ellipsoid", "pinched"])
 def test_cap_tree_identity(zef, oracle_mod, which):
     """Every node of the library's cap tree: outside the node's box its
     cap's solid angle equals that of its leaves' triangles (FP64 oracle),
@@ -234,8 +234,17 @@ def test_cap_tree_identity(zef, oracle_mod, which):
         v, t = s.verts, s.tris
     elif which == "torus":
         v, t = zs.torus(10.0, 3.0, 40, 18, seed=1, amp=0.5)
-    else:
+    elif which == "ellipsoid":
         v, t = zs.perturbed_ellipsoid(16, (9.0, 7.0, 5.0), amp=1.0, seed=3)
+    else:
+        # two spheres sharing one vertex: patch boundaries through it twice
+        u, t0 = zs.geodesic_sphere(4)
+        va = u * 9.0
+        k = int(np.argmax(va[:, 0]))
+        tb = t0[:, [0, 2, 1]] + va.shape[0]
+        tb = np.where(tb == k + va.shape[0], k, tb)
+        v = np.concatenate([va, 2.0 * va[k] - va]).astype(np.float32)
+        t = np.concatenate([t0, tb]).astype(np.int32)
     ctx = _host_ctx(zef)
     ctx.add_compartment(1, v, t)
     boxes, links, ent = ctx.cap_tree(0)
@@ -268,7 +277,9 @@ def test_cap_tree_identity(zef, oracle_mod, which):
             np.testing.assert_allclose(tw[:, 4:7], nn, rtol=1e-5, atol=1e-6 * max(np.abs(nn).max(), 1e-30))
             np.testing.assert_allclose(tw[:, 7], np.linalg.norm(nn, axis=1) / 8192.0, rtol=1e-5)
     # the leaves hold every oriented triangle once
-    index = {tuple(p): i for i, p in enumerate(v.astype(np.float32).tolist())}
+    index = {}
+    for i in np.unique(t):  # referenced vertices (the pinched case holds an unused duplicate)
+        index.setdefault(tuple(v[i].astype(np.float32).tolist()), int(i))
     got = []
     for k in np.nonzero(leaf)[0]:
         for tr in _seg_triangles(seg(k, False)):
