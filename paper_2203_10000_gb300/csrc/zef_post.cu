@@ -66,6 +66,7 @@ struct Adj {
 };
 
 // every tet's six edges into the table; the first insertion counts the edge
+// in both end nodes' degrees (the edge count is half the degree sum)
 __global__ void __launch_bounds__(256) k_pp_edges(Adj g, const int32_t *tets, int64_t m, uint32_t *status) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
     int32_t v[4];
@@ -91,7 +92,6 @@ __global__ void __launch_bounds__(256) k_pp_edges(Adj g, const int32_t *tets, in
         if (prev == kNoKey) {
           atomicAdd(g.deg + min(a, b), 1u);
           atomicAdd(g.deg + max(a, b), 1u);
-          atomicAdd((unsigned long long *)(g.words + PP_EDGES), 1ull);
           break;
         }
         if (prev == key) break;
@@ -419,14 +419,16 @@ zef_status build_adjacency(zef_ctx *ctx, const int32_t *tets, int64_t m, int64_t
   st = scan_exclusive(ctx, g.deg, nullptr, 1, n + 1, nullptr, (uint32_t *)ctx->pp_buf[5]);
   if (st) return st;
   int64_t words[PP_WORDS];
-  CK(cudaMemcpyAsync(words, g.words, sizeof(words), cudaMemcpyDeviceToHost, s), "read edge count");
+  uint32_t deg_sum = 0;  // 2 x edges: the scanned degrees' last entry
+  CK(cudaMemcpyAsync(words, g.words, sizeof(words), cudaMemcpyDeviceToHost, s), "read adjacency status");
+  CK(cudaMemcpyAsync(&deg_sum, g.deg + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read edge count");
   CK(cudaStreamSynchronize(s), "build adjacency");
   if (words[PP_BAD]) {
     zef_synchronize(ctx);  // clears the recorded status
     return fail(ctx, ZEF_ERR_INVALID_ARG, "a tet references a node index outside [0, num_nodes)");
   }
-  *edges = words[PP_EDGES];
-  if ((st = pp_grow(ctx, 3, (size_t)std::max<int64_t>(2 * words[PP_EDGES], 1) * sizeof(int32_t)))) return st;
+  *edges = (int64_t)deg_sum / 2;
+  if ((st = pp_grow(ctx, 3, (size_t)std::max<int64_t>((int64_t)deg_sum, 1) * sizeof(int32_t)))) return st;
   g.nbr = (int32_t *)ctx->pp_buf[3];
   k_pp_scatter<<<grid_blocks(ctx, cap, 256), 256, 0, s>>>(g);
   k_pp_sort_rows<<<grid_blocks(ctx, n, 256), 256, 0, s>>>(g);
