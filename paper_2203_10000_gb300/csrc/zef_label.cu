@@ -1995,6 +1995,20 @@ __global__ void __launch_bounds__(256) k_bbox(const float *pts, int64_t *cnt, un
   }
 }
 
+// Warp-aggregated increment of ctr[key]: the lanes with equal keys share one
+// atomic (neighbouring points often fall in one bucket); returns the counter
+// before the increment plus the lane's rank among them.  Every lane of the
+// warp calls it; lanes with valid = false take no part.
+__device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key, bool valid, int lane) {
+  const uint32_t k = valid ? key : 0xffffffffu;  // keys have 21 bits
+  const uint32_t peers = __match_any_sync(0xffffffffu, k);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (valid && lane == leader) base = atomicAdd(ctr + key, (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
 __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, uint32_t *keys, uint32_t *hist) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
   const int *box = reinterpret_cast<const int *>(cnt + CNT_BOX);
@@ -2004,22 +2018,29 @@ __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, ui
     float ext = o2f(box[3 + k]) - lo[k];
     sc[k] = ext > 0.f ? (float)(1 << kMortonBits) / ext : 0.f;
   }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float *p = pts + 3 * (off + i);
-    float x = p[0], y = p[1], z = p[2];
+  const int lane = threadIdx.x & 31;
+  // warp-uniform loop: all lanes take part in the aggregated increments
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    const bool valid = i < n;
     uint32_t key = 0;
-    if (finite3(x, y, z)) {
-      uint32_t q[3];
-      float v[3] = {x, y, z};
-      for (int k = 0; k < 3; ++k) {
-        float f = (v[k] - lo[k]) * sc[k];
-        int qi = (int)f;
-        q[k] = (uint32_t)min(max(qi, 0), (1 << kMortonBits) - 1);
+    if (valid) {
+      const float *p = pts + 3 * (off + i);
+      const float x = p[0], y = p[1], z = p[2];
+      if (finite3(x, y, z)) {
+        uint32_t q[3];
+        const float v[3] = {x, y, z};
+        for (int k = 0; k < 3; ++k) {
+          const float f = (v[k] - lo[k]) * sc[k];
+          const int qi = (int)f;
+          q[k] = (uint32_t)min(max(qi, 0), (1 << kMortonBits) - 1);
+        }
+        key = spread7(q[0]) | (spread7(q[1]) << 1) | (spread7(q[2]) << 2);
       }
-      key = spread7(q[0]) | (spread7(q[1]) << 1) | (spread7(q[2]) << 2);
+      keys[i] = key;
     }
-    keys[i] = key;
-    atomicAdd(hist + key, 1u);
+    agg_inc(hist, key, valid, lane);
   }
 }
 
@@ -2034,9 +2055,14 @@ __device__ __forceinline__ float scaled_coord(float x, float s) {
 __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt, const uint32_t *keys,
                                                 uint32_t *cursor, float4 *spts, int32_t *perm, float scale) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    const bool valid = i < n;
+    const uint32_t pos = agg_inc(cursor, valid ? keys[i] : 0u, valid, lane);
+    if (!valid) continue;
     const float *p = pts + 3 * (off + i);
-    const uint32_t pos = atomicAdd(cursor + keys[i], 1u);
     const float x = p[0], y = p[1], z = p[2];
     float4 q;
     if (finite3(x, y, z)) {
