@@ -12,28 +12,36 @@
 //   scan           exclusive scan of the histogram
 //   k_scatter      points into bucket order (float4) + permutation
 //   k_tile_box     bounding box of every tile of consecutive sorted points
-//   k_flags/scan/k_emit
-//                  work list of (tile, compartment) whose boxes overlap,
-//                  ordered by decreasing compartment triangle count (LPT);
-//                  a point outside a closed surface's box has winding number
-//                  0, so the culling is exact
-//   k_label32      persistent FP32 kernel over the work list (hot loop)
-//   k_rescue64     FP64 re-evaluation of the uncertain (point, compartment)
-//                  pairs over the full surface
+//   k_tile_work/scan/k_tile_scatter
+//                  work list of the tiles whose box meets some compartment's
+//                  box and convex-hull bound, largest estimated work first;
+//                  a point outside a closed surface's box or hull has
+//                  winding number 0, so the culling is exact (k_flags/scan/
+//                  k_emit: (tile, compartment) items for the plain FP64 kernel)
+//   k_label32      persistent FP32 kernel over the work list (hot loop); the
+//                  default form walks each compartment's cap tree for the
+//                  tile (far patches replaced by their caps, zef_tree.cpp)
+//   k_unc_list + k_rescue64_list (cap-tree form; k_rescue64_caps when the
+//                  pair list overflows) / k_rescue64 (strip forms)
+//                  FP64 re-evaluation of the uncertain (point, compartment)
+//                  pairs
 //   k_resolve      priority resolve + un-permute
 //
-// FP32 hot loop.  Triangles of a compartment are stored as triangle strips
-// (one new vertex per triangle), staged into shared memory by 1-D bulk TMA
-// copies (cp.async.bulk + mbarrier, double buffered) and broadcast to every
-// thread; each thread holds P points in registers.  With the window (a, b, c)
-// of the strip and R_k = v_k - p:
+// FP32 hot loop.  Surfaces (whole, or the leaves and caps a tile's walk of the
+// cap tree lists) are stored as triangle strips (one new vertex per
+// triangle), staged into shared memory by 1-D bulk TMA copies
+// (cp.async.bulk + mbarrier, double buffered) and broadcast to every thread;
+// each thread holds P points in registers.  With the window (a, b, c) of the
+// strip and R_k = v_k - p:
 //     N = R_c . n            (n = (v2 - v1) x (v3 - v1) of the triangle, host
 //                             precomputed in FP64; equal to R1 . (R2 x R3))
 //     D = r_a r_b r_c + (R_a . R_b) r_c + (R_a . R_c) r_b + (R_b . R_c) r_a
 // where R_a, R_b, r_a, r_b and r_a r_b + R_a . R_b are carried from the two
-// previous strip steps.  atan2 is a range-reduced minimax polynomial (see
-// half_angle).  Omega is accumulated plainly over groups of 16 entries and the
-// group sums are combined with Kahan compensation.
+// previous strip steps.  The (D + iN) factors of four consecutive steps are
+// multiplied with their 2 pi wraps counted exactly and one atan2 is taken of
+// the product (a range-reduced minimax polynomial, see half_angle).  Omega
+// is accumulated plainly over groups of 16 entries and the group sums are
+// combined with Kahan compensation.
 //
 // A (point, compartment) pair is sent to the FP64 re-evaluation when
 //   |Omega32 - 2 pi| < margin                (the stated margin), or
