@@ -119,6 +119,10 @@ struct LabelBuffers {
 };
 
 constexpr int64_t kUncListCap = 1 << 15;  // uncertain-pair list of the cap-tree re-evaluation
+constexpr int kSplitPairs = 1024;         // up to this many listed pairs split over several blocks
+constexpr int kMaxParts = 8;              // blocks per split pair
+// the list, then the split pairs' partial sums and completion counts
+constexpr size_t kUncBytes = (size_t)kUncListCap * 8 + (size_t)kSplitPairs * kMaxParts * 8 + (size_t)kSplitPairs * 4;
 
 enum Counter {
   CNT_N = 0,          // points of this call

@@ -302,6 +302,8 @@ struct LabelArgs {
   const Entry *cseg;     // cap-tree strip segments
   int2 *unc_list;        // uncertain (sorted point, row) pairs of the cap-tree re-evaluation
   int64_t unc_cap;
+  double *unc_part;      // [kSplitPairs][kMaxParts] partial half-angle sums of split pairs
+  uint32_t *unc_done;    // [kSplitPairs] parts finished
 };
 
 // Classification of one (point, compartment) pair after the FP32 sum:
@@ -1627,16 +1629,17 @@ __device__ double group64(const Entry *E, int pos, double px, double py, double 
   return have ? atan2(I, R) : 0.0;
 }
 
-// FP64 half-angle sum over a range list, the block's threads splitting the
-// groups of four (fixed assignment and reduction order: deterministic);
-// every thread of the block returns the block's total, Omega / 2.
-__device__ double block_sum64(const LabelArgs &a, const int2 *rng, int total, double px, double py, double pz,
+// FP64 half-angle sum over the flattened entries [j0, j1) of a range list
+// (multiples of four), the block's threads splitting the groups of four
+// (fixed assignment and reduction order: deterministic); every thread of the
+// block returns the block's total.
+__device__ double block_sum64(const LabelArgs &a, const int2 *rng, int j0, int j1, double px, double py, double pz,
                               double *s_red, int *s_kred) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   double part = 0.0;
   int K = 0;
   int r = 0, rb = 0;
-  for (int j = 4 * tid; j < total; j += 4 * kRescueT) part += group64(a.cseg, range_pos(rng, r, rb, j), px, py, pz, &K);
+  for (int j = j0 + 4 * tid; j < j1; j += 4 * kRescueT) part += group64(a.cseg, range_pos(rng, r, rb, j), px, py, pz, &K);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -1670,6 +1673,8 @@ __device__ __forceinline__ void store64(const LabelArgs &a, int row, int64_t i, 
 // Uncertain (point, row) pairs of the FP32 kernel into the pair list.
 __global__ void __launch_bounds__(256) k_unc_list(LabelArgs a) {
   const int64_t n = a.counters[CNT_N];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < kSplitPairs; j += (int64_t)gridDim.x * blockDim.x)
+    a.unc_done[j] = 0u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long m = a.unc_mask[i];
     while (m) {
@@ -1681,28 +1686,39 @@ __global__ void __launch_bounds__(256) k_unc_list(LabelArgs a) {
   }
 }
 
-// FP64 re-evaluation over the cap tree, one block per listed pair: the
-// point's own range list (the tree walked for the point's zero-size box, so
-// leaves near the point and caps of every farther node), group64 over it.
-// Outside a node's box its cap subtends its patch exactly, so the sum is
-// Omega up to FP64 rounding.  Runs only when the list held every pair.
+// FP64 re-evaluation over the cap tree by listed pair: the point's own
+// range list (the tree walked for the point's zero-size box, so leaves near
+// the point and caps of every farther node), group64 over it.  Outside a
+// node's box its cap subtends its patch exactly, so the sum is Omega up to
+// FP64 rounding.  GB300's FP64 pipe is slow, so when the list holds at most
+// kSplitPairs pairs each pair is split into P parts (as many as the grid's
+// blocks allow, at most kMaxParts): every part walks the tree, sums its
+// share of the groups, and the last part to finish adds the partial sums in
+// part order (deterministic) and stores the result.  Runs only when the list
+// held every pair.
 __global__ void __launch_bounds__(kRescueT) k_rescue64_list(LabelArgs a) {
   __shared__ int s_rowcomp[ZEF_MAX_COMPARTMENTS];
-  __shared__ int64_t s_pair;
+  __shared__ int64_t s_item;
   __shared__ double s_red[kRescueT / 32];
   __shared__ int s_kred[kRescueT / 32];
   __shared__ int2 s_rng[kMaxRanges];
   __shared__ int s_tot, s_tris;
   const int64_t npairs = a.counters[CNT_UNC_LIST];
   if (npairs > a.unc_cap) return;  // k_rescue64_caps takes them all
+  int P = 1;
+  if (npairs > 0 && npairs <= kSplitPairs) {
+    const int64_t fit = (int64_t)gridDim.x / npairs;
+    P = fit < 1 ? 1 : (fit > kMaxParts ? kMaxParts : (int)fit);
+  }
+  const int64_t nitems = npairs * P;
   const int tid = threadIdx.x;
   for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
   for (;;) {
     if (tid == 0) {
-      const int64_t pr = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_UNC_WORK), 1ull);
-      s_pair = pr;
-      if (pr < npairs) {
-        const int2 e = a.unc_list[pr];
+      const int64_t it = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_UNC_WORK), 1ull);
+      s_item = it;
+      if (it < nitems) {
+        const int2 e = a.unc_list[it / P];
         const float4 p = a.spts[e.x];
         const float box[6] = {p.x, p.y, p.z, p.x, p.y, p.z};
         int tot = 0, nt = 0;
@@ -1712,11 +1728,29 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_list(LabelArgs a) {
       }
     }
     __syncthreads();
-    if (s_pair >= npairs) break;
-    const int2 e = a.unc_list[s_pair];
+    if (s_item >= nitems) break;
+    const int64_t pair = s_item / P;
+    const int part = (int)(s_item - pair * P);
+    const int2 e = a.unc_list[pair];
     const float4 p = a.spts[e.x];
-    const double half = block_sum64(a, s_rng, s_tot, p.x, p.y, p.z, s_red, s_kred);
-    if (tid == 0) store64(a, e.y, e.x, half, s_tris);
+    // this part's share of the groups of four
+    const int groups = s_tot / 4;
+    const int g0 = (int)((int64_t)groups * part / P), g1 = (int)((int64_t)groups * (part + 1) / P);
+    const double half = block_sum64(a, s_rng, 4 * g0, 4 * g1, p.x, p.y, p.z, s_red, s_kred);
+    if (tid == 0) {
+      if (P == 1) {
+        store64(a, e.y, e.x, half, s_tris);
+      } else {
+        a.unc_part[pair * kMaxParts + part] = half;
+        __threadfence();
+        if (atomicAdd(a.unc_done + pair, 1u) == (uint32_t)(P - 1)) {
+          __threadfence();
+          double h = 0.0;
+          for (int q = 0; q < P; ++q) h += *(volatile double *)(a.unc_part + pair * kMaxParts + q);
+          store64(a, e.y, e.x, h, s_tris);
+        }
+      }
+    }
     __syncthreads();
   }
 }
@@ -1771,7 +1805,7 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
           s_tris = nt;
         }
         __syncthreads();
-        const double half = block_sum64(a, s_rng, s_tot, p.x, p.y, p.z, s_red, s_kred);
+        const double half = block_sum64(a, s_rng, 0, s_tot, p.x, p.y, p.z, s_red, s_kred);
         if (tid == 0) store64(a, row, i, half, s_tris);
       }
     }
@@ -2515,7 +2549,7 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(hist)");
   }
   if (!b.unc_list) {
-    cudaError_t e = cudaMalloc(&b.unc_list, (size_t)kUncListCap * sizeof(int2));
+    cudaError_t e = cudaMalloc(&b.unc_list, kUncBytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(uncertain pairs)");
     b.cap_unc = kUncListCap;
   }
@@ -2594,6 +2628,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.cseg = ctx->d_cseg;
   a.unc_list = b.unc_list;
   a.unc_cap = b.unc_list ? b.cap_unc : 0;
+  a.unc_part = b.unc_list ? reinterpret_cast<double *>(b.unc_list + kUncListCap) : nullptr;
+  a.unc_done = b.unc_list ? reinterpret_cast<uint32_t *>(a.unc_part + (size_t)kSplitPairs * kMaxParts) : nullptr;
   a.masks_out = plan.masks;
   if (plan.timed) cudaEventRecord(ctx->ev[1], s);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {

@@ -45,7 +45,7 @@ constexpr size_t kOffFlags = align256(kOffHist + kBuckets * sizeof(uint32_t));
 constexpr size_t kOffSums = align256(kOffFlags + kMaxFlags * sizeof(uint32_t));
 constexpr size_t kOffItems = align256(kOffSums + kMaxBlockSums * sizeof(uint32_t));
 constexpr size_t kOffUncList = align256(kOffItems + kMaxFlags * sizeof(int2));
-constexpr size_t kOffCnt = align256(kOffUncList + kUncListCap * sizeof(int2));
+constexpr size_t kOffCnt = align256(kOffUncList + kUncBytes);
 constexpr size_t kScratchBytes = align256(kOffCnt + CNT_COUNT_ * sizeof(int64_t));
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
