@@ -38,12 +38,12 @@ zef_status zef_debug_strip_stats(const zef_ctx *ctx, int32_t index, int64_t *ent
 zef_status zef_debug_half_angle(zef_ctx *ctx, const float *y, const float *x, float *out, int64_t n);
 
 /* Cap tree of compartment `index` (registration order), unscaled: for each
-   node its box (lo x, y, z, hi x, y, z of the patch's vertices) and eight
+   node its box (lo x, y, z, hi x, y, z of the patch's vertices) and nine
    int32 (left child, right child (-1 for a leaf), first entry and entry
    count of the leaf's strip segment (0, 0 for an inner node), first entry
    and entry count of the node's cap segment, triangles of the leaf segment,
-   triangles of the cap segment; entries relative to the compartment's
-   block); the block's entries as 8 floats each (vertex x, y, z, weight;
+   triangles of the cap segment, the node after its subtree in pre-order;
+   nodes and entries relative to the compartment's block); the block's entries as 8 floats each (vertex x, y, z, weight;
    n x, y, z, kappa |n|), weight 2 opening a segment, +-1 closing a
    triangle window in its own / reversed orientation, 0 for the windows that
    repeat a vertex.  *n_nodes and *n_entries receive the counts; the arrays

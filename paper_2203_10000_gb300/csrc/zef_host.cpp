@@ -1006,7 +1006,7 @@ extern "C" zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int6
         boxes[6 * k + 3 + d] = nd.hi[d];
       }
     if (links) {
-      int32_t *l = links + 8 * k;
+      int32_t *l = links + 9 * k;
       l[0] = nd.left < 0 ? -1 : nd.left - c.cap_root;
       l[1] = nd.right < 0 ? -1 : nd.right - c.cap_root;
       l[2] = nd.left < 0 ? nd.leaf_begin - (int32_t)c.cseg_off : 0;
@@ -1015,6 +1015,7 @@ extern "C" zef_status zef_debug_cap_tree(const zef_ctx *ctx, int32_t index, int6
       l[5] = nd.cap_cnt;
       l[6] = nd.left < 0 ? nd.leaf_tris : 0;
       l[7] = nd.cap_tris;
+      l[8] = nd.skip - c.cap_root;
     }
   }
   if (entries)

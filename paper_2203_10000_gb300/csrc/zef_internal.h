@@ -43,7 +43,8 @@ struct __align__(16) DevComp {
 // Node of a compartment's cap tree (zef_tree.cpp): the box of the patch's
 // vertices, children (-1 for a leaf), the leaf's strip segment and the
 // node's cap segment (entries of the cap-tree segment array) with the
-// triangles each holds.
+// triangles each holds.  Nodes are stored in pre-order, so a depth-first
+// walk needs no stack: descend to this + 1, or continue at skip.
 constexpr int kCapLeaf = 64;  // most triangles of a leaf
 struct __align__(16) CapNode {
   float lo[3];
@@ -54,7 +55,7 @@ struct __align__(16) CapNode {
   int32_t cap_begin, cap_cnt;    // the node's cap: zigzag strip segment
   int32_t leaf_tris, cap_tris;
   int32_t tri_begin;             // leaf: first of its triangles in the tree-ordered index array
-  int32_t pad_;
+  int32_t skip;                  // the node after this subtree in pre-order (left child = this + 1)
 };
 static_assert(sizeof(CapNode) == 64, "CapNode is four 16-byte words");
 void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_base, int64_t seg_base,

@@ -656,11 +656,12 @@ constexpr int kMaxRanges = 192;
 
 __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb, int2 *out, int *total,
                           int *tris, bool all_leaves) {
-  int stack[48];
-  int sp = 0, n = 0, tot = 0, nt = 0;
-  stack[sp++] = __ldg(&cp->cap_root);
-  while (sp > 0) {
-    const CapNode nd = a.nodes[stack[--sp]];
+  int n = 0, tot = 0, nt = 0;
+  // pre-order walk without a stack: descend to i + 1, or continue at skip
+  const int root = __ldg(&cp->cap_root);
+  const int end = __ldg(&a.nodes[root].skip);
+  for (int i = root; i != end;) {
+    const CapNode nd = a.nodes[i];
     const bool far = nd.hi[0] < wb[0] || nd.lo[0] > wb[3] || nd.hi[1] < wb[1] || nd.lo[1] > wb[4] ||
                      nd.hi[2] < wb[2] || nd.lo[2] > wb[5];
     int b, c, t;
@@ -673,14 +674,10 @@ __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb
       c = nd.leaf_cnt;
       t = nd.leaf_tris;
     } else {
-      if (sp + 2 > 48) {  // deeper than any tree of 2^28 triangles: cannot happen
-        n = -1;
-        break;
-      }
-      stack[sp++] = nd.right;
-      stack[sp++] = nd.left;
+      ++i;
       continue;
     }
+    i = nd.skip;
     if (c <= 0) continue;
     tot += c;
     nt += t;
@@ -950,20 +947,18 @@ __device__ __forceinline__ bool lane_far(const CapNode &nd, float x, float y, fl
 
 // Entries of a point's own walk (the same walk as lane_walk_caps).
 __device__ __noinline__ int lane_walk_entries(const LabelArgs &a, int root, float x, float y, float z) {
-  int stack[48];
-  int sp = 0, tot = 0;
-  stack[sp++] = root;
-  while (sp > 0) {
-    const CapNode nd = a.nodes[stack[--sp]];
+  int tot = 0;
+  const int end = __ldg(&a.nodes[root].skip);
+  for (int i = root; i != end;) {
+    const CapNode nd = a.nodes[i];
     if (lane_far(nd, x, y, z)) {
       tot += nd.cap_cnt;
+      i = nd.skip;
     } else if (nd.left < 0) {
       tot += nd.leaf_cnt;
-    } else if (sp + 2 <= 48) {
-      stack[sp++] = nd.right;
-      stack[sp++] = nd.left;
+      i = nd.skip;
     } else {
-      return INT_MAX;
+      ++i;
     }
   }
   return tot;
@@ -986,26 +981,25 @@ __device__ __noinline__ uint32_t lane_walk_caps(const LabelArgs &a, const DevCom
     st.grp = st.sum = st.comp = 0.f;
     st.bad = __int_as_float(0x7f800000);
     st.kp = st.kn = 0u;
-    int stack[48];
-    int sp = 0, b = 0, e = 0, g = 0;
-    stack[sp++] = c.cap_root;
+    int b = 0, e = 0, g = 0;
+    int node = c.cap_root;
+    const int end = __ldg(&a.nodes[node].skip);
     for (;;) {
-      while (b >= e && sp > 0) {
-        const CapNode nd = a.nodes[stack[--sp]];
+      // pre-order walk without a stack to the next segment
+      while (b >= e && node != end) {
+        const CapNode nd = a.nodes[node];
         if (lane_far(nd, p.x, p.y, p.z)) {
           b = nd.cap_begin;
           e = b + nd.cap_cnt;
           np += (unsigned long long)nd.cap_tris;
+          node = nd.skip;
         } else if (nd.left < 0) {
           b = nd.leaf_begin;
           e = b + nd.leaf_cnt;
           np += (unsigned long long)nd.leaf_tris;
-        } else if (sp + 2 <= 48) {
-          stack[sp++] = nd.right;
-          stack[sp++] = nd.left;
-        } else {  // deeper than any tree of 2^28 triangles: cannot happen; left to the FP64 pass
-          st.bad = -1.f;
-          sp = 0;
+          node = nd.skip;
+        } else {
+          ++node;
         }
       }
       if (b >= e) break;

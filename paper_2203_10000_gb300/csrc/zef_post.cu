@@ -306,23 +306,20 @@ __global__ void __launch_bounds__(256) k_in_move(Adj g, const float *x, float *o
         const float lo0 = fminf(p0, p0 + d0) - kBoxMargin, hi0 = fmaxf(p0, p0 + d0) + kBoxMargin;
         const float lo1 = fminf(p1, p1 + d1) - kBoxMargin, hi1 = fmaxf(p1, p1 + d1) + kBoxMargin;
         const float lo2 = fminf(p2, p2 + d2) - kBoxMargin, hi2 = fmaxf(p2, p2 + d2) + kBoxMargin;
-        int stack[48];
-        int sp = 0, nl = 0;
-        stack[sp++] = root;
-        while (sp > 0) {
-          const CapNode nd = nodes[stack[--sp]];
+        int nl = 0;
+        // pre-order walk without a stack: descend to i + 1, or continue at skip
+        const int end = nodes[root].skip;
+        for (int q = root; q != end;) {
+          const CapNode nd = nodes[q];
           if (nd.hi[0] < lo0 || nd.lo[0] > hi0 || nd.hi[1] < lo1 || nd.lo[1] > hi1 || nd.hi[2] < lo2 ||
-              nd.lo[2] > hi2)
-            continue;
-          if (nd.left < 0) {
+              nd.lo[2] > hi2) {
+            q = nd.skip;
+          } else if (nd.left < 0) {
             if (nl < kInLeaves) s_leaf[wid][nl] = make_int2(nd.tri_begin, nd.leaf_tris);
             ++nl;
-          } else if (sp + 2 <= 48) {
-            stack[sp++] = nd.right;
-            stack[sp++] = nd.left;
-          } else {  // deeper than any tree of 2^28 triangles: cannot happen
-            nl = kInLeaves + 1;
-            break;
+            q = nd.skip;
+          } else {
+            ++q;
           }
         }
         s_nleaf[wid] = nl;

@@ -355,6 +355,7 @@ struct Builder {
       node.lo[d] = lo[d];
       node.hi[d] = hi[d];
     }
+    node.skip = (int32_t)nodes->size();  // pre-order: the subtree is [me, skip)
     (*nodes)[me] = node;
     return me;
   }
@@ -394,6 +395,7 @@ void build_cap_tree(const float *V, const int32_t *T, int64_t nt, int64_t node_b
     n.leaf_begin += (int32_t)seg_base;
     n.cap_begin += (int32_t)(seg_base + nleaf);
     n.tri_begin += (int32_t)tidx_base;
+    n.skip += (int32_t)node_base;
   }
   for (int64_t t : bd.idx) tidx.push_back((int32_t)t);
   *root = (int32_t)node_base;

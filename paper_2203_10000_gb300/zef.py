@@ -286,13 +286,13 @@ class Context:
         return int(_lib.zef_debug_wait_probe(self._h, int(limit_ns)))
 
     def cap_tree(self, index: int):
-        """(boxes float32 (n, 6), links int32 (n, 8), entries float32 (m, 8))
+        """(boxes float32 (n, 6), links int32 (n, 9), entries float32 (m, 8))
         of compartment `index`'s cap tree (diagnostics)."""
         nn, ne = _I64(0), _I64(0)
         self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(ne),
                                             None, None, None))
         boxes = np.empty((nn.value, 6), np.float32)
-        links = np.empty((nn.value, 8), np.int32)
+        links = np.empty((nn.value, 9), np.int32)
         ent = np.empty((ne.value, 8), np.float32)
         self._check(_lib.zef_debug_cap_tree(self._h, int(index), ctypes.byref(nn), ctypes.byref(ne),
                                             boxes.ctypes.data, links.ctypes.data, ent.ctypes.data))

@@ -250,6 +250,14 @@ def test_cap_tree_identity(zef, oracle_mod, which):
     boxes, links, ent = ctx.cap_tree(0)
     assert links[0, 5] == 0 and links[0, 7] == 0                 # root: closed, no cap
     leaf = links[:, 0] < 0
+    # pre-order: left child next, skip past the subtree (leaves: the next node)
+    assert links[0, 8] == len(boxes)
+    for k in range(len(boxes)):
+        if leaf[k]:
+            assert links[k, 8] == k + 1
+        else:
+            assert links[k, 0] == k + 1 and links[k, 8] == links[links[k, 1], 8]
+            assert links[links[k, 0], 8] == links[k, 1]
     assert links[leaf, 6].sum() == t.shape[0] and links[leaf, 6].max() <= 64
 
     def seg(k, cap):
