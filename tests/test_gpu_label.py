@@ -140,6 +140,32 @@ def test_config0_host_pointers_match_device(zef):
     assert np.array_equal(om_h, om_d)
 
 
+def test_host_buffers_match_device_large(zef, oracle_mod):
+    """Host arrays (pageable and pinned, lattice order and shuffled) of over
+    2^20 points give the device-pointer labels, which a sample checks
+    against the oracle."""
+    w = zs.config1(npts_limit=0)
+    g = zs.lattice_centroids(60, 10.0 / 3.0, (-100.0, -100.0, -100.0))   # 1,080,000 centroids
+    assert g.shape[0] > (1 << 20)
+    ctx = make_ctx(zef, w.surfaces, w.priority)
+    dev = ctx.label_points(torch.from_numpy(g).cuda(), stats=False)[0].cpu().numpy()
+    host = np.empty(g.shape[0], np.int32)
+    ctx.label_points(g, labels=host, stats=False)
+    assert np.array_equal(host, dev)
+    pin = torch.from_numpy(g).pin_memory()
+    lab_pin = torch.empty(g.shape[0], dtype=torch.int32).pin_memory()
+    ctx.label_points(pin, labels=lab_pin, stats=False)
+    assert np.array_equal(lab_pin.numpy(), dev)
+    perm = np.random.default_rng(12).permutation(g.shape[0])
+    sh = np.ascontiguousarray(g[perm])
+    host_sh = np.empty(g.shape[0], np.int32)
+    ctx.label_points(sh, labels=host_sh, stats=False)
+    assert np.array_equal(host_sh, dev[perm])
+    idx = zs.sample_rows(g, 2000, seed=13)
+    olab, _ = oracle_mod.label_points(g[idx], w.surfaces, w.priority)
+    assert np.array_equal(dev[idx], olab)
+
+
 @pytest.mark.parametrize("shape", [(256, 4), (256, 2), (128, 2), (128, 4)])
 def test_launch_shapes_ragged_tail(zef, oracle_mod, shape):
     w = zs.config0()
