@@ -6,7 +6,9 @@ closest to the threshold and the re-evaluation path decides.
 
 20.48 M centroids of the 1 mm lattice against 20 nested and intersecting deep
 structures (733,162 triangles), and 56.2 M centroids of the 1 mm lattice
-against the 24-compartment head (1,526,588 triangles)."""
+against the 24-compartment head (1,526,588 triangles).  Also the paper's
+three-sphere Ary geometry on all 8.4 M nodes of its 1 mm lattice, against
+the analytic labels by radius and the oracle."""
 import numpy as np
 import pytest
 
@@ -72,3 +74,40 @@ def test_full_size_sampled_parity(zef, oracle_mod, cfg, n_uniform, n_near, kerne
     assert bad.size == 0, (idx[bad][:10], lab[idx][bad][:10], olab[bad][:10])
     # the sample reaches many compartments, not only the bounding box
     assert np.unique(olab).size >= min(10, len(w.priority))
+
+
+def test_ary_spheres_full_lattice(zef, oracle_mod):
+    """The Ary geometry of Sec. 2.4: three concentric geodesic spheres (radii
+    87 / 92 / 100 mm, 88,180 triangles) against all 8,365,427 nodes of the
+    1 mm lattice over [-101, 101]^3.  Every node whose radius is outside a
+    sphere's [inradius, circumradius] shell gets its analytic label by radius;
+    a seeded sample of the rest and of all nodes is checked against the
+    oracle."""
+    w = zs.ary_spheres()
+    ctx = zef.Context(0)
+    for s in w.surfaces:
+        ctx.add_compartment(s.id, s.verts, s.tris)
+    ctx.set_priority(w.priority)
+    lab = ctx.label_points(torch.from_numpy(w.points).cuda(), stats=False)[0].cpu().numpy()
+    r = np.linalg.norm(w.points.astype(np.float64), axis=1)
+
+    def shell(s):
+        v = s.verts.astype(np.float64)
+        a, b, c = v[s.tris[:, 0]], v[s.tris[:, 1]], v[s.tris[:, 2]]
+        n = np.cross(b - a, c - a)
+        inr = np.min(np.abs(np.einsum("ij,ij->i", n, a)) / np.linalg.norm(n, axis=1))
+        return inr, float(np.max(np.linalg.norm(v, axis=1)))
+
+    bounds = [shell(s) for s in w.surfaces]    # priority order: 87, 92, 100 mm
+    analytic = np.full(r.shape, -9)
+    analytic[r > bounds[2][1]] = 0
+    analytic[(r < bounds[2][0]) & (r > bounds[1][1])] = w.priority[2]
+    analytic[(r < bounds[1][0]) & (r > bounds[0][1])] = w.priority[1]
+    analytic[r < bounds[0][0]] = w.priority[0]
+    known = analytic != -9
+    assert known.mean() > 0.9
+    assert np.array_equal(lab[known], analytic[known])
+    idx = np.concatenate([zs.sample_rows(w.points, 3000, seed=21),
+                          np.random.default_rng(22).choice(np.nonzero(~known)[0], 3000, replace=False)])
+    olab, _ = oracle_mod.label_points(w.points[idx], w.surfaces, w.priority)
+    assert np.array_equal(lab[idx], olab)
