@@ -509,9 +509,9 @@ void green_tables(GreenTables &g) {
       int p = -1;
       for (int v = 0; v < 4; ++v)
         if ((E[bits[0]][0] == v || E[bits[0]][1] == v) && (E[bits[1]][0] == v || E[bits[1]][1] == v)) p = v;
-      int o[2], no = 0;
+      int o[2] = {0, 0}, no = 0;  // the two used vertices other than p (nv == 3)
       for (int v = 0; v < 4; ++v)
-        if (((used >> v) & 1) && v != p) o[no++] = v;
+        if (((used >> v) & 1) && v != p && no < 2) o[no++] = v;
       const int q = o[0], r = o[1];  // q < r
       const int mpq = 4 + local_edge(p, q), mpr = 4 + local_edge(p, r);
       substitute(c[0], {{q, mpq}, {r, mpr}});
