@@ -29,8 +29,11 @@
 // (x0, x0, x1)).  Every non-triangle window repeats a vertex, so its N is 0
 // and its D >= 0: a positive real factor.
 //
-// Layout per compartment: the leaf segments in tree order, then the cap
-// segments of all its nodes (the leaves' block alone is the whole surface).
+// Layout per compartment: the nodes in pre-order (a node's left child is the
+// next node, and `skip` is the node after its subtree, so walks need no
+// stack); the leaf segments in tree order, then the cap segments of all its
+// nodes (the leaves' block alone is the whole surface); the triangle indices
+// in leaf order (a leaf's triangles for box queries such as the inflation's).
 #include <algorithm>
 #include <array>
 #include <climits>
