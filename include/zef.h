@@ -62,8 +62,12 @@ typedef enum zef_status {
     ZEF_ERR_TIMEOUT = 6,              /* a bounded device wait expired (the kernel
                                          stopped early and reported it) */
     ZEF_ERR_NOT_READY = 7,            /* no compartment registered */
-    ZEF_ERR_CAPACITY = 8              /* refinement needs more nodes/tets than the
+    ZEF_ERR_CAPACITY = 8,             /* refinement needs more nodes/tets than the
                                          caller's capacities */
+    ZEF_ERR_BOUNDS = 9                /* only the debug build (ZEF_DEBUG_BOUNDS):
+                                         a device-side index check failed; the
+                                         access was skipped and the results of
+                                         the call are not valid */
 } zef_status;
 
 /* zef_add_compartment flags */
@@ -85,10 +89,13 @@ typedef struct zef_label_opts {
     /* A pair is also uncertain when Omega32 is farther than winding_tol from
        the nearest multiple of 4 pi k (Omega of a closed surface at a point
        off the surface is 4 pi times the winding number k).  A pair that is
-       certain reports Omega = 4 pi k exactly.  Default 1e-4: the rounding
-       error of an FP32 sum stays orders of magnitude below 2 pi - winding_tol,
-       and the errors of about 4 pi that a wrong sign of a near-zero N can
-       cause are caught by the conditioning test. */
+       certain reports Omega = 4 pi k exactly.  Default 1e-5 (<= 0 selects
+       it): every FP32 sum the library certifies is then within 1e-5 sr of
+       the exact solid angle.  The label argument needs far less -- the
+       rounding error of an FP32 sum stays orders of magnitude below
+       2 pi - winding_tol, and the errors of about 4 pi that a wrong sign of a
+       near-zero N can cause are caught by the conditioning test -- so a
+       looser value (say 1e-4) re-evaluates fewer pairs with the same labels. */
     float winding_tol;
     /* zef_precision */
     int32_t precision;
@@ -104,7 +111,8 @@ typedef struct zef_label_opts {
        product of their (D + iN) factors with 2 pi wraps counted exactly;
        2 = whole-surface strips, one atan2 per triangle. */
     int32_t kernel;
-    /* ZEF_NO_TILE_COHERENCE and / or ZEF_POINT_WALK, or 0 (see below). */
+    /* ZEF_NO_TILE_COHERENCE, ZEF_POINT_WALK, ZEF_OMEGA_RAW (any
+       combination), or 0 (see below). */
     uint32_t flags;
     int32_t reserved;
 } zef_label_opts;
@@ -123,6 +131,15 @@ typedef struct zef_label_opts {
    point walks the tree for itself.  This flag makes every point walk the
    tree for itself. */
 #define ZEF_POINT_WALK 2u
+/* Diagnostics: Omega receives the FP32 sum itself (Kahan-compensated, as the
+   kernel computed it) for every (point, compartment) pair that the FP32
+   kernel evaluated point by point and certified, instead of the certified
+   4 pi k.  Pairs decided without their own sum keep their exact 4 pi k (0
+   outside the box or hull bound, the representative's k on coherent tiles
+   and groups); re-evaluated pairs keep their FP64 sum; with ZEF_FP32_ONLY
+   the uncertain pairs keep their FP32 sum.  Labels are unchanged.  Used to
+   measure the FP32 arithmetic's own error against the FP64 oracle. */
+#define ZEF_OMEGA_RAW 4u
 
 typedef struct zef_label_stats {
     int64_t points;            /* N */
@@ -146,6 +163,8 @@ typedef struct zef_label_stats {
     int64_t lane_walk_items;   /* kernel form 0: (tile, compartment) pairs whose
                                   points each walked their own cap tree (the
                                   tile's shared list of segments was too long) */
+    int64_t kernel_launches;   /* CUDA kernels the library launched for this call
+                                  (autotuning runs excluded) */
 } zef_label_stats;
 
 /* Mesh for zef_refine_and_relabel.  All four arrays must be device memory or
@@ -289,11 +308,12 @@ zef_status zef_label_elements(zef_ctx *ctx, const float *nodes, int64_t n_nodes,
              omega must be DEVICE pointers (ZEF_ERR_INVALID_ARG otherwise)
      n       0 <= n <= ZEF_NOALLOC_MAX_POINTS, else ZEF_ERR_INVALID_ARG
    All scratch comes from one fixed-size array compiled into the library
-   (about 11 MB, held on every GPU that loads the library until the process
+   (about 12 MB, held on every GPU that loads the library until the process
    exits).  The compartments must already be registered (ZEF_ERR_NOT_READY
-   otherwise).  The first call on a device looks up the array's device
-   address (cudaGetSymbolAddress) and caches it: make that first call before
-   any stream capture.  Every call in the process shares the one array of its
+   otherwise).  Every call looks up the array's device address on the
+   context's device (cudaGetSymbolAddress); the first call on a device may
+   load the library's device code, so make that first call before any
+   stream capture.  Every call in the process shares the one array of its
    device, which keeps the last call's contents; each call clears what must
    start at zero.  Calls that overlap on the GPU (other streams, contexts or
    host threads) race on the array and corrupt each other's results:

@@ -261,6 +261,7 @@ zef_status zef_compartment_info(const zef_ctx *ctx, int32_t *num_compartments, i
 
 zef_status zef_add_compartment(zef_ctx *ctx, int32_t id, const float *verts, int64_t nv,
                                const int32_t *tris, int64_t nt, uint32_t flags) {
+  NvtxRange nvtx_("zef.add_compartment");
   if (!ctx) return ZEF_ERR_INVALID_ARG;
   ctx->err.clear();
   if (id <= 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "compartment id must be > 0");
@@ -515,6 +516,8 @@ zef_status zef_synchronize(zef_ctx *ctx) {
       return fail(ctx, ZEF_ERR_INVALID_ARG, "a tet references a node index outside [0, num_nodes)");
     if (st[0] & ST_CAPACITY)
       return fail(ctx, ZEF_ERR_CAPACITY, "refinement exceeded the mesh capacities");
+    if (st[0] & ST_BOUNDS)
+      return fail(ctx, ZEF_ERR_BOUNDS, "a device-side index check failed (site " + std::to_string(st[1]) + ")");
   }
   return ZEF_OK;
 }
@@ -593,6 +596,7 @@ namespace zef {
 zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels, float *omega,
                              const zef_label_opts *opts, zef_label_stats *stats, unsigned long long *d_masks,
                              bool full_masks) {
+  NvtxRange nvtx_("zef.label_points");
   if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
   if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
   if (n < 0 || (n > 0 && (!pts || !labels)))
@@ -603,7 +607,7 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
-  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
+  if (o.flags & ~kLabelFlagsAll) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -654,10 +658,12 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
     st = autotune(ctx, plan, &plan.shape);
     if (st) return st;
   }
+  const int64_t launches0 = ctx->launches;
   st = label_set_count(ctx, n, 0);
   if (st) return st;
   st = label_enqueue(ctx, plan);
   if (st) return st;
+  const int64_t launches = ctx->launches - launches0;
   if (!dlab)
     CK(cudaMemcpyAsync(labels, d_lab, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
        "copy labels");
@@ -685,6 +691,7 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
     stats->coherent_pairs = h[CNT_COHERENT];
     stats->representative_pairs = h[CNT_REP_PAIRS];
     stats->lane_walk_items = h[CNT_LANE_TILES];
+    stats->kernel_launches = launches;
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;
@@ -721,7 +728,7 @@ zef_status zef_relabel_boundary(zef_ctx *ctx, const float *nodes, int64_t n_node
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
-  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
+  if (o.flags & ~kLabelFlagsAll) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (per_pass) std::memset(per_pass, 0, sizeof(zef_relabel_pass) * (size_t)max_passes);
@@ -789,7 +796,7 @@ zef_status zef_refine_and_relabel(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, 
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
-  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
+  if (o.flags & ~kLabelFlagsAll) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   DeviceGuard g(ctx->device);
@@ -898,6 +905,23 @@ zef_status ensure_uploaded(zef_ctx *ctx) {
   if (!ctx->h_ctidx.empty())
     CK(cudaMemcpy(ctx->d_ctidx, ctx->h_ctidx.data(), ctx->h_ctidx.size() * sizeof(int32_t), cudaMemcpyHostToDevice),
        "upload cap-tree triangle order");
+  // union box of the surfaces in the caller's coordinates: the binning keys'
+  // range (a point outside it is outside every compartment's box)
+  UnionBox ub;
+  for (int k = 0; k < 3; ++k) {
+    ub.lo[k] = std::numeric_limits<float>::infinity();
+    ub.hi[k] = -std::numeric_limits<float>::infinity();
+  }
+  for (const CompHost &h : ctx->comps)
+    for (int k = 0; k < 3; ++k) {
+      ub.lo[k] = std::min(ub.lo[k], h.lo[k]);
+      ub.hi[k] = std::max(ub.hi[k], h.hi[k]);
+    }
+  // cubic Morton cells: the scale of the box's longest side on every axis
+  float ext = 0.f;
+  for (int k = 0; k < 3; ++k) ext = std::max(ext, ub.hi[k] - ub.lo[k]);
+  for (int k = 0; k < 3; ++k) ub.sc[k] = ext > 0.f ? (float)(1 << kMortonBits) / ext : 0.f;
+  ctx->ubox = ub;
   std::vector<DevComp> dc(C);
   std::vector<int32_t> rows(C), lpt(C);
   for (int i = 0; i < C; ++i) {

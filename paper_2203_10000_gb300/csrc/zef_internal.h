@@ -7,9 +7,25 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "zef.h"
 
 namespace zef {
+
+// NVTX range over a host scope (a profiler attached through NVTX shows the
+// library's stages by these names; without one the calls cost nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  // end this range and open the next stage's
+  void next(const char *name) {
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // One strip-stream entry, 32 bytes (two float4, TMA-friendly):
 //   v = (x, y, z, weight): the vertex entering the sliding triangle window;
@@ -67,7 +83,28 @@ enum : uint32_t {
   ST_TIMEOUT = 1u,
   ST_CAPACITY = 2u,
   ST_INVALID = 4u,
+  ST_BOUNDS = 8u,   // debug build: a device-side index check failed
 };
+
+// Debug build (compiled with ZEF_DEBUG_BOUNDS): the labeling kernels check the
+// indices they compute before they use them; a failed check records
+// ST_BOUNDS with a site code in the context's status word and skips the
+// access (it never traps).  In the release build every check is `true`.
+#if defined(ZEF_DEBUG_BOUNDS) && defined(__CUDACC__)
+__device__ __forceinline__ bool bounds_ok(bool ok, uint32_t *status, uint32_t site) {
+  if (!ok) {
+    atomicOr(status, ST_BOUNDS);
+    atomicExch(status + 1, site);
+  }
+  return ok;
+}
+#define ZEF_BOUNDS_OK(cond, status, site) ::zef::bounds_ok((cond), (status), (site))
+#else
+#define ZEF_BOUNDS_OK(cond, status, site) true
+#endif
+
+// every zef_label_opts.flags bit the library knows
+constexpr uint32_t kLabelFlagsAll = ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK | ZEF_OMEGA_RAW;
 
 constexpr int kGroup = 16;        // Kahan group: entries summed plainly before compensation
 constexpr int kChunk = 256;       // entries per TMA chunk
@@ -75,6 +112,27 @@ constexpr int kTriChunk = 128;    // plain triangles per TMA chunk (FP64 baselin
 constexpr float kKappa = 1.0f / 8192.0f;  // conditioning threshold of a pair
 constexpr int kMortonBits = 7;    // bits per axis of the binning key
 constexpr int kBuckets = 1 << (3 * kMortonBits);
+// binning keys past the Morton cells: finite points outside the surfaces'
+// union box, then non-finite points (sorted to the tail in that order), each
+// spread over kTailKeys keys by warp so that their counts and cursors are not
+// one contended address
+constexpr uint32_t kTailKeys = 256;
+constexpr uint32_t kKeyOutside = (uint32_t)kBuckets;                // first of kTailKeys
+constexpr uint32_t kKeyNonfinite = (uint32_t)kBuckets + kTailKeys;  // first of kTailKeys
+constexpr int64_t kHistLen = (int64_t)kBuckets + 2 * kTailKeys;     // key histogram / cursor entries
+constexpr int kWorkBuckets = 4096;                    // log-scale work buckets of the tile list
+// exclusive scan: threads per block, values per thread, values per block
+constexpr int kScanT = 256;
+constexpr int kScanV = 8;
+constexpr int kScanB = kScanT * kScanV;
+// block sums needed to scan len values (one per block, plus one spare)
+constexpr int64_t scan_block_sums(int64_t len) { return (len + kScanB - 1) / kScanB + 1; }
+
+// Union box of the registered surfaces in the caller's (unscaled)
+// coordinates, with the Morton cell scale 2^kMortonBits / extent per axis.
+struct UnionBox {
+  float lo[3], hi[3], sc[3];
+};
 
 // Convex-hull bound of a compartment: kDop fixed unit directions d_k (a
 // Fibonacci sphere); h_k >= max over the surface's vertices of d_k . v, with
@@ -106,7 +164,7 @@ struct LabelBuffers {
   unsigned long long *in_mask = nullptr;   // per sorted point: inside bits (priority rows)
   unsigned long long *unc_mask = nullptr;  // per sorted point: uncertain bits
   float *tile_box = nullptr;    // [tiles][6]
-  uint32_t *hist = nullptr;     // kBuckets
+  uint32_t *hist = nullptr;     // kHistLen key cursor, then kWorkBuckets work cursor
   uint32_t *flags = nullptr;    // [C * tiles] work-list flags, scanned in place
   uint32_t *block_sums = nullptr;
   int2 *items = nullptr;        // (tile, comp)
@@ -135,9 +193,9 @@ enum Counter {
   CNT_NONFINITE,
   CNT_PAIRS_EVAL,     // FP32 (or FP64 plain) pairs
   CNT_PAIRS_RESCUE,   // FP64 re-evaluation pairs
-  CNT_BOX,            // 6 x int32 ordered bounding box packed in 3 int64 slots
-  CNT_BOX1,
-  CNT_BOX2,
+  CNT_NIN,            // sorted points inside the surfaces' union box (they come first)
+  CNT_NFIN,           // finite points (the non-finite ones are the sorted tail)
+  CNT_SPARE,
   CNT_TILES,
   CNT_LEVEL_FLAGGED,  // refinement
   CNT_LEVEL_NEW,
@@ -208,6 +266,8 @@ struct zef_ctx {
   int64_t *h_counters = nullptr;      // pinned mirror of the counters
 
   cudaEvent_t ev[6] = {};
+  zef::UnionBox ubox = {};            // union box of the surfaces (unscaled), set at upload
+  int64_t launches = 0;               // kernels launched by the labeling pipeline (running count)
 
   // autotuner cache: key -> shape
   std::vector<std::pair<uint64_t, zef::LaunchShape>> tune_cache;

@@ -6,25 +6,30 @@
 // compartment of the priority list that encloses p labels it.
 //
 // Pipeline of one call (all on the context stream, no host round trip):
-//   k_prepare      counters for this call
-//   k_bbox         bounding box of the finite points
-//   k_keys         21-bit Morton bucket of every point + bucket histogram
-//   scan           exclusive scan of the histogram
-//   k_scatter      points into bucket order (float4) + permutation
-//   k_tile_box     bounding box of every tile of consecutive sorted points
-//   k_tile_work/scan/k_tile_scatter
-//                  work list of the tiles whose box meets some compartment's
-//                  box and convex-hull bound, largest estimated work first;
-//                  a point outside a closed surface's box or hull has
-//                  winding number 0, so the culling is exact (k_flags/scan/
-//                  k_emit: (tile, compartment) items for the plain FP64 kernel)
+//   k_prepare      point count and offset of this call
+//   k_reset        counters, work histogram, split-pair completion counts
+//   k_keys         binning key of every point: its 21-bit Morton cell in the
+//                  union box of the surfaces, or the tail keys of the points
+//                  outside that box (outside every compartment: winding
+//                  number 0) and of the non-finite points; key histogram
+//   scan           exclusive scan of the histogram (records where the tails
+//                  start and the tile count)
+//   k_scatter      points into key order (float4, scaled) + permutation,
+//                  inside / uncertain masks cleared
+//   k_tile_work/k_scan_work/k_tile_scatter
+//                  work list of the tiles of sorted points inside the union
+//                  box whose box meets some compartment's box and convex-hull
+//                  bound, largest estimated work first; a point outside a
+//                  closed surface's box or hull has winding number 0, so the
+//                  culling is exact (k_tile_box/k_flags/scan/k_emit: the
+//                  (tile, compartment) items of the plain FP64 kernel)
 //   k_label32      persistent FP32 kernel over the work list (hot loop); the
 //                  default form walks each compartment's cap tree for the
-//                  tile (far patches replaced by their caps, zef_tree.cpp)
-//   k_unc_list + k_rescue64_list (cap-tree form; k_rescue64_caps when the
-//                  pair list overflows) / k_rescue64 (strip forms)
-//                  FP64 re-evaluation of the uncertain (point, compartment)
-//                  pairs
+//                  tile (far patches replaced by their caps, zef_tree.cpp) and
+//                  appends the uncertain (point, compartment) pairs to a list
+//   k_rescue64_list (cap-tree form; k_rescue64_caps when the pair list
+//                  overflowed) / k_rescue64 (strip forms)
+//                  FP64 re-evaluation of the uncertain pairs
 //   k_resolve      priority resolve + un-permute
 //
 // FP32 hot loop.  Surfaces (whole, or the leaves and caps a tile's walk of the
@@ -82,12 +87,12 @@ constexpr float kA6 = 0.043553530224279755f;
 constexpr float kA7 = -0.0165811779740931f;
 constexpr float kA8 = 0.0029745887848576756f;
 
-// directions of the convex-hull bound (uploaded once per device)
+// directions of the convex-hull bound (uploaded once per device): constant
+// memory for loops whose lanes read the same direction, a global copy (read
+// through the L1) for the warp-split test, whose lanes read different ones
 __constant__ float c_dop[kDop][3];
+__device__ float g_dop[kDop][3];
 
-constexpr int kScanT = 256;
-constexpr int kScanV = 8;
-constexpr int kScanB = kScanT * kScanV;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded mbarrier wait: 2 s
 
 // ------------------------------------------------------------------ PTX helpers
@@ -147,12 +152,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
     if (global_ns() - t0 > limit_ns) return false;
   }
 }
-
-__device__ __forceinline__ int f2o(float f) {
-  int i = __float_as_int(f);
-  return i >= 0 ? i : i ^ 0x7fffffff;
-}
-__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
 
 __device__ __forceinline__ bool finite3(float x, float y, float z) {
   return isfinite(x) && isfinite(y) && isfinite(z);
@@ -297,6 +296,7 @@ struct LabelArgs {
   int coherence;  // tile representatives allowed
   int early;      // priority early exit: a point certainly inside needs no later compartment
   int lane_walk;  // kernel form 2 (cap trees): 0 = every point walks the tree for itself
+  int omega_raw;  // diagnostics: certified pairs report their FP32 sum, not 4 pi k
   unsigned long long *masks_out;  // nullable: inside bits per point in the caller's order
   const CapNode *nodes;  // cap trees
   const Entry *cseg;     // cap-tree strip segments
@@ -304,10 +304,10 @@ struct LabelArgs {
   int64_t unc_cap;
   double *unc_part;      // [kSplitPairs][kMaxParts] partial half-angle sums of split pairs
   uint32_t *unc_done;    // [kSplitPairs] parts finished
+  int64_t n_nodes;       // cap-tree nodes and segment entries (debug-build index checks)
+  int64_t n_cseg;
 };
 
-// Classification of one (point, compartment) pair after the FP32 sum:
-// Omega / 2 = half + 2 pi K (K the net count of 2 pi wraps).
 // True when the box b (lo x, y, z, hi x, y, z) misses the compartment's box.
 __device__ __forceinline__ bool box_misses(const float *b, const DevComp *cp) {
   return b[3] < __ldg(&cp->lo[0]) || b[0] > __ldg(&cp->hi[0]) || b[4] < __ldg(&cp->lo[1]) ||
@@ -328,6 +328,20 @@ __device__ __forceinline__ bool dop_box_misses(const float *b, const float *thr)
   return false;
 }
 
+// The same test with the directions split over the lanes of a warp (three
+// per lane); every lane of the warp must call it with the same box.
+__device__ __forceinline__ bool dop_box_misses_warp(const float *b, const float *thr, int lane) {
+  bool miss = false;
+#pragma unroll
+  for (int k = lane; k < kDop; k += 32) {
+    const float dx = __ldg(&g_dop[k][0]), dy = __ldg(&g_dop[k][1]), dz = __ldg(&g_dop[k][2]);
+    const float t = fmaf(dx, dx >= 0.f ? b[0] : b[3], fmaf(dy, dy >= 0.f ? b[1] : b[4], dz * (dz >= 0.f ? b[2] : b[5])));
+    miss |= t > __ldg(thr + k);
+  }
+  return __any_sync(0xffffffffu, miss);
+}
+static_assert(kDop % 32 == 0, "whole directions per lane");
+
 __device__ __forceinline__ bool dop_point_outside(float x, float y, float z, const float *thr) {
 #pragma unroll 4
   for (int k = 0; k < kDop; ++k)
@@ -335,30 +349,36 @@ __device__ __forceinline__ bool dop_point_outside(float x, float y, float z, con
   return false;
 }
 
-// Returns true when the point is certainly inside the compartment.
+// Classification of one (point, compartment) pair after the FP32 sum:
+// Omega / 2 = half + 2 pi K (K the net count of 2 pi wraps).  Returns true
+// when the point is certainly inside the compartment.
 __device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp &c, const float *thr, int64_t i,
                                                float px, float py, float pz, float half, int K, float bad) {
+  if (!ZEF_BOUNDS_OK(i >= 0 && i < a.counters[CNT_NIN], a.status, 14)) return false;
   float omega = 2.f * fmaf(kTwoPi, (float)K, half);
   bool inside = false;
-  const bool fin = finite3(px, py, pz);
-  // outside the box or the hull bound: winding number 0, Omega exactly 0
-  const bool outside_box = px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] ||
-                           pz > c.hi[2] || dop_point_outside(px, py, pz, thr);
   const unsigned long long bit = 1ull << c.row;
-  if (!fin) {
+  if (!finite3(px, py, pz)) {
     omega = __int_as_float(0x7fc00000);
-  } else if (outside_box) {
-    omega = 0.f;
   } else {
     // distance of Omega to 4 pi Z, from the small half angle (K drops out)
     const float k = rintf(half * kInvTwoPi);
     const float dist = 2.f * fabsf(fmaf(-kTwoPi, k, half));
     const bool unc = !(bad > 0.f) || !(dist <= a.winding_tol) || !(fabsf(omega - kTwoPi) >= a.margin);
-    if (unc && !a.fp32_only) {
+    if (unc && (px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] ||
+                pz > c.hi[2] || dop_point_outside(px, py, pz, thr))) {
+      // outside the box or the hull bound the winding number is 0 whatever
+      // the sum says: Omega is exactly 0 (tested only here, where it decides)
+      omega = 0.f;
+    } else if (unc && !a.fp32_only) {
       atomicOr(a.unc_mask + i, bit);
+      if (a.unc_list) {  // the cap-tree re-evaluation's pair list (may overflow: counted beyond its capacity)
+        const unsigned long long slot = atomicAdd((unsigned long long *)(a.counters + CNT_UNC_LIST), 1ull);
+        if ((int64_t)slot < a.unc_cap) a.unc_list[slot] = make_int2((int)i, c.row);
+      }
     } else {
       // a certified winding number K + k: Omega is exactly 4 pi (K + k)
-      if (!unc) omega = kFourPi * ((float)K + k);
+      if (!unc && !a.omega_raw) omega = kFourPi * ((float)K + k);
       if (omega > kTwoPi) {
         atomicOr(a.in_mask + i, bit);
         inside = true;
@@ -369,17 +389,18 @@ __device__ __forceinline__ bool classify_store(const LabelArgs &a, const DevComp
   return inside;
 }
 
-// Classification of a point of a coherent tile: Omega = 4 pi k exactly
-// (k the tile's winding number), 0 outside the compartment's box or hull.
-__device__ __forceinline__ bool classify_coherent(const LabelArgs &a, const DevComp &c, const float *thr, int64_t i,
-                                                  float px, float py, float pz, int k) {
+// Classification of a point of a coherent tile or group: Omega = 4 pi k
+// exactly, k the winding number of the tile's or group's representative.  No
+// triangle of the surface meets the box of those points, so the winding
+// number is k at every one of them -- 0 in particular wherever a point lies
+// outside the compartment's box or hull, which therefore needs no test here.
+__device__ __forceinline__ bool classify_coherent(const LabelArgs &a, const DevComp &c, int64_t i, float px,
+                                                  float py, float pz, int k) {
+  if (!ZEF_BOUNDS_OK(i >= 0 && i < a.counters[CNT_NIN], a.status, 15)) return false;
   float omega;
   bool inside = false;
   if (!finite3(px, py, pz)) {
     omega = __int_as_float(0x7fc00000);
-  } else if (px < c.lo[0] || px > c.hi[0] || py < c.lo[1] || py > c.hi[1] || pz < c.lo[2] || pz > c.hi[2] ||
-             dop_point_outside(px, py, pz, thr)) {
-    omega = 0.f;
   } else {
     omega = kFourPi * (float)k;
     if (k >= 1) {
@@ -653,17 +674,31 @@ __device__ __forceinline__ bool stream_sums(const LabelArgs &a, const DevComp *c
 // more than kMaxRanges ranges return -1, or with `all_leaves` fall back to
 // every leaf segment.
 constexpr int kMaxRanges = 192;
+// A tile's walk takes a node's cap only when the tile's box misses the node's
+// box grown by kCapMargin times the box's longest side: a cap triangle spans
+// its patch's boundary, and one that passes within a small fraction of its
+// own size from a point carries the largest FP32 rounding (measured on the
+// full head: with no margin about 3 % of the certified sums were more than
+// 1e-5 from their winding number's 4 pi k, with 1/64 about 0.03 %, for 3 %
+// more evaluated pairs).
+constexpr float kCapMargin = 1.f / 64.f;
 
 __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb, int2 *out, int *total,
-                          int *tris, bool all_leaves) {
+                          int *tris, bool all_leaves, float margin = 0.f) {
   int n = 0, tot = 0, nt = 0;
   // pre-order walk without a stack: descend to i + 1, or continue at skip
   const int root = __ldg(&cp->cap_root);
   const int end = __ldg(&a.nodes[root].skip);
   for (int i = root; i != end;) {
+    if (!ZEF_BOUNDS_OK(i >= 0 && i < a.n_nodes, a.status, 10)) {
+      n = 0;
+      tot = nt = 0;
+      break;
+    }
     const CapNode nd = a.nodes[i];
-    const bool far = nd.hi[0] < wb[0] || nd.lo[0] > wb[3] || nd.hi[1] < wb[1] || nd.lo[1] > wb[4] ||
-                     nd.hi[2] < wb[2] || nd.lo[2] > wb[5];
+    const float m = margin * fmaxf(nd.hi[0] - nd.lo[0], fmaxf(nd.hi[1] - nd.lo[1], nd.hi[2] - nd.lo[2]));
+    const bool far = nd.hi[0] + m < wb[0] || nd.lo[0] - m > wb[3] || nd.hi[1] + m < wb[1] || nd.lo[1] - m > wb[4] ||
+                     nd.hi[2] + m < wb[2] || nd.lo[2] - m > wb[5];
     int b, c, t;
     if (far) {
       b = nd.cap_begin;
@@ -679,6 +714,7 @@ __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb
     }
     i = nd.skip;
     if (c <= 0) continue;
+    if (!ZEF_BOUNDS_OK(b >= 0 && (int64_t)b + c <= a.n_cseg, a.status, 11)) continue;
     tot += c;
     nt += t;
     if (n > 0 && out[n - 1].x + out[n - 1].y == b) {
@@ -987,6 +1023,10 @@ __device__ __noinline__ uint32_t lane_walk_caps(const LabelArgs &a, const DevCom
     for (;;) {
       // pre-order walk without a stack to the next segment
       while (b >= e && node != end) {
+        if (!ZEF_BOUNDS_OK(node >= 0 && node < a.n_nodes, a.status, 12)) {
+          node = end;
+          break;
+        }
         const CapNode nd = a.nodes[node];
         if (lane_far(nd, p.x, p.y, p.z)) {
           b = nd.cap_begin;
@@ -1003,6 +1043,7 @@ __device__ __noinline__ uint32_t lane_walk_caps(const LabelArgs &a, const DevCom
         }
       }
       if (b >= e) break;
+      if (!ZEF_BOUNDS_OK(b >= 0 && (int64_t)b + 4 <= a.n_cseg, a.status, 13)) break;
       const Entry *E = a.cseg + b;
       const float4 v0 = __ldg(&E[0].v), n0 = __ldg(&E[0].n), v1 = __ldg(&E[1].v), n1 = __ldg(&E[1].n);
       const float4 v2 = __ldg(&E[2].v), n2 = __ldg(&E[2].n), v3 = __ldg(&E[3].v), n3 = __ldg(&E[3].n);
@@ -1126,7 +1167,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
   for (int c = threadIdx.x; c < a.ncomp; c += NT) s_rowcomp[a.comps[c].row] = c;
   __syncthreads();
   uint32_t ph0 = 0, ph1 = 0;
-  const int n = (int)a.counters[CNT_N];  // < 2^31 (checked on the host)
+  const int n = (int)a.counters[CNT_NIN];  // sorted points inside the union box, < 2^31 (checked on the host)
   const int64_t nitems = a.counters[CNT_ITEMS];
   const bool early = a.early;
   for (;;) {
@@ -1135,6 +1176,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= nitems) break;
     const int tile = a.items[item].x;
+    if (!ZEF_BOUNDS_OK(tile >= 0 && (int64_t)tile * TILE < (int64_t)n, a.status, 20)) continue;
     const int base = tile * TILE;
     uint32_t done = 0;    // bit q: point q is invalid, non-finite or certainly inside an earlier compartment
     uint32_t usable = 0;  // bit q: point q is valid and finite
@@ -1182,7 +1224,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       const DevComp *cp = a.comps + s_rowcomp[r];
       const float *thr = a.dop + (int64_t)s_rowcomp[r] * kDop;
       // winding number 0 for every point of the tile
-      if (box_misses(s_wbox[wid], cp) || dop_box_misses(s_wbox[wid], thr)) continue;
+      if (box_misses(s_wbox[wid], cp) || dop_box_misses_warp(s_wbox[wid], thr, lane)) continue;
       // groups with a point that still needs this compartment
       uint32_t need = 0;
 #pragma unroll
@@ -1201,7 +1243,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       if constexpr (V == 2) {
         if (lane == 0) {
           int tot = 0, nt = 0;
-          const int nr = cap_ranges(a, cp, s_wbox[wid], s_rng[wid], &tot, &nt, false);
+          const int nr = cap_ranges(a, cp, s_wbox[wid], s_rng[wid], &tot, &nt, false, kCapMargin);
           s_rtot[wid][0] = nr < 0 ? -1 : tot;
           s_rtot[wid][1] = nt;
         }
@@ -1327,7 +1369,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
             if (mine) {
               const int i = base + q * 32 + lane;
               const float4 p = a.spts[i];
-              if (classify_coherent(a, c, thr, i, p.x, p.y, p.z, half ? kg[2 * q + 1] : kg[2 * q]))
+              if (classify_coherent(a, c, i, p.x, p.y, p.z, half ? kg[2 * q + 1] : kg[2 * q]))
                 done |= 1u << q;
             }
             assigned += __popc(__ballot_sync(0xffffffffu, mine));
@@ -1404,7 +1446,7 @@ __global__ void __launch_bounds__(NT) k_label64(LabelArgs a) {
   }
   __syncthreads();
   uint32_t ph0 = 0, ph1 = 0;
-  const int64_t n = a.counters[CNT_N];
+  const int64_t n = a.counters[CNT_NIN];  // sorted points inside the union box
   const int64_t nitems = a.counters[CNT_ITEMS];
   for (;;) {
     if (tid == 0) s_item = (int64_t)atomicAdd((unsigned long long *)(a.counters + CNT_WORK), 1ull);
@@ -1664,22 +1706,6 @@ __device__ __forceinline__ void store64(const LabelArgs &a, int row, int64_t i, 
   atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_RESCUE), (unsigned long long)tris);
 }
 
-// Uncertain (point, row) pairs of the FP32 kernel into the pair list.
-__global__ void __launch_bounds__(256) k_unc_list(LabelArgs a) {
-  const int64_t n = a.counters[CNT_N];
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < kSplitPairs; j += (int64_t)gridDim.x * blockDim.x)
-    a.unc_done[j] = 0u;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long m = a.unc_mask[i];
-    while (m) {
-      const int row = __ffsll((long long)m) - 1;
-      m &= m - 1;
-      const unsigned long long slot = atomicAdd((unsigned long long *)(a.counters + CNT_UNC_LIST), 1ull);
-      if ((int64_t)slot < a.unc_cap) a.unc_list[slot] = make_int2((int)i, row);
-    }
-  }
-}
-
 // FP64 re-evaluation over the cap tree by listed pair: the point's own
 // range list (the tree walked for the point's zero-size box, so leaves near
 // the point and caps of every farther node), group64 over it.  Outside a
@@ -1726,6 +1752,10 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_list(LabelArgs a) {
     const int64_t pair = s_item / P;
     const int part = (int)(s_item - pair * P);
     const int2 e = a.unc_list[pair];
+    if (!ZEF_BOUNDS_OK(e.x >= 0 && e.x < a.counters[CNT_NIN] && e.y >= 0 && e.y < a.ncomp, a.status, 16)) {
+      __syncthreads();
+      continue;
+    }
     const float4 p = a.spts[e.x];
     // this part's share of the groups of four
     const int groups = s_tot / 4;
@@ -1765,7 +1795,7 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64_caps(LabelArgs a) {
   if (a.counters[CNT_UNC_LIST] <= a.unc_cap) return;  // k_rescue64_list took them
   const int tid = threadIdx.x;
   for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
-  const int64_t n = a.counters[CNT_N];
+  const int64_t n = a.counters[CNT_NIN];  // sorted points inside the union box
   const int64_t ngroups = (n + kRescueT - 1) / kRescueT;
   for (;;) {
     if (tid == 0) {
@@ -1817,7 +1847,7 @@ __global__ void __launch_bounds__(kRescueT) k_rescue64(LabelArgs a) {
   __shared__ int s_kred[kRescueT / 32];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (int c = tid; c < a.ncomp; c += blockDim.x) s_rowcomp[a.comps[c].row] = c;
-  const int64_t n = a.counters[CNT_N];
+  const int64_t n = a.counters[CNT_NIN];  // sorted points inside the union box
   const int64_t ngroups = (n + kRescueT - 1) / kRescueT;
   for (;;) {
     if (tid == 0) {
@@ -1964,11 +1994,12 @@ __global__ void k_prepare(int64_t *cnt, int64_t n, int64_t off) {
   }
 }
 
-// Device-count version used inside the refinement graph: n and offset come
-// from other counters.
-__global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
+// Counters of one call (the point count and offset are already in place: set
+// by k_prepare for host-known counts, by other kernels inside the refinement
+// and re-labeling graphs), the work-bucket histogram and the completion
+// counts of split FP64 re-evaluation pairs.
+__global__ void __launch_bounds__(256) k_reset(int64_t *cnt, uint32_t *work_hist, uint32_t *unc_done) {
   if (threadIdx.x == 0) {
-    const int64_t n = cnt[CNT_N];
     cnt[CNT_ITEMS] = 0;
     cnt[CNT_WORK] = 0;
     cnt[CNT_UNC] = 0;
@@ -1980,55 +2011,13 @@ __global__ void k_reset(int64_t *cnt, int tile, int ncomp) {
     cnt[CNT_REP_PAIRS] = 0;
     cnt[CNT_LANE_TILES] = 0;
     cnt[CNT_UNC_LIST] = 0;
-    int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
-    for (int k = 0; k < 3; ++k) {
-      box[k] = INT32_MAX;
-      box[3 + k] = INT32_MIN;
-    }
-    cnt[CNT_TILES] = (n + tile - 1) / tile;
-    (void)ncomp;
+    cnt[CNT_NIN] = 0;
+    cnt[CNT_NFIN] = 0;
+    cnt[CNT_TILES] = 0;
   }
-}
-
-__global__ void __launch_bounds__(256) k_bbox(const float *pts, int64_t *cnt, unsigned long long *in_mask,
-                                             unsigned long long *unc_mask) {
-  const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float *p = pts + 3 * (off + i);
-    float x = p[0], y = p[1], z = p[2];
-    in_mask[i] = 0ull;
-    unc_mask[i] = 0ull;
-    if (finite3(x, y, z)) {
-      lo[0] = fminf(lo[0], x); lo[1] = fminf(lo[1], y); lo[2] = fminf(lo[2], z);
-      hi[0] = fmaxf(hi[0], x); hi[1] = fmaxf(hi[1], y); hi[2] = fmaxf(hi[2], z);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    for (int o = 16; o > 0; o >>= 1) {
-      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-    }
-  }
-  // block reduction, then one atomic per block and bound (six addresses
-  // shared by the whole grid: per-warp atomics serialised on them)
-  __shared__ float red[6][8];
-  const int wid = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0)
-    for (int k = 0; k < 3; ++k) {
-      red[k][wid] = lo[k];
-      red[3 + k][wid] = hi[k];
-    }
-  __syncthreads();
-  if (threadIdx.x < 6) {
-    const int k = threadIdx.x;
-    float v = red[k][0];
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = k < 3 ? fminf(v, red[k][q]) : fmaxf(v, red[k][q]);
-    int *box = reinterpret_cast<int *>(cnt + CNT_BOX);
-    if (k < 3 && v != INFINITY) atomicMin(box + k, f2o(v));
-    if (k >= 3 && v != -INFINITY) atomicMax(box + k, f2o(v));
-  }
+  for (int j = threadIdx.x; j < kWorkBuckets; j += blockDim.x) work_hist[j] = 0u;
+  if (unc_done)
+    for (int j = threadIdx.x; j < kSplitPairs; j += blockDim.x) unc_done[j] = 0u;
 }
 
 // Warp-aggregated increment of ctr[key]: the lanes with equal keys share one
@@ -2036,7 +2025,7 @@ __global__ void __launch_bounds__(256) k_bbox(const float *pts, int64_t *cnt, un
 // before the increment plus the lane's rank among them.  Every lane of the
 // warp calls it; lanes with valid = false take no part.
 __device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key, bool valid, int lane) {
-  const uint32_t k = valid ? key : 0xffffffffu;  // keys have 21 bits
+  const uint32_t k = valid ? key : 0xffffffffu;  // keys are below kHistLen
   const uint32_t peers = __match_any_sync(0xffffffffu, k);
   const int leader = __ffs(peers) - 1;
   uint32_t base = 0;
@@ -2045,33 +2034,36 @@ __device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key, bool va
   return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, uint32_t *keys, uint32_t *hist) {
+// Binning key of every point: the 21-bit Morton cell of the point in the
+// union box of the registered surfaces (7 bits per axis), kKeyOutside for a
+// finite point outside that box -- outside every compartment's box, so its
+// winding number is 0 for every surface and it needs no tile -- and
+// kKeyNonfinite for a point with a NaN or infinite coordinate.  Sorted by
+// key, the points inside the box come first, then those outside, then the
+// non-finite ones.
+__global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, UnionBox ub, uint32_t *keys,
+                                             uint32_t *hist) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
-  const int *box = reinterpret_cast<const int *>(cnt + CNT_BOX);
-  float lo[3], sc[3];
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = o2f(box[k]);
-    float ext = o2f(box[3 + k]) - lo[k];
-    sc[k] = ext > 0.f ? (float)(1 << kMortonBits) / ext : 0.f;
-  }
   const int lane = threadIdx.x & 31;
   // warp-uniform loop: all lanes take part in the aggregated increments
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n;
        i0 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = i0 + lane;
     const bool valid = i < n;
+    const uint32_t spread = (uint32_t)(i0 >> 5) % kTailKeys;  // one tail key per warp and pass
     uint32_t key = 0;
     if (valid) {
       const float *p = pts + 3 * (off + i);
-      const float x = p[0], y = p[1], z = p[2];
-      if (finite3(x, y, z)) {
+      const float v[3] = {p[0], p[1], p[2]};
+      if (!finite3(v[0], v[1], v[2])) {
+        key = kKeyNonfinite + spread;
+      } else if (v[0] < ub.lo[0] || v[0] > ub.hi[0] || v[1] < ub.lo[1] || v[1] > ub.hi[1] ||
+                 v[2] < ub.lo[2] || v[2] > ub.hi[2]) {
+        key = kKeyOutside + spread;
+      } else {
         uint32_t q[3];
-        const float v[3] = {x, y, z};
-        for (int k = 0; k < 3; ++k) {
-          const float f = (v[k] - lo[k]) * sc[k];
-          const int qi = (int)f;
-          q[k] = (uint32_t)min(max(qi, 0), (1 << kMortonBits) - 1);
-        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) q[k] = (uint32_t)min((int)((v[k] - ub.lo[k]) * ub.sc[k]), (1 << kMortonBits) - 1);
         key = spread7(q[0]) | (spread7(q[1]) << 1) | (spread7(q[2]) << 2);
       }
       keys[i] = key;
@@ -2080,16 +2072,18 @@ __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, ui
   }
 }
 
-// Points in bucket order, multiplied by the context's power-of-two scale
-// (exact).  A non-finite input point becomes NaN; a finite one that the scale
-// would push past the float range is clamped (it is far outside every
-// surface either way).
+// Points in key order, multiplied by the context's power-of-two scale
+// (exact), with their permutation and cleared inside / uncertain masks.  A
+// non-finite input point becomes NaN; a finite one that the scale would push
+// past the float range is clamped (it lies outside every surface's box).
 __device__ __forceinline__ float scaled_coord(float x, float s) {
   return fminf(fmaxf(x * s, -3.0e38f), 3.0e38f);
 }
 
 __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt, const uint32_t *keys,
-                                                uint32_t *cursor, float4 *spts, int32_t *perm, float scale) {
+                                                uint32_t *cursor, float4 *spts, int32_t *perm,
+                                                unsigned long long *in_mask, unsigned long long *unc_mask,
+                                                float scale, uint32_t *status) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
   const int lane = threadIdx.x & 31;
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n;
@@ -2107,35 +2101,42 @@ __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt,
       const float nan = __int_as_float(0x7fc00000);
       q = make_float4(nan, nan, nan, 0.f);
     }
+    if (!ZEF_BOUNDS_OK((int64_t)pos < n, status, 17)) continue;
     spts[pos] = q;
     perm[pos] = (int32_t)i;
+    in_mask[pos] = 0ull;
+    unc_mask[pos] = 0ull;
   }
 }
 
-// Bounding box of every tile of `tile` (= 32 P) consecutive sorted points:
-// one warp per tile, P points per lane, shuffle reductions.
+// Box of the points [b, e) of the sorted array, reduced over the warp (every
+// lane returns it); empty: (+inf, -inf).
+__device__ __forceinline__ void warp_box(const float4 *spts, int64_t b, int64_t e, int lane, float *lo, float *hi) {
+  lo[0] = lo[1] = lo[2] = INFINITY;
+  hi[0] = hi[1] = hi[2] = -INFINITY;
+  for (int64_t i = b + lane; i < e; i += 32) {
+    const float4 p = spts[i];
+    lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+    hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+}
+
+// Bounding box of every tile of `tile` consecutive sorted points inside the
+// union box (the plain FP64 kernel's tiles): one warp per tile.
 __global__ void __launch_bounds__(256) k_tile_box(const float4 *spts, int64_t *cnt, float *tile_box, int tile) {
-  const int64_t n = cnt[CNT_N];
+  const int64_t nin = cnt[CNT_NIN];
   const int64_t ntiles = cnt[CNT_TILES];
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += warps) {
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    const int64_t b = t * tile;
-    const int64_t e = min(b + tile, n);
-    for (int64_t i = b + lane; i < e; i += 32) {
-      const float4 p = spts[i];
-      if (finite3(p.x, p.y, p.z)) {
-        lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
-        hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      for (int o = 16; o > 0; o >>= 1) {
-        lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-        hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-      }
+    float lo[3], hi[3];
+    warp_box(spts, t * tile, min(t * tile + tile, nin), lane, lo, hi);
     if (lane < 6) tile_box[t * 6 + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
   }
 }
@@ -2171,66 +2172,88 @@ __global__ void __launch_bounds__(256) k_emit(int64_t *cnt, const uint32_t *scan
   }
 }
 
-// Work list of the FP32 kernel: every tile whose box meets at least one
-// compartment box, largest estimated work (sum of the met compartments'
-// triangle counts) first, bucketed on a log scale (4096 buckets).
-constexpr int kWorkBuckets = 4096;
+// Work list of the FP32 kernel: every tile of `tile` (= 32 P) consecutive
+// sorted points inside the union box whose box meets at least one
+// compartment's box and convex-hull bound, largest estimated work (the sum of
+// the met compartments' triangle counts) first, bucketed on a log scale
+// (kWorkBuckets buckets).  One warp per tile: the lanes reduce the tile's box,
+// then split the compartments.
 constexpr uint32_t kNoWork = 0xffffffffu;
 
-__global__ void __launch_bounds__(256) k_tile_work(int64_t *cnt, const float *tile_box, const DevComp *comps,
+__global__ void __launch_bounds__(256) k_tile_work(const float4 *spts, int64_t *cnt, int tile, const DevComp *comps,
                                                   int ncomp, const float *dop, uint32_t *tile_key, uint32_t *hist) {
+  const int64_t nin = cnt[CNT_NIN];
   const int64_t ntiles = cnt[CNT_TILES];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
-    const float *b = tile_box + t * 6;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += warps) {
+    float lo[3], hi[3];
+    warp_box(spts, t * tile, min(t * tile + tile, nin), lane, lo, hi);
+    const float b[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
     float est = 0.f;
-    for (int c = 0; c < ncomp; ++c) {
-      const DevComp &d = comps[c];
-      const bool ov = !(b[3] < d.lo[0] || b[0] > d.hi[0] || b[4] < d.lo[1] || b[1] > d.hi[1] || b[5] < d.lo[2] ||
-                        b[2] > d.hi[2]) &&
-                      !dop_box_misses(b, dop + (int64_t)c * kDop);
-      if (ov) est += (float)d.tri_cnt;
+    for (int c0 = 0; c0 < ncomp; c0 += 32) {
+      // box test: one compartment per lane; hull test of the met ones: the
+      // whole warp per compartment
+      const int c = c0 + lane;
+      bool ov = false;
+      if (c < ncomp) {
+        const DevComp &d = comps[c];
+        ov = !(b[3] < d.lo[0] || b[0] > d.hi[0] || b[4] < d.lo[1] || b[1] > d.hi[1] || b[5] < d.lo[2] ||
+               b[2] > d.hi[2]);
+      }
+      uint32_t met = __ballot_sync(0xffffffffu, ov);
+      while (met) {
+        const int cc = c0 + __ffs(met) - 1;
+        met &= met - 1;
+        if (!dop_box_misses_warp(b, dop + (int64_t)cc * kDop, lane)) est += (float)__ldg(&comps[cc].tri_cnt);
+      }
     }
-    uint32_t key = kNoWork;
-    if (est > 0.f) {
-      const int lg = (int)(__log2f(est) * 128.f);
-      key = (uint32_t)(kWorkBuckets - 1 - min(kWorkBuckets - 1, max(0, lg)));
-      atomicAdd(hist + key, 1u);
+    if (lane == 0) {
+      uint32_t key = kNoWork;
+      if (est > 0.f) {
+        const int lg = (int)(__log2f(est) * 128.f);
+        key = (uint32_t)(kWorkBuckets - 1 - min(kWorkBuckets - 1, max(0, lg)));
+        atomicAdd(hist + key, 1u);
+      }
+      tile_key[t] = key;
     }
-    tile_key[t] = key;
   }
 }
 
 __global__ void __launch_bounds__(256) k_tile_scatter(int64_t *cnt, const uint32_t *tile_key, uint32_t *cursor,
-                                                     int2 *items) {
+                                                     int2 *items, uint32_t *status) {
   const int64_t ntiles = cnt[CNT_TILES];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t key = tile_key[t];
     if (key == kNoWork) continue;
     const uint32_t pos = atomicAdd(cursor + key, 1u);
+    if (!ZEF_BOUNDS_OK((int64_t)pos < ntiles, status, 19)) continue;
     items[pos] = make_int2((int)t, (int)key);
   }
 }
 
-__global__ void __launch_bounds__(256) k_resolve(LabelArgs a, const float *pts, int32_t *labels,
-                                                const int32_t *row_ids) {
-  const int64_t n = a.counters[CNT_N], off = a.counters[CNT_OFF];
+// Labels in the caller's order: the first set bit of the priority-ordered
+// inside mask -> id (0 when none; the points outside the union box have an
+// empty mask), -1 for the non-finite points (the tail of the sorted order).
+__global__ void __launch_bounds__(256) k_resolve(LabelArgs a, int32_t *labels, const int32_t *row_ids) {
+  const int64_t n = a.counters[CNT_N], off = a.counters[CNT_OFF], nfin = a.counters[CNT_NFIN];
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[CNT_NONFINITE] = n - nfin;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 p = a.spts[i];
+    const int32_t o = a.perm[i];
+    if (!ZEF_BOUNDS_OK(o >= 0 && o < n, a.status, 18)) continue;
     int32_t lab;
-    if (!finite3(p.x, p.y, p.z)) {
+    if (i >= nfin) {
       lab = -1;
-      atomicAdd((unsigned long long *)(a.counters + CNT_NONFINITE), 1ull);
-      if (a.masks_out) a.masks_out[off + a.perm[i]] = 0ull;
+      if (a.masks_out) a.masks_out[off + o] = 0ull;
       if (a.omega)
-        for (int r = 0; r < a.ncomp; ++r) a.omega[(int64_t)r * a.omega_ld + a.perm[i]] = __int_as_float(0x7fc00000);
+        for (int r = 0; r < a.ncomp; ++r) a.omega[(int64_t)r * a.omega_ld + o] = __int_as_float(0x7fc00000);
     } else {
       const unsigned long long m = a.in_mask[i];
       lab = m ? row_ids[__ffsll((long long)m) - 1] : 0;
-      if (a.masks_out) a.masks_out[off + a.perm[i]] = m;
+      if (a.masks_out) a.masks_out[off + o] = m;
     }
-    labels[off + a.perm[i]] = lab;
+    labels[off + o] = lab;
   }
-  (void)pts;
 }
 
 // ------------------------------------------------------------------ exclusive scan (uint32, in place)
@@ -2307,6 +2330,52 @@ __global__ void __launch_bounds__(kScanT) k_scan_add(uint32_t *data, const int64
     if (b0 + k < len) data[b0 + k] += add;
 }
 
+// k_scan_add of the key histogram (kHistLen entries), which also records
+// where the sorted order's tails start -- the first position of the points
+// outside the union box (= the points inside it) and of the non-finite
+// points -- and the tile count of the points inside.
+__global__ void __launch_bounds__(kScanT) k_scan_add_keys(uint32_t *data, const uint32_t *bsums, int64_t *cnt,
+                                                         int tile) {
+  const int64_t b0 = (int64_t)blockIdx.x * kScanB + (int64_t)threadIdx.x * kScanV;
+  const uint32_t add = bsums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanV; ++k) {
+    const int64_t j = b0 + k;
+    if (j < kHistLen) {
+      const uint32_t v = data[j] + add;
+      data[j] = v;
+      if (j == (int64_t)kKeyOutside) {
+        cnt[CNT_NIN] = v;
+        cnt[CNT_TILES] = ((int64_t)v + tile - 1) / tile;
+      } else if (j == (int64_t)kKeyNonfinite) {
+        cnt[CNT_NFIN] = v;
+      }
+    }
+  }
+}
+
+// Exclusive scan of the kWorkBuckets work histogram by one block; the total
+// (work items) goes to *total_out.
+__global__ void __launch_bounds__(1024) k_scan_work(uint32_t *data, int64_t *total_out) {
+  constexpr int V = kWorkBuckets / 1024;
+  uint32_t v[V];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    v[k] = data[threadIdx.x * V + k];
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t pre = block_excl_scan(s, &tot);
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    data[threadIdx.x * V + k] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) *total_out = (int64_t)tot;
+}
+static_assert(kWorkBuckets % 1024 == 0, "k_scan_work: whole values per thread");
+
 // ------------------------------------------------------------------ launch helpers
 template <int NT, int P, int V>
 zef_status launch_label32(zef_ctx *ctx, const LabelArgs &a) {
@@ -2360,8 +2429,22 @@ zef_status scan_inplace(zef_ctx *ctx, uint32_t *data, const int64_t *len_ptr, in
   k_scan_blocks<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(data, len_ptr, len_c, len_mul, ctx->lb.block_sums);
   k_scan_sums<<<1, 1024, 0, ctx->stream>>>(ctx->lb.block_sums, len_ptr, len_c, len_mul, total_out);
   k_scan_add<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(data, len_ptr, len_c, len_mul, ctx->lb.block_sums);
+  ctx->launches += 3;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "scan launch");
+  return ZEF_OK;
+}
+
+// Exclusive scan of the key histogram, recording the tails of the sorted
+// order and the tile count (k_scan_add_keys).
+zef_status scan_keys(zef_ctx *ctx, uint32_t *hist, int tile) {
+  const int64_t nb = (kHistLen + kScanB - 1) / kScanB;
+  k_scan_blocks<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(hist, nullptr, kHistLen, 1, ctx->lb.block_sums);
+  k_scan_sums<<<1, 1024, 0, ctx->stream>>>(ctx->lb.block_sums, nullptr, kHistLen, 1, nullptr);
+  k_scan_add_keys<<<(unsigned)nb, kScanT, 0, ctx->stream>>>(hist, ctx->lb.block_sums, ctx->lb.counters, tile);
+  ctx->launches += 3;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "key scan launch");
   return ZEF_OK;
 }
 
@@ -2391,7 +2474,7 @@ bool shape_valid(int threads, int ppt) {
 
 void fill_default_opts(zef_label_opts *o) {
   if (!(o->margin > 0.f)) o->margin = 1e-3f;
-  if (!(o->winding_tol > 0.f)) o->winding_tol = 1e-4f;
+  if (!(o->winding_tol > 0.f)) o->winding_tol = 1e-5f;
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -2517,7 +2600,7 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap) {
     if ((st = realloc((void **)&b.pts_tmp, cap * 3 * sizeof(float)))) return st;
     b.cap_points = cap;
   }
-  const int64_t need_flags = std::max<int64_t>(tiles * std::max(C, 1), (int64_t)kBuckets);
+  const int64_t need_flags = std::max<int64_t>(tiles * std::max(C, 1), kHistLen);
   if (b.cap_tiles < tiles || b.cap_items < need_flags) {
     if (b.tile_box) cudaFree(b.tile_box);
     if (b.flags) cudaFree(b.flags);
@@ -2533,13 +2616,13 @@ zef_status label_reserve(zef_ctx *ctx, int64_t n_cap) {
     if ((e = cudaMalloc(&b.tile_box, ft * 6 * sizeof(float))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
     if ((e = cudaMalloc(&b.flags, need_flags * sizeof(uint32_t))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
     if ((e = cudaMalloc(&b.items, need_flags * sizeof(int2))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
-    if ((e = cudaMalloc(&b.block_sums, ((need_flags + kScanB - 1) / kScanB + 1) * sizeof(uint32_t))) != cudaSuccess)
+    if ((e = cudaMalloc(&b.block_sums, scan_block_sums(need_flags) * sizeof(uint32_t))) != cudaSuccess)
       return cuda_fail(ctx, e, "cudaMalloc");
     b.cap_tiles = ft;
     b.cap_items = need_flags;
   }
   if (!b.hist) {
-    cudaError_t e = cudaMalloc(&b.hist, (size_t)kBuckets * sizeof(uint32_t));
+    cudaError_t e = cudaMalloc(&b.hist, (size_t)(kHistLen + kWorkBuckets) * sizeof(uint32_t));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(hist)");
   }
   if (!b.unc_list) {
@@ -2565,35 +2648,46 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   const int tile = plan.opts.precision == ZEF_FP64_PLAIN ? plan.shape.threads * plan.shape.ppt
                                                          : 32 * plan.shape.ppt;
   cudaStream_t s = ctx->stream;
+  uint32_t *work_hist = b.hist + kHistLen;
+  double *unc_part = b.unc_list ? reinterpret_cast<double *>(b.unc_list + kUncListCap) : nullptr;
+  uint32_t *unc_done = b.unc_list ? reinterpret_cast<uint32_t *>(unc_part + (size_t)kSplitPairs * kMaxParts) : nullptr;
+  int64_t launches = 0;
+  NvtxRange nvtx_stage("zef.binning");
   if (plan.timed) cudaEventRecord(ctx->ev[0], s);
-  k_reset<<<1, 32, 0, s>>>(b.counters, tile, C);
+  k_reset<<<1, 256, 0, s>>>(b.counters, work_hist, unc_done);
+  ++launches;
   // Omega of (point, compartment) pairs culled by the bounding boxes is 0
   if (plan.omega) cudaMemsetAsync(plan.omega, 0, (size_t)C * plan.omega_ld * sizeof(float), s);
   const int64_t ncap = plan.n_cap;
   const int g = grid_for(ctx, ncap, 256);
-  k_bbox<<<g, 256, 0, s>>>(plan.pts, b.counters, b.in_mask, b.unc_mask);
-  cudaMemsetAsync(b.hist, 0, (size_t)kBuckets * sizeof(uint32_t), s);
-  k_keys<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist);
-  zef_status st = scan_inplace(ctx, b.hist, nullptr, 1, kBuckets, nullptr);
+  // binning: keys in the surfaces' union box, key histogram, scan, scatter
+  cudaMemsetAsync(b.hist, 0, (size_t)kHistLen * sizeof(uint32_t), s);
+  k_keys<<<g, 256, 0, s>>>(plan.pts, b.counters, ctx->ubox, b.keys, b.hist);
+  ++launches;
+  zef_status st = scan_keys(ctx, b.hist, tile);
   if (st) return st;
-  k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm, ctx->scale);
+  k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm, b.in_mask, b.unc_mask,
+                              ctx->scale, ctx->d_status);
+  ++launches;
   const int64_t tiles_cap = (ncap + tile - 1) / tile;
-  k_tile_box<<<grid_for(ctx, tiles_cap * 32, 256), 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
+  const int gt = grid_for(ctx, tiles_cap * 32, 256);  // one warp per tile
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
     // (tile, compartment) items for the plain FP64 kernel
+    k_tile_box<<<gt, 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
     k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,
                                                                ctx->d_dop, b.flags);
+    launches += 2;
     st = scan_inplace(ctx, b.flags, b.counters + CNT_TILES, C, tiles_cap * C, b.counters + CNT_ITEMS);
     if (st) return st;
     k_emit<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.flags, ctx->d_lpt, C, b.items);
+    ++launches;
   } else {
     // tile items, largest estimated work first
-    cudaMemsetAsync(b.hist, 0, (size_t)kWorkBuckets * sizeof(uint32_t), s);
-    k_tile_work<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, C, ctx->d_dop,
-                                                              b.flags, b.hist);
-    st = scan_inplace(ctx, b.hist, nullptr, 1, kWorkBuckets, b.counters + CNT_ITEMS);
-    if (st) return st;
-    k_tile_scatter<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.flags, b.hist, b.items);
+    k_tile_work<<<gt, 256, 0, s>>>(b.spts, b.counters, tile, ctx->d_comps, C, ctx->d_dop, b.flags, work_hist);
+    k_scan_work<<<1, 1024, 0, s>>>(work_hist, b.counters + CNT_ITEMS);
+    k_tile_scatter<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.flags, work_hist, b.items,
+                                                                 ctx->d_status);
+    launches += 3;
   }
 
   LabelArgs a;
@@ -2617,14 +2711,20 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   a.fp32_only = plan.opts.precision == ZEF_FP32_ONLY;
   a.coherence = !(plan.opts.flags & ZEF_NO_TILE_COHERENCE);
   a.lane_walk = (plan.opts.flags & ZEF_POINT_WALK) ? 0 : 1;
+  a.omega_raw = (plan.opts.flags & ZEF_OMEGA_RAW) ? 1 : 0;
   a.early = plan.omega == nullptr && !plan.full_masks;
   a.nodes = ctx->d_nodes;
   a.cseg = ctx->d_cseg;
-  a.unc_list = b.unc_list;
-  a.unc_cap = b.unc_list ? b.cap_unc : 0;
-  a.unc_part = b.unc_list ? reinterpret_cast<double *>(b.unc_list + kUncListCap) : nullptr;
-  a.unc_done = b.unc_list ? reinterpret_cast<uint32_t *>(a.unc_part + (size_t)kSplitPairs * kMaxParts) : nullptr;
+  // the pair list serves the cap-tree form's FP64 re-evaluation
+  const bool pair_list = plan.shape.variant == 2 && plan.opts.precision == ZEF_FP32_RESCUE && b.unc_list;
+  a.unc_list = pair_list ? b.unc_list : nullptr;
+  a.unc_cap = pair_list ? b.cap_unc : 0;
+  a.unc_part = unc_part;
+  a.unc_done = unc_done;
   a.masks_out = plan.masks;
+  a.n_nodes = (int64_t)ctx->h_nodes.size();
+  a.n_cseg = (int64_t)ctx->h_cseg.size();
+  nvtx_stage.next("zef.label_kernel");
   if (plan.timed) cudaEventRecord(ctx->ev[1], s);
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
     // the FP64 kernel's tile is 128 x 2 points (choose_shape guarantees it)
@@ -2634,21 +2734,28 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
     st = dispatch_label32(ctx, a, plan.shape);
   }
   if (st) return st;
+  ++launches;
   if (plan.timed) cudaEventRecord(ctx->ev[2], s);
+  nvtx_stage.next("zef.rescue64");
   if (plan.timed) cudaEventRecord(ctx->ev[3], s);
   if (plan.opts.precision == ZEF_FP32_RESCUE) {
-    if (plan.shape.variant == 2) {
+    if (pair_list) {
       // the pair list when it holds every uncertain pair, else by point groups
-      k_unc_list<<<g, 256, 0, s>>>(a);
       k_rescue64_list<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
       k_rescue64_caps<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+      launches += 2;
     } else {
       k_rescue64<<<ctx->num_sms * 4, kRescueT, 0, s>>>(a);
+      ++launches;
     }
   }
   if (plan.timed) cudaEventRecord(ctx->ev[4], s);
-  k_resolve<<<g, 256, 0, s>>>(a, plan.pts, plan.labels, ctx->d_row_ids);
+  nvtx_stage.next("zef.resolve");
+  k_resolve<<<g, 256, 0, s>>>(a, plan.labels, ctx->d_row_ids);
+  ++launches;
   if (plan.timed) cudaEventRecord(ctx->ev[5], s);
+  // scan_keys and scan_inplace counted their own launches
+  ctx->launches += launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "label pipeline launch");
   return ZEF_OK;
@@ -2715,6 +2822,7 @@ zef_status launch_debug_half_angle(zef_ctx *ctx, const float *y, const float *x,
 // Set the point count and offset of a label_points call (host-known values).
 zef_status label_set_count(zef_ctx *ctx, int64_t n, int64_t off) {
   k_prepare<<<1, 32, 0, ctx->stream>>>(ctx->lb.counters, n, off);
+  ++ctx->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "k_prepare launch");
   return ZEF_OK;
@@ -2730,6 +2838,7 @@ zef_status upload_dop_directions(zef_ctx *ctx) {
   float dirs[kDop][3];
   dop_directions(dirs);
   cudaError_t e = cudaMemcpyToSymbol(c_dop, dirs, sizeof(dirs));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dop, dirs, sizeof(dirs));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "upload hull directions");
   return ZEF_OK;
 }

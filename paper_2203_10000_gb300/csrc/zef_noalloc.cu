@@ -10,13 +10,15 @@
 // below, whose size is fixed at compile time.
 //
 // The array is a static __device__ object: every GPU that loads the library
-// holds it (kScratchBytes, about 10.7 MB) until the process exits.  In host
-// code its name is only a host-side stand-in, so its device address is looked
-// up once per device with cudaGetSymbolAddress (device current) and cached.
+// holds it (kScratchBytes, about 12 MB) until the process exits.  In host
+// code its name is only a host-side stand-in, so every call looks up its
+// device address with cudaGetSymbolAddress on the context's device (made
+// current).  The lookup is not cached: a cached address would dangle after
+// cudaDeviceReset, which rebuilds the device's context and reloads the
+// library's device code.
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "zef_internal.h"
 
@@ -27,9 +29,10 @@ using namespace zef;
 constexpr int64_t kMaxPoints = ZEF_NOALLOC_MAX_POINTS;
 constexpr int64_t kMinTile = 32 * 2;                         // smallest tile of any shape
 constexpr int64_t kMaxTiles = (kMaxPoints + kMinTile - 1) / kMinTile;
-constexpr int64_t kMaxFlags = kMaxTiles * ZEF_MAX_COMPARTMENTS;
-constexpr int64_t kScanBlock = 2048;                         // elements per scan block
-constexpr int64_t kMaxBlockSums = (kBuckets > kMaxFlags ? kBuckets : kMaxFlags) / kScanBlock + 2;
+constexpr int64_t kMaxFlags = kMaxTiles * ZEF_MAX_COMPARTMENTS;  // FP64 (tile, compartment) flags
+// block sums of the largest scan the pipeline runs here: the key histogram,
+// or the FP64 kernel's flags
+constexpr int64_t kMaxBlockSums = scan_block_sums(kHistLen > kMaxFlags ? kHistLen : kMaxFlags);
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -41,31 +44,28 @@ constexpr size_t kOffIn = align256(kOffKeys + kMaxPoints * sizeof(uint32_t));
 constexpr size_t kOffUnc = align256(kOffIn + kMaxPoints * sizeof(unsigned long long));
 constexpr size_t kOffBox = align256(kOffUnc + kMaxPoints * sizeof(unsigned long long));
 constexpr size_t kOffHist = align256(kOffBox + kMaxTiles * 6 * sizeof(float));
-constexpr size_t kOffFlags = align256(kOffHist + kBuckets * sizeof(uint32_t));
+constexpr size_t kOffFlags = align256(kOffHist + (kHistLen + kWorkBuckets) * sizeof(uint32_t));
 constexpr size_t kOffSums = align256(kOffFlags + kMaxFlags * sizeof(uint32_t));
 constexpr size_t kOffItems = align256(kOffSums + kMaxBlockSums * sizeof(uint32_t));
 constexpr size_t kOffUncList = align256(kOffItems + kMaxFlags * sizeof(int2));
 constexpr size_t kOffCnt = align256(kOffUncList + kUncBytes);
 constexpr size_t kScratchBytes = align256(kOffCnt + CNT_COUNT_ * sizeof(int64_t));
 
+// What the pipeline may touch must fit the pieces above: tiles of the
+// smallest shape (32 x 2 points) over kMaxPoints points, the (tile,
+// compartment) flags and items of the plain FP64 kernel (tiles of 256 points,
+// so at most kMaxTiles of them as well), the block sums of the key scan and
+// of the flag scan, and the uncertain-pair list.
+static_assert(kMaxTiles * kMinTile >= kMaxPoints, "tile boxes and keys cover every point");
+static_assert(kMaxFlags >= kMaxTiles * ZEF_MAX_COMPARTMENTS, "FP64 flags and items");
+static_assert(kMaxBlockSums >= scan_block_sums(kHistLen), "block sums of the key scan");
+static_assert(kMaxBlockSums >= scan_block_sums(kMaxFlags), "block sums of the flag scan");
+static_assert(kOffCnt - kOffUncList >= kUncBytes, "uncertain-pair list");
+
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_addr[256] = {};  // device address of g_scratch, per device ordinal
-
-// Device address of g_scratch on `device` (which must be current).
-cudaError_t scratch_address(int device, void **out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
-  if (!g_addr[device]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[device] = p;
-  }
-  *out = g_addr[device];
-  return cudaSuccess;
-}
+// Device address of g_scratch on the current device.
+cudaError_t scratch_address(void **out) { return cudaGetSymbolAddress(out, g_scratch); }
 
 bool device_pointer(const void *p, int device) {
   cudaPointerAttributes a;
@@ -81,6 +81,7 @@ bool device_pointer(const void *p, int device) {
 extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
                                                float *omega, const zef_label_opts *opts,
                                                zef_label_stats *stats) {
+  NvtxRange nvtx_("zef.label_points_noalloc");
   if (!ctx) return ZEF_ERR_INVALID_ARG;
   ctx->err.clear();
   if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
@@ -95,7 +96,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
   fill_default_opts(&o);
   if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
-  if (o.flags & ~(ZEF_NO_TILE_COHERENCE | ZEF_POINT_WALK)) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
+  if (o.flags & ~kLabelFlagsAll) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
   if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
   if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -115,7 +116,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
       (omega && !device_pointer(omega, ctx->device)))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "zef_label_points_noalloc needs device pointers");
   void *base = nullptr;
-  cudaError_t e = scratch_address(ctx->device, &base);
+  cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(scratch)");
   unsigned char *s = static_cast<unsigned char *>(base);
 
@@ -157,8 +158,10 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
   // histogram, masks, Omega).
   LabelBuffers saved = ctx->lb;
   ctx->lb = view;
+  const int64_t launches0 = ctx->launches;
   zef_status st = label_set_count(ctx, n, 0);
   if (st == ZEF_OK) st = label_enqueue(ctx, plan);
+  const int64_t launches = ctx->launches - launches0;
   ctx->lb = saved;
   if (st) return st;
   if (stats) {
@@ -180,6 +183,7 @@ extern "C" zef_status zef_label_points_noalloc(zef_ctx *ctx, const float *pts, i
     stats->coherent_pairs = h[CNT_COHERENT];
     stats->representative_pairs = h[CNT_REP_PAIRS];
     stats->lane_walk_items = h[CNT_LANE_TILES];
+    stats->kernel_launches = launches;
     stats->block_threads = plan.shape.threads;
     stats->points_per_thread = plan.shape.ppt;
     float ms = 0.f;

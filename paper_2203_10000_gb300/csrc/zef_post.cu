@@ -438,6 +438,7 @@ zef_status build_adjacency(zef_ctx *ctx, const int32_t *tets, int64_t m, int64_t
 
 zef_status taubin_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m, const uint8_t *fixed,
                       const zef_smooth_opts &o, int32_t *iters_out) {
+  NvtxRange nvtx_("zef.taubin_smooth");
   const bool dn = on_dev(nodes, ctx->device);
   const bool dt = m == 0 ? dn : on_dev(tets, ctx->device);
   const bool df = fixed ? on_dev(fixed, ctx->device) : dn;
@@ -526,6 +527,7 @@ zef_status taubin_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets
 
 zef_status inflate_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m, int32_t id,
                        float zeta, int64_t *moved_out) {
+  NvtxRange nvtx_("zef.inflate");
   int row = -1, ci = -1;
   for (size_t r = 0; r < ctx->priority.size(); ++r)
     if (ctx->priority[r] == id) row = (int)r;

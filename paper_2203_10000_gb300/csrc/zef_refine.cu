@@ -579,6 +579,7 @@ zef_status capture_while(zef_ctx *ctx, cudaStream_t cap, cudaStream_t aux, F &&b
 
 zef_status refine_run(zef_ctx *ctx, zef_mesh *mesh, int32_t levels, const zef_label_opts &opts,
                       zef_level_stats *per_level) {
+  NvtxRange nvtx_("zef.refine_and_relabel");
   const int64_t N0 = mesh->num_nodes, M0 = mesh->num_tets;
   const int64_t ncap = mesh->node_capacity, tcap = mesh->tet_capacity;
   const bool dn = device_ptr(mesh->nodes, ctx->device), dt = device_ptr(mesh->tets, ctx->device),

@@ -167,6 +167,7 @@ uint64_t bits(float f) {
 zef_status relabel_run(zef_ctx *ctx, const float *nodes_in, int64_t n, const int32_t *tets_in, int64_t m,
                        int32_t *labels_io, int32_t max_passes, const zef_label_opts &opts,
                        zef_relabel_pass *per_pass, int32_t *passes, int32_t *converged) {
+  NvtxRange nvtx_("zef.relabel_boundary");
   if (n == 0) {
     if (converged) *converged = 1;
     return ZEF_OK;

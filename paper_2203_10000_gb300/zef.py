@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libzef.so")
+# ZEF_LIBRARY selects another build of the library (the debug variant built by
+# build.build(debug=True)); default: the release build
+LIB_PATH = os.environ.get("ZEF_LIBRARY") or os.path.join(_HERE, "_build", "libzef.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libzef.so is not built ({LIB_PATH}); run paper_2203_10000_gb300.build.build()")
@@ -29,17 +31,19 @@ ZEF_ERR_CUDA = 5
 ZEF_ERR_TIMEOUT = 6
 ZEF_ERR_NOT_READY = 7
 ZEF_ERR_CAPACITY = 8
+ZEF_ERR_BOUNDS = 9
 ZEF_AUTO_ORIENT = 1
 ZEF_FP32_RESCUE = 0
 ZEF_FP64_PLAIN = 1
 ZEF_FP32_ONLY = 2
 ZEF_NO_TILE_COHERENCE = 1
 ZEF_POINT_WALK = 2
+ZEF_OMEGA_RAW = 4
 MAX_COMPARTMENTS = 64
 
 STATUS_NAMES = {0: "ZEF_OK", 1: "ZEF_ERR_INVALID_ARG", 2: "ZEF_ERR_SURFACE_NOT_CLOSED",
                 3: "ZEF_ERR_SURFACE_ORIENTATION", 4: "ZEF_ERR_OOM", 5: "ZEF_ERR_CUDA",
-                6: "ZEF_ERR_TIMEOUT", 7: "ZEF_ERR_NOT_READY", 8: "ZEF_ERR_CAPACITY"}
+                6: "ZEF_ERR_TIMEOUT", 7: "ZEF_ERR_NOT_READY", 8: "ZEF_ERR_CAPACITY", 9: "ZEF_ERR_BOUNDS"}
 
 # exported symbols of include/zef.h (checked by the CPU tests)
 EXPORTED = ["zef_create", "zef_destroy", "zef_last_error", "zef_add_compartment",
@@ -63,7 +67,7 @@ class LabelStats(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("ms_label", ctypes.c_float),
                 ("ms_rescue", ctypes.c_float), ("reserved", ctypes.c_float),
                 ("coherent_pairs", ctypes.c_int64), ("representative_pairs", ctypes.c_int64),
-                ("lane_walk_items", ctypes.c_int64)]
+                ("lane_walk_items", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -186,10 +190,12 @@ def _contig(x, dtype_np, dtype_name):
 
 
 def make_opts(margin=0.0, winding_tol=0.0, precision=ZEF_FP32_RESCUE, block_threads=0,
-              points_per_thread=0, kernel=0, coherence=True, point_walk=False) -> LabelOpts:
+              points_per_thread=0, kernel=0, coherence=True, point_walk=False,
+              omega_raw=False) -> LabelOpts:
     o = LabelOpts()
     o.kernel = kernel
-    o.flags = (0 if coherence else ZEF_NO_TILE_COHERENCE) | (ZEF_POINT_WALK if point_walk else 0)
+    o.flags = ((0 if coherence else ZEF_NO_TILE_COHERENCE) | (ZEF_POINT_WALK if point_walk else 0)
+               | (ZEF_OMEGA_RAW if omega_raw else 0))
     o.margin = margin
     o.winding_tol = winding_tol
     o.precision = precision

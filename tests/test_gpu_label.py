@@ -127,7 +127,13 @@ def test_config0_parity(zef, oracle_mod):
     assert_parity(lab, om, olab, oom)
     assert st["pairs_evaluated"] <= st["pairs_nominal"]
     tile = 32 * st["points_per_thread"]   # one warp's tile
-    assert st["work_items"] >= 1 and st["tiles"] == (len(w.points) + tile - 1) // tile
+    # tiles cover the points inside the surfaces' union box (the others are
+    # outside every compartment: winding number 0, no tile)
+    v = np.concatenate([s.verts for s in w.surfaces])
+    inside = np.all((w.points >= v.min(0)) & (w.points <= v.max(0)), axis=1)
+    assert 0 < inside.sum() < len(w.points)
+    assert st["work_items"] >= 1 and st["tiles"] == (int(inside.sum()) + tile - 1) // tile
+    assert st["kernel_launches"] > 0
 
 
 def test_config0_host_pointers_match_device(zef):
@@ -217,7 +223,7 @@ def test_point_walk_matches_shared_lists(zef, oracle_mod):
     assert_parity(lab_p[idx], om_p[:, idx], olab, oom)
     # the flag is validated
     o = zef.make_opts()
-    o.flags = 4
+    o.flags = 8  # not a label flag
     with pytest.raises(zef.ZefError):
         ctx.label_points(torch.from_numpy(g[:100]).cuda(), opts=o)
 

@@ -4,8 +4,14 @@ compiled into libzef instead of cudaMalloc).
 
 Its results must equal those of zef_label_points on the same inputs, on two
 calls in a row (the shared scratch keeps the previous call's contents, so the
-second call checks that everything that must start at zero is cleared).  This
-file is collected last so that a failure here does not hide any other test.
+second call checks that everything that must start at zero is cleared).  The
+cases cover the sizing edges of the fixed array: exactly
+ZEF_NOALLOC_MAX_POINTS points over several compartments, the plain FP64
+kernel (whose (tile, compartment) flags and items live in the array), the
+strip kernel forms, and a call without Omega.  The first calls run on a fresh
+context, before zef_label_points ever ran on it, and free device memory must
+not change across them.  This file is collected last so that a failure here
+does not hide any other test.
 """
 import ctypes
 
@@ -30,37 +36,101 @@ def zef():
     return z
 
 
-def _call_noalloc(zef, ctx, pts, labels, omega):
-    st = zef.LabelStats()
-    rc = zef.lib().zef_label_points_noalloc(ctx.handle, pts.data_ptr(), pts.shape[0], labels.data_ptr(),
-                                            omega.data_ptr() if omega is not None else None,
-                                            ctypes.byref(zef.make_opts()), ctypes.byref(st))
-    return rc, st
-
-
-def test_noalloc_matches_label_points_two_calls(zef):
-    w = zs.config0()
+def _ctx(zef, w):
     ctx = zef.Context(0)
     for s in w.surfaces:
         ctx.add_compartment(s.id, s.verts, s.tris)
     ctx.set_priority(w.priority)
+    return ctx
+
+
+def _call_noalloc(zef, ctx, pts, labels, omega, opts=None):
+    st = zef.LabelStats()
+    o = opts if opts is not None else zef.make_opts()
+    rc = zef.lib().zef_label_points_noalloc(ctx.handle, pts.data_ptr(), pts.shape[0], labels.data_ptr(),
+                                            omega.data_ptr() if omega is not None else None,
+                                            ctypes.byref(o), ctypes.byref(st))
+    return rc, st
+
+
+def _head_sample(n):
+    """n points of the three-layer head's 2 mm lattice: the centred window of
+    the lattice order (every compartment's box is crossed there)."""
+    w = zs.config1()
+    c = w.points.shape[0] // 2
+    w.points = np.ascontiguousarray(w.points[c - n // 2: c - n // 2 + n])
+    return w
+
+
+def test_noalloc_matches_label_points_two_calls(zef):
+    w = zs.config0()
+    ctx = _ctx(zef, w)
     pts = torch.from_numpy(w.points).cuda()
     n = pts.shape[0]
     assert n <= zef.NOALLOC_MAX_POINTS
-    ref_lab, ref_om, _ = ctx.label_points(pts, want_omega=True)
+    # the allocation-free calls first, on a fresh context (no work buffers of
+    # zef_label_points exist yet): free device memory must not move between
+    # them (the first call may load the library's device code)
+    outs = []
+    labs = [torch.full((n,), -7, dtype=torch.int32, device="cuda") for _ in range(2)]
+    oms = [torch.full((1, n), float("nan"), dtype=torch.float32, device="cuda") for _ in range(2)]
     torch.cuda.synchronize()
-    ref_lab = ref_lab.cpu().numpy()
-    ref_om = ref_om.cpu().numpy()
+    free = []
     for rep in range(2):
-        lab = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-        om = torch.full((1, n), float("nan"), dtype=torch.float32, device="cuda")
-        rc, st = _call_noalloc(zef, ctx, pts, lab, om)
+        rc, st = _call_noalloc(zef, ctx, pts, labs[rep], oms[rep])
         assert rc == zef.ZEF_OK, zef.lib().zef_last_error(ctx.handle)
         torch.cuda.synchronize()
-        assert np.array_equal(lab.cpu().numpy(), ref_lab), f"labels differ on call {rep + 1}"
-        err = np.abs(om.cpu().numpy().astype(np.float64) - ref_om.astype(np.float64)).max()
+        free.append(torch.cuda.mem_get_info()[0])
+        assert st.points == n and st.pairs_evaluated > 0 and st.kernel_launches > 0
+        outs.append((labs[rep].cpu().numpy(), oms[rep].cpu().numpy()))
+    assert free[0] == free[1], f"free device memory changed by {free[0] - free[1]} bytes"
+    # then the reference on a second context
+    ctx2 = _ctx(zef, w)
+    ref_lab, ref_om, _ = ctx2.label_points(pts, want_omega=True)
+    torch.cuda.synchronize()
+    ref_lab = ref_lab.cpu().numpy()
+    ref_om = ref_om.cpu().numpy().astype(np.float64)
+    for rep, (lab, om) in enumerate(outs):
+        assert np.array_equal(lab, ref_lab), f"labels differ on call {rep + 1}"
+        err = np.abs(om.astype(np.float64) - ref_om).max()
         assert err <= OMEGA_TOL, f"Omega differs by {err} on call {rep + 1}"
-        assert st.points == n and st.pairs_evaluated > 0
+    ctx.close()
+    ctx2.close()
+
+
+@pytest.mark.parametrize("case", ["max_points", "fp64_plain", "strip_kernel", "no_omega"])
+def test_noalloc_sizing_edges_match_label_points(zef, oracle_mod, case):
+    """Multi-compartment head at the largest call size (and the FP64 tiles,
+    the strip form, the call without Omega), two calls in a row against
+    zef_label_points; a seeded sample also against the FP64 oracle."""
+    n = {"max_points": zef.NOALLOC_MAX_POINTS, "fp64_plain": 8192, "strip_kernel": 16384,
+         "no_omega": zef.NOALLOC_MAX_POINTS}[case]
+    opts = {"fp64_plain": zef.make_opts(precision=zef.ZEF_FP64_PLAIN),
+            "strip_kernel": zef.make_opts(kernel=1)}.get(case, zef.make_opts())
+    w = _head_sample(n)
+    C = len(w.surfaces)
+    ctx = _ctx(zef, w)
+    pts = torch.from_numpy(w.points).cuda()
+    want_omega = case != "no_omega"
+    ref_lab, ref_om, _ = ctx.label_points(pts, want_omega=want_omega, opts=opts)
+    torch.cuda.synchronize()
+    ref_lab = ref_lab.cpu().numpy()
+    for rep in range(2):
+        lab = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        om = torch.full((C, n), float("nan"), dtype=torch.float32, device="cuda") if want_omega else None
+        rc, st = _call_noalloc(zef, ctx, pts, lab, om, opts)
+        assert rc == zef.ZEF_OK, zef.lib().zef_last_error(ctx.handle)
+        torch.cuda.synchronize()
+        lab = lab.cpu().numpy()
+        assert np.array_equal(lab, ref_lab), f"labels differ on call {rep + 1}"
+        if want_omega:
+            err = np.abs(om.cpu().numpy().astype(np.float64) - ref_om.cpu().numpy().astype(np.float64)).max()
+            assert err <= OMEGA_TOL, f"Omega differs by {err} on call {rep + 1}"
+        assert st.points == n and st.tiles > 0
+    idx = zs.sample_rows(w.points, 400, seed=7)
+    olab, _ = oracle_mod.label_points(w.points[idx], w.surfaces, w.priority)
+    assert np.array_equal(lab[idx], olab)
+    assert np.unique(olab).size >= 3       # the sample reaches several compartments
     ctx.close()
 
 
