@@ -5,7 +5,12 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 Readings where the printed formulas are garbled or silent:
   * smoothing: N_i is node i together with the nodes joined to it by a mesh
-    edge (volumetric smoothing); the printed sums of neighbour positions are
+    edge (volumetric smoothing), or, for the smoothing of the tissue
+    boundaries, by an edge of a boundary face -- a triangle shared by two
+    tets of different element labels (a face of only one tet lies on the
+    mesh's outer boundary, not between tissues); only the nodes of boundary
+    faces move then, and the norms of the stopping rule run over them; the
+    printed sums of neighbour positions are
     read as the Laplacian L(x)_i = sum_{j in N_i} (x_j - x_i) / |N_i|; one
     iteration is x' = x + lambda L(x) (forward step) followed by
     x'' = x' - mu L(x') (backward step); nodes marked fixed do not move; the
@@ -61,6 +66,57 @@ def taubin_smooth(nodes, tets, lam: float, mu: float, xi: float, max_iters: int,
         if step <= xi:
             break
     return x, it
+
+
+def boundary_faces(tets, elem_labels) -> np.ndarray:
+    """Tissue-boundary faces of a labeled tet mesh: sorted node triples of the
+    triangles shared by two tets whose element labels differ."""
+    t = np.asarray(tets, dtype=np.int64).reshape(-1, 4)
+    lab = np.asarray(elem_labels).reshape(-1)
+    faces = np.concatenate([t[:, [0, 1, 2]], t[:, [0, 1, 3]], t[:, [0, 2, 3]], t[:, [1, 2, 3]]])
+    faces.sort(axis=1)
+    flab = np.concatenate([lab, lab, lab, lab])
+    uniq, inv, cnt = np.unique(faces, axis=0, return_inverse=True, return_counts=True)
+    inv = inv.reshape(-1)
+    lo = np.full(uniq.shape[0], np.iinfo(np.int64).max)
+    hi = np.full(uniq.shape[0], np.iinfo(np.int64).min)
+    np.minimum.at(lo, inv, flab)
+    np.maximum.at(hi, inv, flab)
+    return uniq[(cnt == 2) & (lo != hi)]
+
+
+def face_edges(faces) -> np.ndarray:
+    """Sorted unique node pairs of the triangles' three edges."""
+    f = np.asarray(faces, dtype=np.int64).reshape(-1, 3)
+    if f.size == 0:
+        return np.zeros((0, 2), np.int64)
+    pairs = np.concatenate([f[:, [0, 1]], f[:, [0, 2]], f[:, [1, 2]]])
+    pairs.sort(axis=1)
+    return np.unique(pairs, axis=0)
+
+
+def taubin_smooth_surface(nodes, tets, elem_labels, lam: float, mu: float, xi: float, max_iters: int):
+    """Taubin smoothing of the tissue boundaries (Sec. 2.2.1): the iteration of
+    taubin_smooth over the graph of the boundary faces' edges; nodes off the
+    boundary do not move.  Returns (positions float64 (N, 3), iterations run,
+    number of boundary faces)."""
+    x = np.asarray(nodes, dtype=np.float64).reshape(-1, 3).copy()
+    faces = boundary_faces(tets, elem_labels)
+    edges = face_edges(faces)
+    on = np.zeros(x.shape[0], bool)
+    on[faces.ravel()] = True
+    x0 = np.linalg.norm(x[on])
+    it = 0
+    while it < max_iters and on.any():
+        xh = x + lam * laplacian(x, edges)
+        xh[~on] = x[~on]
+        step = np.linalg.norm(xh[on] - x[on]) / x0
+        x = xh - mu * laplacian(xh, edges)
+        x[~on] = xh[~on]
+        it += 1
+        if step <= xi:
+            break
+    return x, it, int(faces.shape[0])
 
 
 def segment_surface_distance(p, q, verts, tris):

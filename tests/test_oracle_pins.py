@@ -614,3 +614,105 @@ def test_inflation_towards_box_faces():
     want[m] += disp[m] / cnt[m, None]
     assert moved == int(m.sum()) > 10
     np.testing.assert_allclose(out, want, atol=1e-12)
+
+
+# ------------------------------------------------------------------ boundary-surface smoothing (Sec. 2.2.1)
+def _block_labels(nodes, tets, lo, hi):
+    """Element label 1 for the tets of the lattice cells inside [lo, hi)
+    (cell corners on the integer lattice), else 0."""
+    c = nodes[tets].astype(np.float64).mean(axis=1)
+    cell = np.floor(c)
+    return np.all((cell >= lo) & (cell < hi), axis=1).astype(np.int32)
+
+
+def _faces_brute(tets, labels):
+    """Tissue-boundary faces by a dictionary over every tet face."""
+    seen = {}
+    for t, lab in zip(tets, labels):
+        t = [int(v) for v in t]
+        for f in ((t[0], t[1], t[2]), (t[0], t[1], t[3]), (t[0], t[2], t[3]), (t[1], t[2], t[3])):
+            seen.setdefault(tuple(sorted(f)), []).append(int(lab))
+    return sorted(f for f, ls in seen.items() if len(ls) == 2 and ls[0] != ls[1])
+
+
+def test_boundary_faces_of_a_labeled_block():
+    """A block of a x b x c lattice cells labeled 1 in a lattice labeled 0:
+    every cell face of the block's surface is split into two triangles by
+    the five-tet subdivision, so there are 4 (ab + bc + ca) boundary faces,
+    each on one of the block's six planes."""
+    from oracle import postprocess as pp
+    nodes, tets = zs.lattice_5tet(6, 1.0, (0.0, 0.0, 0.0))
+    lo, hi = np.array([1, 2, 1]), np.array([4, 5, 3])
+    lab = _block_labels(nodes, tets, lo, hi)
+    faces = pp.boundary_faces(tets, lab)
+    a, b, c = hi - lo
+    assert faces.shape[0] == 4 * (a * b + b * c + c * a)
+    assert [tuple(f) for f in faces.tolist()] == _faces_brute(tets, lab)
+    x = nodes[faces].astype(np.float64)          # (F, 3 nodes, 3)
+    on_plane = np.zeros(faces.shape[0], bool)
+    for ax in range(3):
+        for v in (lo[ax], hi[ax]):
+            on_plane |= np.all(x[:, :, ax] == v, axis=1)
+    assert on_plane.all()
+    # no boundary where every label is equal
+    assert pp.boundary_faces(tets, np.zeros(len(tets), np.int32)).shape[0] == 0
+
+
+def test_surface_taubin_step_equals_dense_form():
+    """One iteration over the boundary graph equals
+    (I - mu M)(I + lambda M) x on the boundary nodes, M = (D + I)^-1 (A - D)
+    with A the adjacency of the brute-force boundary faces' edges; the other
+    nodes keep their positions exactly."""
+    from oracle import postprocess as pp
+    nodes, tets = zs.lattice_5tet(5, 1.0, (0.0, 0.0, 0.0))
+    lab = _block_labels(nodes, tets, np.array([1, 1, 1]), np.array([4, 3, 4]))
+    rng = np.random.default_rng(11)
+    x = nodes.astype(np.float64) + rng.normal(0, 0.15, nodes.shape)
+    faces = _faces_brute(tets, lab)
+    n = x.shape[0]
+    A = np.zeros((n, n))
+    for f in faces:
+        for i in f:
+            for j in f:
+                if i != j:
+                    A[i, j] = 1.0
+    on = A.sum(1) > 0
+    D = np.diag(A.sum(1))
+    M = np.linalg.solve(D + np.eye(n), A - D)
+    lam, mu = 0.4, 0.4
+    out, it, nf = pp.taubin_smooth_surface(x, tets, lab, lam, mu, xi=10.0, max_iters=1)
+    assert it == 1 and nf == len(faces)
+    want = (np.eye(n) - mu * M) @ ((np.eye(n) + lam * M) @ x)
+    np.testing.assert_allclose(out[on], want[on], rtol=0, atol=1e-12)
+    assert np.array_equal(out[~on], x[~on])
+
+
+def test_surface_taubin_keeps_face_planes_and_stops():
+    """On the unperturbed lattice a node inside a face of the block, two
+    lattice steps or more from the face's edges, has its boundary neighbours
+    and theirs in that face's plane through one iteration (forward and
+    backward step), so its normal coordinate stays exactly; the block's
+    corners move (the boundary shrinks where it bends); translation commutes
+    with the smoothing; a large xi stops after one iteration."""
+    from oracle import postprocess as pp
+    nodes, tets = zs.lattice_5tet(8, 1.0, (0.0, 0.0, 0.0))
+    lo, hi = np.array([1, 1, 1]), np.array([7, 7, 6])
+    lab = _block_labels(nodes, tets, lo, hi)
+    x = nodes.astype(np.float64)
+    out, it, _ = pp.taubin_smooth_surface(x, tets, lab, 0.4, 0.4, 0.0, 1)
+    assert it == 1
+    for ax in range(3):
+        others = [k for k in range(3) if k != ax]
+        for v in (lo[ax], hi[ax]):
+            inner = (x[:, ax] == v) & np.all((x[:, others] >= lo[others] + 2) & (x[:, others] <= hi[others] - 2),
+                                             axis=1)
+            assert inner.any()
+            assert np.array_equal(out[inner, ax], x[inner, ax])
+    corner = np.all((x == lo) | (x == hi), axis=1)
+    assert corner.sum() == 8 and np.all(np.linalg.norm(out[corner] - x[corner], axis=1) > 1e-3)
+    off = ~np.isin(np.arange(len(x)), pp.boundary_faces(tets, lab).ravel())
+    assert np.array_equal(out[off], x[off])
+    moved, _, _ = pp.taubin_smooth_surface(x + [3.0, -2.0, 5.0], tets, lab, 0.4, 0.4, 0.0, 1)
+    np.testing.assert_allclose(moved - [3.0, -2.0, 5.0], out, atol=1e-12)
+    _, i1, _ = pp.taubin_smooth_surface(x, tets, lab, 0.4, 0.4, 0.9, 50)
+    assert i1 == 1
