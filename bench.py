@@ -374,6 +374,13 @@ def refine_measure(zef, torch, dev):
         its, ms = timed(lambda: ctx.taubin_smooth(xs, rt, 0.4, 0.4, 0.0, 10))
     out["taubin_smooth"] = {"nodes": n1, "tets": m1, "iterations": its, "ms": ms,
                             "note": "includes building the unique-edge adjacency"}
+    # the tissue boundaries of the element labels, the paper's stop rule xi = 0.1
+    for rep in range(2):
+        xs.copy_(rn)
+        (sits, nfaces), ms = timed(lambda: ctx.taubin_smooth_surface(xs, rt, elem, 0.4, 0.4, 0.1, 100))
+    out["taubin_smooth_surface"] = {"nodes": n1, "tets": m1, "boundary_faces": nfaces, "iterations": sits,
+                                    "xi": 0.1, "ms": ms,
+                                    "note": "includes finding the boundary faces and their edge adjacency"}
     brain = [s_.id for s_ in w.surfaces if s_.name == "brain"][0]
     for rep in range(2):
         xs.copy_(rn)

@@ -383,6 +383,29 @@ zef_status zef_taubin_smooth(zef_ctx *ctx, float *nodes, int64_t n_nodes, const 
                              int64_t n_tets, const uint8_t *fixed, const zef_smooth_opts *opts,
                              int32_t *iterations);
 
+/* Taubin smoothing of the tissue boundaries (Sec. 2.2.1: both the volume and
+   the tissue boundaries are smoothed; the paper's experiments stop the
+   boundary smoothing at xi = 0.1).  A boundary face is a triangle shared by
+   two tets whose element labels differ (a face of a single tet lies on the
+   mesh's outer boundary, not between tissues).  The neighbourhood N_i of a
+   node on a boundary face is the node and every node joined to it by an edge
+   of a boundary face; the iteration is zef_taubin_smooth's over that graph,
+   so nodes on no boundary face do not move, and the norms of the stopping
+   rule run over the boundary nodes.
+     nodes           [n_nodes][3] float32, in/out
+     tets            [n_tets][4] int32 node indices
+     elem_labels     [n_tets] int32 element labels (zef_label_elements' output,
+                     or any other labeling)
+     opts            as zef_taubin_smooth
+     iterations      nullable out: iterations run (0 when there is no
+                     boundary face)
+     boundary_faces  nullable out: boundary faces found
+   nodes, tets and elem_labels must all be host or all device memory; the
+   call synchronizes.  Errors as zef_taubin_smooth. */
+zef_status zef_taubin_smooth_surface(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets,
+                                     int64_t n_tets, const int32_t *elem_labels, const zef_smooth_opts *opts,
+                                     int32_t *iterations, int64_t *boundary_faces);
+
 /* One inflation of the nodes inside compartment `compartment_id`'s surface S
    towards S (Sec. 2.2.2).  A mesh edge with one node inside S (Omega > 2 pi)
    and the other outside crosses S; the inside node i moves by

@@ -759,6 +759,27 @@ zef_status zef_taubin_smooth(zef_ctx *ctx, float *nodes, int64_t n_nodes, const 
   return taubin_run(ctx, nodes, n_nodes, tets, n_tets, fixed, *opts, iterations);
 }
 
+zef_status zef_taubin_smooth_surface(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets,
+                                     int64_t n_tets, const int32_t *elem_labels, const zef_smooth_opts *opts,
+                                     int32_t *iterations, int64_t *boundary_faces) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context");
+  if (!opts || n_nodes < 0 || n_tets < 0 || (n_nodes > 0 && !nodes) || (n_tets > 0 && (!tets || !elem_labels)))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "bad smoothing arguments");
+  if (n_nodes > ((int64_t)1 << 31) - 1 || n_tets > ((int64_t)1 << 31) - 1)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "too many nodes or tets (max 2^31-1)");
+  if (n_tets > 0 && n_nodes == 0) return fail(ctx, ZEF_ERR_INVALID_ARG, "tets without nodes");
+  if (!(opts->lambda >= 0.f && opts->lambda < 1.f) || !(opts->mu >= 0.f && opts->mu < 1.f) ||
+      !(opts->xi >= 0.f) || opts->max_iters < 1 || opts->max_iters > 100000)
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "smoothing parameters out of range");
+  if (iterations) *iterations = 0;
+  if (boundary_faces) *boundary_faces = 0;
+  if (n_nodes == 0) return ZEF_OK;
+  DeviceGuard g(ctx->device);
+  return taubin_surface_run(ctx, nodes, n_nodes, tets, n_tets, elem_labels, *opts, iterations, boundary_faces);
+}
+
 zef_status zef_inflate(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                        int32_t compartment_id, float zeta, int64_t *moved) {
   if (!ctx) return ZEF_ERR_INVALID_ARG;

@@ -280,8 +280,8 @@ struct zef_ctx {
   int64_t el_cap_nodes = 0, el_cap_masks = 0, el_cap_tets = 0, el_cap_labels = 0;
 
   // post-processing scratch (smoothing, inflation)
-  void *pp_buf[14] = {};
-  size_t pp_cap[14] = {};
+  void *pp_buf[18] = {};
+  size_t pp_cap[18] = {};
 
   // recursive re-labeling scratch and its cached graph
   void *rb_buf[9] = {};
@@ -335,6 +335,9 @@ zef_status taubin_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets
                       const zef_smooth_opts &o, int32_t *iters_out);
 zef_status inflate_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m, int32_t id,
                        float zeta, int64_t *moved_out);
+zef_status taubin_surface_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m,
+                              const int32_t *elem_labels, const zef_smooth_opts &o, int32_t *iters_out,
+                              int64_t *faces_out);
 zef_status launch_elem_labels(zef_ctx *ctx, const int32_t *tets, int64_t n_tets, int64_t n_nodes,
                               const int32_t *node_labels, const unsigned long long *masks, int32_t *elem);
 zef_status debug_fma_rate(zef_ctx *ctx, int fp64, double *tflops);

@@ -683,16 +683,23 @@ constexpr int kMaxRanges = 192;
 // more evaluated pairs).
 constexpr float kCapMargin = 1.f / 64.f;
 
+// With `lout` (non-null) the walk also lists the leaf segments alone (the
+// only ones whose triangles can meet the box: a cap lies in its node's box,
+// which misses it): *lcnt ranges holding *ltot entries, or *lcnt = -1 when
+// they exceed kMaxLeafRanges.
+constexpr int kMaxLeafRanges = 64;
+
 __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb, int2 *out, int *total,
-                          int *tris, bool all_leaves, float margin = 0.f) {
-  int n = 0, tot = 0, nt = 0;
+                          int *tris, bool all_leaves, float margin = 0.f, int2 *lout = nullptr,
+                          int *lcnt = nullptr, int *ltot = nullptr) {
+  int n = 0, tot = 0, nt = 0, nl = 0, lt = 0;
   // pre-order walk without a stack: descend to i + 1, or continue at skip
   const int root = __ldg(&cp->cap_root);
   const int end = __ldg(&a.nodes[root].skip);
   for (int i = root; i != end;) {
     if (!ZEF_BOUNDS_OK(i >= 0 && i < a.n_nodes, a.status, 10)) {
       n = 0;
-      tot = nt = 0;
+      tot = nt = nl = lt = 0;
       break;
     }
     const CapNode nd = a.nodes[i];
@@ -725,6 +732,12 @@ __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb
       n = -1;
       break;
     }
+    if (lout && !far && nl >= 0) {
+      lt += c;
+      if (nl > 0 && lout[nl - 1].x + lout[nl - 1].y == b) lout[nl - 1].y += c;
+      else if (nl < kMaxLeafRanges) lout[nl++] = make_int2(b, c);
+      else nl = -1;
+    }
   }
   if (n < 0 && all_leaves) {  // every leaf segment: the compartment's own triangles
     out[0] = make_int2(__ldg(&cp->cseg_off), __ldg(&cp->cseg_leaf));
@@ -734,6 +747,10 @@ __device__ int cap_ranges(const LabelArgs &a, const DevComp *cp, const float *wb
   }
   *total = tot;
   *tris = nt;
+  if (lout) {
+    *lcnt = nl;
+    *ltot = nl < 0 ? 0 : lt;
+  }
   return n;
 }
 
@@ -759,85 +776,27 @@ __device__ __forceinline__ bool seg_tri(const Entry *E, int pos, float4 &A, floa
   return true;
 }
 
-// Van Oosterom-Strackee half angle of a triangle (A, B, C) with oriented
-// normal n seen from r: N = R_A . n, D = r_A r_B r_C + (R_A . R_B) r_C +
-// (R_A . R_C) r_B + (R_B . R_C) r_A; bad = min(bad, max(|N|, D) - kappa |n| r_A).
-__device__ __forceinline__ void tri_nd(float px, float py, float pz, float4 A, float4 B, float4 C, float4 nn,
-                                       float &N, float &D, float &bad) {
-  const float ax = A.x - px, ay = A.y - py, az = A.z - pz;
-  const float bx = B.x - px, by = B.y - py, bz = B.z - pz;
-  const float cx = C.x - px, cy = C.y - py, cz = C.z - pz;
-  const float qa = fmaf(ax, ax, fmaf(ay, ay, az * az));
-  const float qb = fmaf(bx, bx, fmaf(by, by, bz * bz));
-  const float qc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-  const float ra = qa * rsqrtf(qa), rb = qb * rsqrtf(qb), rc = qc * rsqrtf(qc);
-  N = fmaf(ax, nn.x, fmaf(ay, nn.y, az * nn.z));
-  const float dab = fmaf(ax, bx, fmaf(ay, by, az * bz));
-  const float dac = fmaf(ax, cx, fmaf(ay, cy, az * cz));
-  const float dbc = fmaf(bx, cx, fmaf(by, cy, bz * cz));
-  D = fmaf(ra * rb, rc, fmaf(dab, rc, fmaf(dac, rb, dbc * ra)));
-  bad = fminf(bad, fmaf(-nn.w, ra, fmaxf(fabsf(N), D)));
-}
 
-// rep_pass over a range list (one entry per lane; *scanned receives the
-// triangles evaluated)
-__device__ __forceinline__ bool rep_pass_caps(const LabelArgs &a, const int2 *rng, int total, const float *wb,
-                                              float rx, float ry, float rz, int lane, int *k, int *t_hit,
-                                              int *scanned) {
-  float lx = 0.f, ly = 0.f, lz = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
-  if (wb) {
-    lx = wb[0]; ly = wb[1]; lz = wb[2]; hx = wb[3]; hy = wb[4]; hz = wb[5];
-  }
-  *t_hit = -1;
-  int ntri = 0;
-  float sum = 0.f, comp = 0.f, bad = __int_as_float(0x7f800000);
-  int r = 0, rb = 0;
-  for (int t0 = 0; t0 < total; t0 += 32) {
-    const int j = t0 + lane;
-    bool ov = false, is_tri = false;
-    float term = 0.f;
-    if (j < total) {
-      float4 A, B, C, nn;
-      is_tri = seg_tri(a.cseg, range_pos(rng, r, rb, j), A, B, C, nn);
-      if (is_tri) {
-        if (wb)
-          ov = !(fmaxf(A.x, fmaxf(B.x, C.x)) < lx || fminf(A.x, fminf(B.x, C.x)) > hx ||
-                 fmaxf(A.y, fmaxf(B.y, C.y)) < ly || fminf(A.y, fminf(B.y, C.y)) > hy ||
-                 fmaxf(A.z, fmaxf(B.z, C.z)) < lz || fminf(A.z, fminf(B.z, C.z)) > hz);
-        float N, D;
-        tri_nd(rx, ry, rz, A, B, C, nn, N, D, bad);
-        term = half_angle(N, D);
-      }
-    }
-    if (wb && __any_sync(0xffffffffu, ov)) {
-      *t_hit = t0;
-      *scanned = ntri;
-      return false;
-    }
-    ntri += __popc(__ballot_sync(0xffffffffu, is_tri));
-    const float y = term - comp;
-    const float tt = sum + y;
-    comp = (tt - sum) - y;
-    sum = tt;
-  }
-  *scanned = ntri;
-  return rep_certain(a, sum, -comp, bad, k);
-}
-
+// Groups of a tile (16 consecutive points each, boxes gb[g]) whose box
+// meets the box of some triangle of the leaf ranges (the surface's own
+// triangles near the tile); *tile_hit reports whether any triangle box meets
+// the tile's box wb.  Only the groups in `need` are tested; the pass ends
+// once all of them are hit.
 template <int NG>
-__device__ __forceinline__ uint32_t touched_groups_caps(const LabelArgs &a, const int2 *rng, int total,
-                                                        const float *wb, const float (*gb)[6], uint32_t need,
-                                                        int t_begin, int lane) {
+__device__ __forceinline__ uint32_t touched_leaves(const LabelArgs &a, const int2 *lrng, int ltot, const float *wb,
+                                                   const float (*gb)[6], uint32_t need, int lane, bool *tile_hit) {
   uint32_t hit = 0;
+  bool th = false;
   int r = 0, rb = 0;
-  for (int t0 = t_begin; t0 < total; t0 += 32) {
+  for (int t0 = 0; t0 < ltot; t0 += 32) {
     const int j = t0 + lane;
     float4 A, B, C, nn;
-    if (j < total && seg_tri(a.cseg, range_pos(rng, r, rb, j), A, B, C, nn)) {
+    if (j < ltot && seg_tri(a.cseg, range_pos(lrng, r, rb, j), A, B, C, nn)) {
       const float ux = fmaxf(A.x, fmaxf(B.x, C.x)), lx = fminf(A.x, fminf(B.x, C.x));
       const float uy = fmaxf(A.y, fmaxf(B.y, C.y)), ly = fminf(A.y, fminf(B.y, C.y));
       const float uz = fmaxf(A.z, fmaxf(B.z, C.z)), lz = fminf(A.z, fminf(B.z, C.z));
       if (!(ux < wb[0] || lx > wb[3] || uy < wb[1] || ly > wb[4] || uz < wb[2] || lz > wb[5])) {
+        th = true;
 #pragma unroll
         for (int g = 0; g < NG; ++g)
           if (((need >> g) & 1u) && !(ux < gb[g][0] || lx > gb[g][3] || uy < gb[g][1] || ly > gb[g][4] ||
@@ -846,40 +805,147 @@ __device__ __forceinline__ uint32_t touched_groups_caps(const LabelArgs &a, cons
       }
     }
     hit = __reduce_or_sync(0xffffffffu, hit);
+    th = __any_sync(0xffffffffu, th);
     if (hit == need) break;
   }
+  *tile_hit = th;
   return hit;
 }
 
-template <int NG>
-__device__ __forceinline__ uint32_t group_reps_caps(const LabelArgs &a, const int2 *rng, int total, uint32_t u,
-                                                    const float (*rp)[3], int lane, int (&k)[NG]) {
-  float sum[NG], comp[NG], bad[NG];
-#pragma unroll
-  for (int g = 0; g < NG; ++g) {
-    sum[g] = comp[g] = 0.f;
-    bad[g] = __int_as_float(0x7f800000);
-  }
-  int r = 0, rb = 0;
-  for (int j = lane; j < total; j += 32) {
-    float4 A, B, C, nn;
-    if (!seg_tri(a.cseg, range_pos(rng, r, rb, j), A, B, C, nn)) continue;
-#pragma unroll
-    for (int g = 0; g < NG; ++g)
-      if ((u >> g) & 1u) {
-        float N, D;
-        tri_nd(rp[g][0], rp[g][1], rp[g][2], A, B, C, nn, N, D, bad[g]);
-        const float y = half_angle(N, D) - comp[g];
-        const float tt = sum[g] + y;
-        comp[g] = (tt - sum[g]) - y;
-        sum[g] = tt;
+// Window of a strip group opened from the two entries before it (A, B): the
+// state the sequential stream holds after those two steps, computed with the
+// same operations (so the group's factors are the stream's own).
+__device__ __forceinline__ void window_prime(PState &s, float4 A, float4 B) {
+  s.ax = A.x - s.px;
+  s.ay = A.y - s.py;
+  s.az = A.z - s.pz;
+  s.bx = B.x - s.px;
+  s.by = B.y - s.py;
+  s.bz = B.z - s.pz;
+  const float qa = fmaf(s.ax, s.ax, fmaf(s.ay, s.ay, s.az * s.az));
+  const float qb = fmaf(s.bx, s.bx, fmaf(s.by, s.by, s.bz * s.bz));
+  s.ra = qa * rsqrtf(qa);
+  s.rb = qb * rsqrtf(qb);
+  s.sab = fmaf(s.ra, s.rb, fmaf(s.ax, s.bx, fmaf(s.ay, s.by, s.az * s.bz)));
+}
+
+// Sums of nr <= NR representative points over a range list of strip
+// segments, the entries split over the lanes instead of the points: the list
+// streams through the warp's double buffer in chunks of kWChunk entries and
+// lane l takes the group of four entries [4 l, 4 l + 4) of each chunk.  A
+// group opens its window from the two entries before it (the same segment:
+// segments hold whole groups of four) or restarts at a reset entry, so its
+// four (D + i N) factors are those the sequential stream forms; one atan2 per
+// group, wraps counted as in the point-by-point sums, a Kahan sum per lane.
+// The lanes' sums, wraps and conditioning minima are then combined and each
+// representative is certified by the tests of classify_store.  Returns false
+// when a bounded wait expired; bit r of *certain (r < nr) marks a certified
+// representative, its winding number in k[r].
+template <int NR>
+__device__ __noinline__ bool rep_stream(const LabelArgs &a, const int2 *rng, int total, Entry *wbuf, uint64_t *bar,
+                                        uint32_t &ph0, uint32_t &ph1, int lane, const float (*rp)[3], int nr,
+                                        uint32_t *certain, int (&k)[NR]) {
+  const int nchunks = (total + kWChunk - 1) / kWChunk;
+  int fr = 0, fb = 0;  // lane 0's fill cursor over the ranges
+  auto fill = [&](int ch, int b) {
+    const int j0 = ch * kWChunk, j1 = min(total, j0 + kWChunk);
+    tma_expect(&bar[b], (uint32_t)(j1 - j0) * (uint32_t)sizeof(Entry));
+    int j = j0;
+    while (j < j1) {
+      while (j >= fb + rng[fr].y) {
+        fb += rng[fr].y;
+        ++fr;
       }
+      const int take = min(j1 - j, fb + rng[fr].y - j);
+      tma_copy_1d(wbuf + b * kWChunk + (j - j0), a.cseg + (rng[fr].x + (j - fb)),
+                  (uint32_t)take * (uint32_t)sizeof(Entry), &bar[b]);
+      j += take;
+    }
+  };
+  if (lane == 0) {
+    if (nchunks > 0) fill(0, 0);
+    if (nchunks > 1) fill(1, 1);
   }
-  uint32_t certain = 0;
+  float sum[NR], comp[NR], bad[NR];
+  int wr[NR];
 #pragma unroll
-  for (int g = 0; g < NG; ++g)
-    if (((u >> g) & 1u) && rep_certain(a, sum[g], -comp[g], bad[g], &k[g])) certain |= 1u << g;
-  return certain;
+  for (int r = 0; r < NR; ++r) {
+    sum[r] = comp[r] = 0.f;
+    bad[r] = __int_as_float(0x7f800000);
+    wr[r] = 0;
+  }
+  float4 p2 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p2;  // the previous chunk's last two vertices
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int b = ch & 1;
+    const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
+    if (__any_sync(0xffffffffu, !ok)) return false;
+    if (b) ph1 ^= 1; else ph0 ^= 1;
+    const Entry *E = wbuf + b * kWChunk;
+    const int cnt = min(kWChunk, total - ch * kWChunk);  // a multiple of four
+    const int j = 4 * lane;
+    if (j < cnt) {
+      const float4 v0 = E[j].v, n0 = E[j].n, v1 = E[j + 1].v, n1 = E[j + 1].n;
+      const float4 v2 = E[j + 2].v, n2 = E[j + 2].n, v3 = E[j + 3].v, n3 = E[j + 3].n;
+      const float4 A = j >= 2 ? E[j - 2].v : p2, B = j >= 1 ? E[j - 1].v : p1;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r >= nr) break;
+        PState st;
+        st.px = rp[r][0];
+        st.py = rp[r][1];
+        st.pz = rp[r][2];
+        st.bad = __int_as_float(0x7f800000);
+        st.kp = st.kn = 0u;
+        if (v0.w == 2.f) window_init(st, v0);
+        else window_prime(st, A, B);
+        float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+        geom_step(st, v0, n0, N0, D0);
+        geom_step(st, v1, n1, N1, D1);
+        cmul_wrap(D0, N0, D1, N1, r01, i01, st.kp, st.kn);
+        geom_step(st, v2, n2, N0, D0);
+        geom_step(st, v3, n3, N1, D1);
+        cmul_wrap(D0, N0, D1, N1, r23, i23, st.kp, st.kn);
+        cmul_wrap(r01, i01, r23, i23, R, I, st.kp, st.kn);
+        const float y = half_angle(I, R) - comp[r];
+        const float t = sum[r] + y;
+        comp[r] = (t - sum[r]) - y;
+        sum[r] = t;
+        wr[r] += (int)st.kp - (int)st.kn;
+        bad[r] = fminf(bad[r], st.bad);
+      }
+    }
+    p2 = E[cnt - 2].v;  // every chunk holds at least four entries
+    p1 = E[cnt - 1].v;
+    __syncwarp();  // every lane is done with buffer b before it is refilled
+    if (lane == 0 && ch + 2 < nchunks) fill(ch + 2, b);
+  }
+  uint32_t cert = 0;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    if (r >= nr) break;
+    float h = sum[r], he = -comp[r], bd = bad[r];
+    int w = wr[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ph = __shfl_xor_sync(0xffffffffu, h, o);
+      const float pe = __shfl_xor_sync(0xffffffffu, he, o);
+      two_sum_acc(h, he, ph, pe);
+      bd = fminf(bd, __shfl_xor_sync(0xffffffffu, bd, o));
+      w += __shfl_xor_sync(0xffffffffu, w, o);
+    }
+    h += he;
+    // Omega / 2 = h + 2 pi w; the distance to 4 pi Z from h alone (w drops out)
+    const float kf = rintf(h * kInvTwoPi);
+    const float dist = 2.f * fabsf(fmaf(-kTwoPi, kf, h));
+    const float om = 2.f * fmaf(kTwoPi, (float)w, h);
+    const bool unc = !isfinite(om) || !(bd > 0.f) || !(dist <= a.winding_tol) || !(fabsf(om - kTwoPi) >= a.margin);
+    if (!unc) {
+      cert |= 1u << r;
+      k[r] = w + (int)kf;
+    }
+  }
+  *certain = cert;
+  return true;
 }
 
 // Point-by-point sums over a range list of strip segments: chunks of
@@ -1155,7 +1221,9 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
   __shared__ float s_rep[NW][NG][3];
   constexpr int RN = V == 2 ? kMaxRanges : 1;
   __shared__ int2 s_rng[NW][RN];   // form 2: the tile's range list of the compartment
-  __shared__ int s_rtot[NW][2];
+  constexpr int LN = V == 2 ? kMaxLeafRanges : 1;
+  __shared__ int2 s_lrng[NW][LN];  // form 2: its leaf ranges alone
+  __shared__ int s_rtot[NW][4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, half = lane >> 4;
   Entry *wbuf = reinterpret_cast<Entry *>(smem_raw) + wid * 2 * kWChunk;
   uint64_t *bar = bars[wid];
@@ -1242,10 +1310,13 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       int rtotal = 0, rtris = 0;
       if constexpr (V == 2) {
         if (lane == 0) {
-          int tot = 0, nt = 0;
-          const int nr = cap_ranges(a, cp, s_wbox[wid], s_rng[wid], &tot, &nt, false, kCapMargin);
+          int tot = 0, nt = 0, nl = 0, lt = 0;
+          const int nr = cap_ranges(a, cp, s_wbox[wid], s_rng[wid], &tot, &nt, false, kCapMargin, s_lrng[wid], &nl,
+                                    &lt);
           s_rtot[wid][0] = nr < 0 ? -1 : tot;
           s_rtot[wid][1] = nt;
+          s_rtot[wid][2] = nl;
+          s_rtot[wid][3] = lt;
         }
         __syncwarp();
         rtotal = s_rtot[wid][0];
@@ -1284,14 +1355,125 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       int kg[NG];
 #pragma unroll
       for (int g = 0; g < NG; ++g) kg[g] = 0;
-      if (a.coherence) {
-        // Coherence: where no triangle's box meets a box of points, the
-        // surface does not cross that box (convex, hence connected), so all
-        // its points have the winding number of any one of them.  First the
-        // whole tile (representative: its first usable point), then, if some
-        // triangle box meets the tile, each group of 16 points.
-        // the tile's first usable point (positions are re-read from memory,
-        // not held in registers across the hot loop)
+      bool rep_ok = true;
+      if (a.coherence && V == 2) {
+        // Coherence (cap-tree form): where no triangle's box meets a box of
+        // points, the surface does not cross that box (convex, hence
+        // connected), so all its points have the winding number of any one of
+        // them.  Only the leaf triangles of the tile's list can meet the
+        // tile's box (a cap lies in its node's box, which misses it), so the
+        // box tests run over the leaf ranges alone; then one representative
+        // (the tile's first usable point) when no triangle box meets the
+        // tile's box, else one per group of 16 points that no triangle box
+        // meets.  The representatives' sums stream the whole list through the
+        // warp's buffer with the entries split over the lanes (rep_stream).
+        const int nl = s_rtot[wid][2], ltot = s_rtot[wid][3];
+        bool tile_hit = false;
+        uint32_t touched = 0;
+        if (nl < 0)  // leaf ranges overflowed: every entry of the list (caps never hit)
+          touched = touched_leaves<NG>(a, s_rng[wid], rtotal, s_wbox[wid], s_gbox[wid], need, lane, &tile_hit);
+        else if (ltot > 0)
+          touched = touched_leaves<NG>(a, s_lrng[wid], ltot, s_wbox[wid], s_gbox[wid], need, lane, &tile_hit);
+        uint32_t untouched = need & ~touched;
+        // an odd number of touched groups leaves half a slot of lanes free:
+        // one untouched group is evaluated there instead of by its
+        // representative
+        if (tile_hit && (__popc(need & ~untouched) & 1) && untouched) untouched &= untouched - 1u;
+        int nrep = 0;
+        if (untouched) {
+          // representatives in shared memory: the tile's first usable point,
+          // or each untouched group's
+          uint32_t ub[P];
+#pragma unroll
+          for (int q = 0; q < P; ++q) ub[q] = __ballot_sync(0xffffffffu, (usable >> q) & 1u);
+          if (lane == 0) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+              const uint32_t gl = (ub[g >> 1] >> (16 * (g & 1))) & 0xffffu;
+              const bool take = tile_hit ? ((untouched >> g) & 1u) != 0u : (nrep == 0 && gl != 0u);
+              if (take) {
+                const float4 gp = a.spts[base + 32 * (g >> 1) + 16 * (g & 1) + __ffs(gl) - 1];
+                s_rep[wid][nrep][0] = gp.x;
+                s_rep[wid][nrep][1] = gp.y;
+                s_rep[wid][nrep][2] = gp.z;
+                ++nrep;
+              }
+            }
+          }
+          nrep = __shfl_sync(0xffffffffu, nrep, 0);
+          __syncwarp();
+          uint32_t rep_cert = 0;
+          int rk[NG];
+#pragma unroll
+          for (int g = 0; g < NG; ++g) rk[g] = 0;
+          for (int r0 = 0; r0 < nrep && rep_ok; r0 += 2) {
+            uint32_t c2 = 0;
+            int k2[2] = {0, 0};
+            rep_ok = rep_stream<2>(a, s_rng[wid], rtotal, wbuf, bar, ph0, ph1, lane, s_rep[wid] + r0,
+                                   min(2, nrep - r0), &c2, k2);
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+              if (g == r0 && (c2 & 1u)) rk[g] = k2[0];
+              if (g == r0 + 1 && (c2 & 2u)) rk[g] = k2[1];
+            }
+            rep_cert |= c2 << r0;
+          }
+          if (!tile_hit) {
+            if (rep_cert & 1u) {
+              coh = need;
+#pragma unroll
+              for (int g = 0; g < NG; ++g) kg[g] = rk[0];
+            }
+          } else {
+            // representative r stands for the r-th group of `untouched`
+            int r = 0;
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+              if ((untouched >> g) & 1u) {
+                int kr = 0;
+#pragma unroll
+                for (int q = 0; q < NG; ++q)
+                  if (q == r) kr = rk[q];
+                if ((rep_cert >> r) & 1u) {
+                  coh |= 1u << g;
+                  kg[g] = kr;
+                }
+                ++r;
+              }
+          }
+          __syncwarp();
+        }
+        const unsigned long long reps = (unsigned long long)nrep * surf;
+        if (coh) {
+          const DevComp c = *cp;
+          int assigned = 0;
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            const int g = 2 * q + half;
+            const bool mine = ((coh >> g) & 1u) && ((usable >> q) & 1u);
+            if (mine) {
+              const int i = base + q * 32 + lane;
+              const float4 p = a.spts[i];
+              if (classify_coherent(a, c, i, p.x, p.y, p.z, half ? kg[2 * q + 1] : kg[2 * q]))
+                done |= 1u << q;
+            }
+            assigned += __popc(__ballot_sync(0xffffffffu, mine));
+          }
+          if (lane == 0)
+            atomicAdd((unsigned long long *)(a.counters + CNT_COHERENT), (unsigned long long)assigned);
+        }
+        if (lane == 0 && reps) {
+          atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), reps);
+          atomicAdd((unsigned long long *)(a.counters + CNT_REP_PAIRS), reps);
+        }
+      } else if (a.coherence) {
+        // Coherence (strip forms): where no triangle's box meets a box of
+        // points, the surface does not cross that box (convex, hence
+        // connected), so all its points have the winding number of any one of
+        // them.  First the whole tile (representative: its first usable
+        // point), then, if some triangle box meets the tile, each group of 16
+        // points.  The tile's first usable point (positions are re-read from
+        // memory, not held in registers across the hot loop):
         int first = -1;
 #pragma unroll
         for (int q = P - 1; q >= 0; --q) {
@@ -1302,13 +1484,8 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         const float rx = rp.x, ry = rp.y, rz = rp.z;
         int k_t = 0, t_hit = -1, scanned = 0;
         unsigned long long reps = 0;
-        bool cert;
-        if constexpr (V == 2) {
-          cert = rep_pass_caps(a, s_rng[wid], rtotal, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit, &scanned);
-        } else {
-          cert = rep_pass(a, cp, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit);
-          scanned = t_hit;
-        }
+        const bool cert = rep_pass(a, cp, s_wbox[wid], rx, ry, rz, lane, &k_t, &t_hit);
+        scanned = t_hit;
         if (cert) {
           coh = need;
 #pragma unroll
@@ -1318,11 +1495,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
           reps += surf;  // completed, but the representative is uncertain
         } else {
           reps += scanned;
-          uint32_t touched;
-          if constexpr (V == 2)
-            touched = touched_groups_caps<NG>(a, s_rng[wid], rtotal, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
-          else
-            touched = touched_groups<NG>(a, cp, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
+          const uint32_t touched = touched_groups<NG>(a, cp, s_wbox[wid], s_gbox[wid], need, t_hit, lane);
           uint32_t untouched = need & ~touched;
           // an odd number of touched groups leaves half a slot of lanes free:
           // one untouched group is evaluated there instead of by its
@@ -1346,11 +1519,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
             }
             __syncwarp();
             int kk[NG];
-            uint32_t gcert;
-            if constexpr (V == 2)
-              gcert = group_reps_caps<NG>(a, s_rng[wid], rtotal, untouched, s_rep[wid], lane, kk);
-            else
-              gcert = group_reps<NG>(a, cp, untouched, s_rep[wid], lane, kk);
+            const uint32_t gcert = group_reps<NG>(a, cp, untouched, s_rep[wid], lane, kk);
             __syncwarp();
 #pragma unroll
             for (int g = 0; g < NG; ++g)
@@ -1381,6 +1550,10 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
           atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), reps);
           atomicAdd((unsigned long long *)(a.counters + CNT_REP_PAIRS), reps);
         }
+      }
+      if (!rep_ok) {
+        timed_out = true;
+        break;
       }
       const uint32_t act = need & ~coh;
       if (!act) continue;

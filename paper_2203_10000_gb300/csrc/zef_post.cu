@@ -16,6 +16,13 @@
 // L(x)_i = sum_j (x_j - x_i) / (deg_i + 1) over the edge neighbours j of i
 // (node i itself belongs to its neighbourhood and adds nothing to the sum).
 //
+// Smoothing of the tissue boundaries (surface variant of Sec. 2.2.1): the
+// tets' faces go into an open-addressing table keyed by their sorted node
+// triple (128-bit compare-and-swap) with the smallest and largest element
+// label of the tets that share them; a face whose two labels differ is a
+// boundary face, and its three edges build the adjacency of the same
+// iteration, so that only the boundary nodes move.
+//
 // Inflation: the nodes are labeled (inside bits of every compartment); every
 // node inside compartment c with an outside neighbour is listed, and one warp
 // per listed node intersects each of its crossing edges with c's triangles
@@ -44,7 +51,7 @@ namespace {
 constexpr unsigned long long kNoKey = ~0ull;
 __constant__ int kEdgeLocal[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 // words of the post-processing statistics (device)
-enum PpWord { PP_EDGES = 0, PP_BAD, PP_ITER, PP_STOP, PP_LISTED, PP_WORDS };
+enum PpWord { PP_EDGES = 0, PP_BAD, PP_ITER, PP_STOP, PP_LISTED, PP_FACES, PP_FULL, PP_WORDS };
 
 __device__ __forceinline__ unsigned long long pp_mix(unsigned long long x) {
   x ^= x >> 33;
@@ -98,6 +105,112 @@ __global__ void __launch_bounds__(256) k_pp_edges(Adj g, const int32_t *tets, in
         h = (h + 1) & g.mask;
       }
     }
+  }
+}
+
+// one undirected edge into the table (first insertion counts it at both ends)
+__device__ __forceinline__ void insert_edge(const Adj &g, uint32_t a, uint32_t b) {
+  if (a == b) return;
+  const unsigned long long key = ((unsigned long long)min(a, b) << 32) | max(a, b);
+  unsigned long long h = pp_mix(key) & g.mask;
+  for (unsigned long long it = 0; it <= g.mask; ++it) {
+    const unsigned long long prev = atomicCAS(g.keys + h, kNoKey, key);
+    if (prev == kNoKey) {
+      atomicAdd(g.deg + min(a, b), 1u);
+      atomicAdd(g.deg + max(a, b), 1u);
+      return;
+    }
+    if (prev == key) return;
+    h = (h + 1) & g.mask;
+  }
+  atomicExch((unsigned long long *)(g.words + PP_FULL), 1ull);  // cannot happen at load <= 1/2
+}
+
+// ---- tissue-boundary faces
+struct FaceTab {
+  unsigned long long *keys;  // [2 * (mask + 1)]: (a | b << 32, c) of the sorted triple, all ones when empty
+  int32_t *lo, *hi;          // smallest / largest element label of the tets sharing the face
+  unsigned long long mask;
+};
+
+// 128-bit compare-and-swap (sm_90 and later): returns the previous value
+__device__ __forceinline__ void cas128(unsigned long long *p, unsigned long long clo, unsigned long long chi,
+                                       unsigned long long vlo, unsigned long long vhi, unsigned long long &olo,
+                                       unsigned long long &ohi) {
+  asm volatile(
+      "{\n\t.reg .b128 d, c, v;\n\tmov.b128 c, {%2, %3};\n\tmov.b128 v, {%4, %5};\n\t"
+      "atom.global.cas.b128 d, [%6], c, v;\n\tmov.b128 {%0, %1}, d;\n\t}"
+      : "=l"(olo), "=l"(ohi)
+      : "l"(clo), "l"(chi), "l"(vlo), "l"(vhi), "l"(p)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(256) k_sf_clear(FaceTab f) {
+  for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s <= f.mask;
+       s += (unsigned long long)gridDim.x * blockDim.x) {
+    f.keys[2 * s] = kNoKey;
+    f.keys[2 * s + 1] = kNoKey;
+    f.lo[s] = INT32_MAX;
+    f.hi[s] = INT32_MIN;
+  }
+}
+
+// every tet's four faces into the table with the tet's element label
+__global__ void __launch_bounds__(256) k_sf_faces(FaceTab f, const int32_t *tets, const int32_t *labels, int64_t m,
+                                                 int64_t n, int64_t *words, uint32_t *status) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[4];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = tets[4 * t + k];
+      bad |= v[k] < 0 || v[k] >= n;
+    }
+    if (bad) {
+      atomicOr(status, ST_INVALID);
+      atomicExch((unsigned long long *)(words + PP_BAD), 1ull);
+      continue;
+    }
+    const int32_t lab = labels[t];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // face q leaves out vertex 3 - q
+      uint32_t a = (uint32_t)v[q == 3 ? 1 : 0], b = (uint32_t)v[q >= 2 ? 2 : 1], c = (uint32_t)v[q >= 1 ? 3 : 2];
+      uint32_t lo = min(a, min(b, c)), hi = max(a, max(b, c));
+      const uint32_t mid = a ^ b ^ c ^ lo ^ hi;
+      a = lo;
+      b = mid;
+      c = hi;
+      const unsigned long long klo = (unsigned long long)a | ((unsigned long long)b << 32), khi = c;
+      unsigned long long h = pp_mix(klo ^ pp_mix(khi)) & f.mask;
+      bool placed = false;
+      for (unsigned long long it = 0; it <= f.mask; ++it) {
+        unsigned long long olo, ohi;
+        cas128(f.keys + 2 * h, kNoKey, kNoKey, klo, khi, olo, ohi);
+        if ((olo == kNoKey && ohi == kNoKey) || (olo == klo && ohi == khi)) {
+          atomicMin(f.lo + h, lab);
+          atomicMax(f.hi + h, lab);
+          placed = true;
+          break;
+        }
+        h = (h + 1) & f.mask;
+      }
+      if (!placed) atomicExch((unsigned long long *)(words + PP_FULL), 1ull);
+    }
+  }
+}
+
+// the boundary faces (two tets, different labels) and their edges
+__global__ void __launch_bounds__(256) k_sf_edges(FaceTab f, Adj g) {
+  for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s <= f.mask;
+       s += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long klo = f.keys[2 * s];
+    if (klo == kNoKey || f.lo[s] == f.hi[s]) continue;
+    const uint32_t a = (uint32_t)(klo & 0xffffffffu), b = (uint32_t)(klo >> 32), c = (uint32_t)f.keys[2 * s + 1];
+    atomicAdd((unsigned long long *)(g.words + PP_FACES), 1ull);
+    insert_edge(g, a, b);
+    insert_edge(g, a, c);
+    insert_edge(g, b, c);
   }
 }
 
@@ -216,12 +329,14 @@ __global__ void k_sm_next(Smooth s, cudaGraphConditionalHandle handle) {
   cudaGraphSetConditional(handle, (!small && it < s.max_iters && !s.g.words[PP_BAD]) ? 1u : 0u);
 }
 
-// ||x||_2 of the starting positions: block sums in a fixed order, then one thread
-__global__ void __launch_bounds__(256) k_sm_norm(const float *x, int64_t n, double *partial) {
+// ||x||_2 of the starting positions (with `off`, the CSR row offsets, only of
+// the nodes that have a neighbour): block sums in a fixed order, then one
+// thread
+__global__ void __launch_bounds__(256) k_sm_norm(const float *x, int64_t n, const uint32_t *off, double *partial) {
   __shared__ double red[256];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x)
-    acc += (double)x[i] * x[i];
+    if (!off || off[i / 3 + 1] > off[i / 3]) acc += (double)x[i] * x[i];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -436,40 +551,22 @@ zef_status build_adjacency(zef_ctx *ctx, const int32_t *tets, int64_t m, int64_t
 
 }  // namespace
 
-zef_status taubin_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m, const uint8_t *fixed,
-                      const zef_smooth_opts &o, int32_t *iters_out) {
-  NvtxRange nvtx_("zef.taubin_smooth");
-  const bool dn = on_dev(nodes, ctx->device);
-  const bool dt = m == 0 ? dn : on_dev(tets, ctx->device);
-  const bool df = fixed ? on_dev(fixed, ctx->device) : dn;
-  if (!(dn == dt && dt == df)) return fail(ctx, ZEF_ERR_INVALID_ARG, "nodes, tets and fixed must all be host or all device");
-  zef_status st;
-  float *x = nodes;
-  const int32_t *tt = tets;
-  const uint8_t *fx = fixed;
+namespace {
+
+// The Taubin iteration loop over the adjacency g (one graph with a
+// conditional while-node), on device positions x; with `boundary_norm` the
+// starting norm runs over the nodes that have a neighbour.  Writes the
+// iterations run; the caller synchronizes and copies back.
+zef_status smooth_loop(zef_ctx *ctx, float *x, int64_t n, const Adj &g, const uint8_t *fx, const zef_smooth_opts &o,
+                       bool boundary_norm, int64_t *words) {
   cudaStream_t s = ctx->stream;
-  if (!dn) {  // stage host arrays (buffers 6: nodes, 7: tets, 8: fixed)
-    if ((st = pp_grow(ctx, 6, (size_t)n * 3 * sizeof(float)))) return st;
-    if ((st = pp_grow(ctx, 7, (size_t)std::max<int64_t>(m, 1) * 4 * sizeof(int32_t)))) return st;
-    x = (float *)ctx->pp_buf[6];
-    tt = (const int32_t *)ctx->pp_buf[7];
-    CK(cudaMemcpyAsync(x, nodes, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s), "copy nodes");
-    if (m > 0) CK(cudaMemcpyAsync((void *)tt, tets, (size_t)m * 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy tets");
-    if (fixed) {
-      if ((st = pp_grow(ctx, 8, (size_t)n))) return st;
-      fx = (const uint8_t *)ctx->pp_buf[8];
-      CK(cudaMemcpyAsync((void *)fx, fixed, (size_t)n, cudaMemcpyHostToDevice, s), "copy fixed");
-    }
-  }
-  Adj g;
-  int64_t edges = 0;
-  if ((st = build_adjacency(ctx, tt, m, n, &g, &edges))) return st;  // synchronizes
+  zef_status st;
   const int threads = 256;
   const int nblocks = grid_blocks(ctx, 3 * n, threads);
   if ((st = pp_grow(ctx, 9, (size_t)n * 3 * sizeof(float)))) return st;
   if ((st = pp_grow(ctx, 10, (size_t)(nblocks + 1) * sizeof(double)))) return st;
   double *partial = (double *)ctx->pp_buf[10];
-  k_sm_norm<<<nblocks, threads, 0, s>>>(x, n, partial);
+  k_sm_norm<<<nblocks, threads, 0, s>>>(x, n, boundary_norm ? g.deg : nullptr, partial);
   k_sm_norm_final<<<1, 32, 0, s>>>(partial, nblocks, partial + nblocks);
   Smooth sm;
   sm.g = g;
@@ -515,13 +612,147 @@ zef_status taubin_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets
   cudaGraphDestroy(graph);
   if (ce != cudaSuccess) return cuda_fail(ctx, ce, "smoothing graph");
   ce = cudaGraphLaunch(exec, s);
-  int64_t words[PP_WORDS] = {0};
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(words, g.words, sizeof(words), cudaMemcpyDeviceToHost, s);
-  if (ce == cudaSuccess && !dn) ce = cudaMemcpyAsync(nodes, x, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(words, g.words, PP_WORDS * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   cudaGraphExecDestroy(exec);
   if (ce != cudaSuccess) return cuda_fail(ctx, ce, "smoothing");
+  return ZEF_OK;
+}
+
+// CSR adjacency of the tissue-boundary faces' edges (buffers 0-5 as
+// build_adjacency, 14-16 for the face table); synchronizes.
+zef_status build_surface_adjacency(zef_ctx *ctx, const int32_t *tets, const int32_t *labels, int64_t m, int64_t n,
+                                   Adj *out, int64_t *faces) {
+  int64_t fcap = 1024;
+  while (fcap < 8 * std::max<int64_t>(m, 1)) fcap <<= 1;  // 4 m face slots, load <= 1/2
+  int64_t cap = 1024;
+  while (cap < 12 * std::max<int64_t>(m, 1)) cap <<= 1;   // boundary edges: far fewer than the tets' 6 m
+  zef_status st;
+  if ((st = pp_grow(ctx, 14, (size_t)fcap * 2 * sizeof(unsigned long long)))) return st;
+  if ((st = pp_grow(ctx, 15, (size_t)fcap * sizeof(int32_t)))) return st;
+  if ((st = pp_grow(ctx, 16, (size_t)fcap * sizeof(int32_t)))) return st;
+  if ((st = pp_grow(ctx, 0, (size_t)cap * sizeof(unsigned long long)))) return st;
+  if ((st = pp_grow(ctx, 1, (size_t)(n + 1) * sizeof(uint32_t)))) return st;
+  if ((st = pp_grow(ctx, 2, (size_t)std::max<int64_t>(n, 1) * sizeof(uint32_t)))) return st;
+  if ((st = pp_grow(ctx, 4, (size_t)PP_WORDS * sizeof(int64_t)))) return st;
+  if ((st = pp_grow(ctx, 5, (size_t)((n + 1) / 2048 + 2) * sizeof(uint32_t)))) return st;
+  FaceTab f;
+  f.keys = (unsigned long long *)ctx->pp_buf[14];
+  f.lo = (int32_t *)ctx->pp_buf[15];
+  f.hi = (int32_t *)ctx->pp_buf[16];
+  f.mask = (unsigned long long)(fcap - 1);
+  Adj g;
+  g.keys = (unsigned long long *)ctx->pp_buf[0];
+  g.mask = (unsigned long long)(cap - 1);
+  g.deg = (uint32_t *)ctx->pp_buf[1];
+  g.fill = (uint32_t *)ctx->pp_buf[2];
+  g.n = n;
+  g.words = (int64_t *)ctx->pp_buf[4];
+  cudaStream_t s = ctx->stream;
+  k_sf_clear<<<grid_blocks(ctx, fcap, 256), 256, 0, s>>>(f);
+  CK(cudaMemsetAsync(g.keys, 0xff, (size_t)cap * sizeof(unsigned long long), s), "clear edge table");
+  CK(cudaMemsetAsync(g.deg, 0, (size_t)(n + 1) * sizeof(uint32_t), s), "clear degrees");
+  CK(cudaMemsetAsync(g.fill, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(uint32_t), s), "clear cursors");
+  k_pp_words<<<1, 32, 0, s>>>(g.words);
+  if (m > 0) {
+    k_sf_faces<<<grid_blocks(ctx, m, 256), 256, 0, s>>>(f, tets, labels, m, n, g.words, ctx->d_status);
+    k_sf_edges<<<grid_blocks(ctx, fcap, 256), 256, 0, s>>>(f, g);
+  }
+  st = scan_exclusive(ctx, g.deg, nullptr, 1, n + 1, nullptr, (uint32_t *)ctx->pp_buf[5]);
+  if (st) return st;
+  int64_t words[PP_WORDS];
+  uint32_t deg_sum = 0;
+  CK(cudaMemcpyAsync(words, g.words, sizeof(words), cudaMemcpyDeviceToHost, s), "read adjacency status");
+  CK(cudaMemcpyAsync(&deg_sum, g.deg + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read edge count");
+  CK(cudaStreamSynchronize(s), "build boundary adjacency");
+  if (words[PP_BAD]) {
+    zef_synchronize(ctx);  // clears the recorded status
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "a tet references a node index outside [0, num_nodes)");
+  }
+  if (words[PP_FULL]) return fail(ctx, ZEF_ERR_CUDA, "internal: face or edge table full");
+  *faces = words[PP_FACES];
+  if ((st = pp_grow(ctx, 3, (size_t)std::max<int64_t>((int64_t)deg_sum, 1) * sizeof(int32_t)))) return st;
+  g.nbr = (int32_t *)ctx->pp_buf[3];
+  k_pp_scatter<<<grid_blocks(ctx, cap, 256), 256, 0, s>>>(g);
+  k_pp_sort_rows<<<grid_blocks(ctx, n, 256), 256, 0, s>>>(g);
+  CK(cudaGetLastError(), "boundary adjacency kernels");
+  *out = g;
+  return ZEF_OK;
+}
+
+}  // namespace
+
+zef_status taubin_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m, const uint8_t *fixed,
+                      const zef_smooth_opts &o, int32_t *iters_out) {
+  NvtxRange nvtx_("zef.taubin_smooth");
+  const bool dn = on_dev(nodes, ctx->device);
+  const bool dt = m == 0 ? dn : on_dev(tets, ctx->device);
+  const bool df = fixed ? on_dev(fixed, ctx->device) : dn;
+  if (!(dn == dt && dt == df)) return fail(ctx, ZEF_ERR_INVALID_ARG, "nodes, tets and fixed must all be host or all device");
+  zef_status st;
+  float *x = nodes;
+  const int32_t *tt = tets;
+  const uint8_t *fx = fixed;
+  cudaStream_t s = ctx->stream;
+  if (!dn) {  // stage host arrays (buffers 6: nodes, 7: tets, 8: fixed)
+    if ((st = pp_grow(ctx, 6, (size_t)n * 3 * sizeof(float)))) return st;
+    if ((st = pp_grow(ctx, 7, (size_t)std::max<int64_t>(m, 1) * 4 * sizeof(int32_t)))) return st;
+    x = (float *)ctx->pp_buf[6];
+    tt = (const int32_t *)ctx->pp_buf[7];
+    CK(cudaMemcpyAsync(x, nodes, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s), "copy nodes");
+    if (m > 0) CK(cudaMemcpyAsync((void *)tt, tets, (size_t)m * 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy tets");
+    if (fixed) {
+      if ((st = pp_grow(ctx, 8, (size_t)n))) return st;
+      fx = (const uint8_t *)ctx->pp_buf[8];
+      CK(cudaMemcpyAsync((void *)fx, fixed, (size_t)n, cudaMemcpyHostToDevice, s), "copy fixed");
+    }
+  }
+  Adj g;
+  int64_t edges = 0;
+  if ((st = build_adjacency(ctx, tt, m, n, &g, &edges))) return st;  // synchronizes
+  int64_t words[PP_WORDS] = {0};
+  if ((st = smooth_loop(ctx, x, n, g, fx, o, false, words))) return st;
+  if (!dn) CK(cudaMemcpy(nodes, x, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost), "copy nodes back");
   if (iters_out) *iters_out = (int32_t)words[PP_ITER];
+  return zef_synchronize(ctx);
+}
+
+zef_status taubin_surface_run(zef_ctx *ctx, float *nodes, int64_t n, const int32_t *tets, int64_t m,
+                              const int32_t *elem_labels, const zef_smooth_opts &o, int32_t *iters_out,
+                              int64_t *faces_out) {
+  NvtxRange nvtx_("zef.taubin_smooth_surface");
+  const bool dn = on_dev(nodes, ctx->device);
+  const bool dt = m == 0 ? dn : on_dev(tets, ctx->device);
+  const bool dl = m == 0 ? dn : on_dev(elem_labels, ctx->device);
+  if (!(dn == dt && dt == dl))
+    return fail(ctx, ZEF_ERR_INVALID_ARG, "nodes, tets and elem_labels must all be host or all device");
+  zef_status st;
+  float *x = nodes;
+  const int32_t *tt = tets;
+  const int32_t *lab = elem_labels;
+  cudaStream_t s = ctx->stream;
+  if (!dn) {  // stage host arrays (buffers 6: nodes, 7: tets, 17: labels)
+    if ((st = pp_grow(ctx, 6, (size_t)n * 3 * sizeof(float)))) return st;
+    if ((st = pp_grow(ctx, 7, (size_t)std::max<int64_t>(m, 1) * 4 * sizeof(int32_t)))) return st;
+    if ((st = pp_grow(ctx, 17, (size_t)std::max<int64_t>(m, 1) * sizeof(int32_t)))) return st;
+    x = (float *)ctx->pp_buf[6];
+    tt = (const int32_t *)ctx->pp_buf[7];
+    lab = (const int32_t *)ctx->pp_buf[17];
+    CK(cudaMemcpyAsync(x, nodes, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s), "copy nodes");
+    if (m > 0) {
+      CK(cudaMemcpyAsync((void *)tt, tets, (size_t)m * 4 * sizeof(int32_t), cudaMemcpyHostToDevice, s), "copy tets");
+      CK(cudaMemcpyAsync((void *)lab, elem_labels, (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice, s),
+         "copy labels");
+    }
+  }
+  Adj g;
+  int64_t faces = 0;
+  if ((st = build_surface_adjacency(ctx, tt, lab, m, n, &g, &faces))) return st;  // synchronizes
+  int64_t words[PP_WORDS] = {0};
+  if (faces > 0 && (st = smooth_loop(ctx, x, n, g, nullptr, o, true, words))) return st;
+  if (!dn) CK(cudaMemcpy(nodes, x, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost), "copy nodes back");
+  if (iters_out) *iters_out = (int32_t)words[PP_ITER];
+  if (faces_out) *faces_out = faces;
   return zef_synchronize(ctx);
 }
 

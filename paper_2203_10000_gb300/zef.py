@@ -121,6 +121,9 @@ _lib.zef_taubin_smooth.argtypes = [_P, _P, _I64, _P, _I64, _P, ctypes.POINTER(Sm
 _lib.zef_taubin_smooth.restype = ctypes.c_int
 _lib.zef_inflate.argtypes = [_P, _P, _I64, _P, _I64, _I32, ctypes.c_float, ctypes.POINTER(_I64)]
 _lib.zef_inflate.restype = ctypes.c_int
+_lib.zef_taubin_smooth_surface.argtypes = [_P, _P, _I64, _P, _I64, _P, ctypes.POINTER(SmoothOpts),
+                                           ctypes.POINTER(_I32), ctypes.POINTER(_I64)]
+_lib.zef_taubin_smooth_surface.restype = ctypes.c_int
 
 
 class RelabelPass(ctypes.Structure):
@@ -416,6 +419,23 @@ class Context:
         it = _I32(0)
         self._check(_lib.zef_taubin_smooth(self._h, xp, n, tp, m, fp, ctypes.byref(o), ctypes.byref(it)))
         return int(it.value)
+
+    def taubin_smooth_surface(self, nodes, tets, elem_labels, lam: float = 0.4, mu: float = 0.4,
+                              xi: float = 0.1, max_iters: int = 100):
+        """Taubin smoothing of the tissue boundaries (faces between tets of
+        different element labels) of `nodes` in place; returns (iterations,
+        boundary faces)."""
+        xp = self._inplace_f32(nodes)
+        tp, tk, _ = _contig(tets, np.int32, "int32")
+        lp, lk, _ = _contig(elem_labels, np.int32, "int32")
+        n = int(np.prod(nodes.shape)) // 3
+        m = int(np.prod(tk.shape)) // 4
+        o = SmoothOpts(lam, mu, xi, int(max_iters))
+        it = _I32(0)
+        nf = _I64(0)
+        self._check(_lib.zef_taubin_smooth_surface(self._h, xp, n, tp, m, lp, ctypes.byref(o), ctypes.byref(it),
+                                                   ctypes.byref(nf)))
+        return int(it.value), int(nf.value)
 
     def inflate(self, nodes, tets, compartment_id: int, zeta: float = 0.05) -> int:
         """One inflation of `nodes` in place towards the compartment's surface;

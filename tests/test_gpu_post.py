@@ -1,5 +1,6 @@
 """GPU post-processing (Sec. 2.2) against the FP64 oracle through the C ABI:
-Taubin smoothing (zef_taubin_smooth) and inflation (zef_inflate).
+Taubin smoothing of the volume (zef_taubin_smooth) and of the tissue
+boundaries (zef_taubin_smooth_surface), and inflation (zef_inflate).
 
 Tolerances: positions are float32; the smoothing sums every node's
 neighbours in float32 (a few dozen terms of lattice-sized differences, error
@@ -98,6 +99,73 @@ def test_taubin_head_mesh(zef):
     want, oit = pp.taubin_smooth(x, w.tets, 0.4, 0.4, 0.0, 5)
     assert it == oit == 5
     assert np.abs(xt.cpu().numpy() - want).max() <= smooth_tol(5, x)
+
+
+# ------------------------------------------------------------------ tissue-boundary smoothing
+def _block_case(n, lo, hi, seed, amp):
+    """Lattice of n^3 cells with element label 2 on the cells inside
+    [lo, hi), 1 elsewhere, nodes jittered (the outer boundary kept)."""
+    nodes, tets = zs.lattice_5tet(n, 1.0, (0.0, 0.0, 0.0))
+    cell = np.floor(nodes[tets].astype(np.float64).mean(axis=1))
+    lab = np.where(np.all((cell >= lo) & (cell < hi), axis=1), 2, 1).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    x = (nodes + rng.uniform(-amp, amp, nodes.shape)).astype(np.float32)
+    return x, tets, lab
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_taubin_surface_matches_oracle(zef, where):
+    """A labeled block inside a jittered lattice: boundary faces, iterations
+    and positions against the oracle; nodes off the boundary keep their bits."""
+    from oracle import postprocess as pp
+    x, tets, lab = _block_case(10, np.array([2, 3, 2]), np.array([8, 7, 6]), 9, 0.25)
+    ctx = zef.Context(0)
+    if where == "device":
+        xt = torch.from_numpy(x.copy()).cuda()
+        it, nf = ctx.taubin_smooth_surface(xt, torch.from_numpy(tets).cuda(), torch.from_numpy(lab).cuda(),
+                                           0.4, 0.4, 0.0, 8)
+        out = xt.cpu().numpy()
+    else:
+        out = x.copy()
+        it, nf = ctx.taubin_smooth_surface(out, tets, lab, 0.4, 0.4, 0.0, 8)
+    want, oit, onf = pp.taubin_smooth_surface(x, tets, lab, 0.4, 0.4, 0.0, 8)
+    assert it == oit == 8
+    assert nf == onf == 4 * (6 * 4 + 4 * 4 + 4 * 6)
+    assert np.abs(out - want).max() <= smooth_tol(8, x)
+    on = np.zeros(len(x), bool)
+    on[pp.boundary_faces(tets, lab).ravel()] = True
+    assert np.array_equal(out[~on], x[~on])
+    assert np.abs(out[on] - x[on]).max() > 1e-3
+
+
+def test_taubin_surface_head_mesh_and_stop_rule(zef, oracle_mod):
+    """Element labels of the 4 mm head lattice (four-nodes rule, through the
+    library) define the tissue boundaries; smoothing with the paper's
+    xi = 0.1 stops where the oracle does; a labeling without boundaries
+    moves nothing."""
+    from oracle import postprocess as pp
+    w = zs.config3()
+    ctx = zef.Context(0)
+    for s_ in w.surfaces:
+        ctx.add_compartment(s_.id, s_.verts, s_.tris)
+    ctx.set_priority(w.priority)
+    elem, _, _ = ctx.label_elements(torch.from_numpy(w.nodes).cuda(), torch.from_numpy(w.tets).cuda())
+    lab = elem.cpu().numpy()
+    olab, _ = oracle_mod.label_elements(w.nodes, w.tets, w.surfaces, w.priority)
+    assert np.array_equal(lab, olab)
+    rng = np.random.default_rng(12)
+    x = (w.nodes + rng.uniform(-1.0, 1.0, w.nodes.shape)).astype(np.float32)
+    for xi, cap in ((0.0, 4), (0.1, 100)):
+        xt = torch.from_numpy(x.copy()).cuda()
+        it, nf = ctx.taubin_smooth_surface(xt, torch.from_numpy(w.tets).cuda(), torch.from_numpy(lab).cuda(),
+                                           0.4, 0.4, xi, cap)
+        want, oit, onf = pp.taubin_smooth_surface(x, w.tets, lab, 0.4, 0.4, xi, cap)
+        assert it == oit and nf == onf > 1000
+        assert np.abs(xt.cpu().numpy() - want).max() <= smooth_tol(it, x)
+    same = np.zeros(len(w.tets), np.int32)
+    y = x.copy()
+    assert ctx.taubin_smooth_surface(y, w.tets, same) == (0, 0)
+    assert np.array_equal(y, x)
 
 
 def _inflate_case(zef, surface, nodes, tets, zeta=0.05, where="device"):
