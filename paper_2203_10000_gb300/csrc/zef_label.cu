@@ -2246,7 +2246,8 @@ __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, Un
 }
 
 // Points in key order, multiplied by the context's power-of-two scale
-// (exact), with their permutation and cleared inside / uncertain masks.  A
+// (exact), with their permutation (the inside / uncertain masks of the points
+// inside the union box are cleared by the tile pass, in sorted order).  A
 // non-finite input point becomes NaN; a finite one that the scale would push
 // past the float range is clamped (it lies outside every surface's box).
 __device__ __forceinline__ float scaled_coord(float x, float s) {
@@ -2254,9 +2255,8 @@ __device__ __forceinline__ float scaled_coord(float x, float s) {
 }
 
 __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt, const uint32_t *keys,
-                                                uint32_t *cursor, float4 *spts, int32_t *perm,
-                                                unsigned long long *in_mask, unsigned long long *unc_mask,
-                                                float scale, uint32_t *status) {
+                                                uint32_t *cursor, float4 *spts, int32_t *perm, float scale,
+                                                uint32_t *status) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
   const int lane = threadIdx.x & 31;
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n;
@@ -2277,17 +2277,19 @@ __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt,
     if (!ZEF_BOUNDS_OK((int64_t)pos < n, status, 17)) continue;
     spts[pos] = q;
     perm[pos] = (int32_t)i;
-    in_mask[pos] = 0ull;
-    unc_mask[pos] = 0ull;
   }
 }
 
 // Box of the points [b, e) of the sorted array, reduced over the warp (every
-// lane returns it); empty: (+inf, -inf).
-__device__ __forceinline__ void warp_box(const float4 *spts, int64_t b, int64_t e, int lane, float *lo, float *hi) {
+// lane returns it); empty: (+inf, -inf).  Also clears the points' inside and
+// uncertain masks (coalesced, in sorted order).
+__device__ __forceinline__ void warp_box(const float4 *spts, int64_t b, int64_t e, int lane, float *lo, float *hi,
+                                         unsigned long long *in_mask, unsigned long long *unc_mask) {
   lo[0] = lo[1] = lo[2] = INFINITY;
   hi[0] = hi[1] = hi[2] = -INFINITY;
   for (int64_t i = b + lane; i < e; i += 32) {
+    in_mask[i] = 0ull;
+    unc_mask[i] = 0ull;
     const float4 p = spts[i];
     lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
     hi[0] = fmaxf(hi[0], p.x); hi[1] = fmaxf(hi[1], p.y); hi[2] = fmaxf(hi[2], p.z);
@@ -2302,14 +2304,15 @@ __device__ __forceinline__ void warp_box(const float4 *spts, int64_t b, int64_t 
 
 // Bounding box of every tile of `tile` consecutive sorted points inside the
 // union box (the plain FP64 kernel's tiles): one warp per tile.
-__global__ void __launch_bounds__(256) k_tile_box(const float4 *spts, int64_t *cnt, float *tile_box, int tile) {
+__global__ void __launch_bounds__(256) k_tile_box(const float4 *spts, int64_t *cnt, float *tile_box, int tile,
+                                                 unsigned long long *in_mask, unsigned long long *unc_mask) {
   const int64_t nin = cnt[CNT_NIN];
   const int64_t ntiles = cnt[CNT_TILES];
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += warps) {
     float lo[3], hi[3];
-    warp_box(spts, t * tile, min(t * tile + tile, nin), lane, lo, hi);
+    warp_box(spts, t * tile, min(t * tile + tile, nin), lane, lo, hi, in_mask, unc_mask);
     if (lane < 6) tile_box[t * 6 + lane] = lane < 3 ? lo[lane] : hi[lane - 3];
   }
 }
@@ -2354,14 +2357,15 @@ __global__ void __launch_bounds__(256) k_emit(int64_t *cnt, const uint32_t *scan
 constexpr uint32_t kNoWork = 0xffffffffu;
 
 __global__ void __launch_bounds__(256) k_tile_work(const float4 *spts, int64_t *cnt, int tile, const DevComp *comps,
-                                                  int ncomp, const float *dop, uint32_t *tile_key, uint32_t *hist) {
+                                                  int ncomp, const float *dop, uint32_t *tile_key, uint32_t *hist,
+                                                  unsigned long long *in_mask, unsigned long long *unc_mask) {
   const int64_t nin = cnt[CNT_NIN];
   const int64_t ntiles = cnt[CNT_TILES];
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += warps) {
     float lo[3], hi[3];
-    warp_box(spts, t * tile, min(t * tile + tile, nin), lane, lo, hi);
+    warp_box(spts, t * tile, min(t * tile + tile, nin), lane, lo, hi, in_mask, unc_mask);
     const float b[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
     float est = 0.f;
     for (int c0 = 0; c0 < ncomp; c0 += 32) {
@@ -2406,10 +2410,12 @@ __global__ void __launch_bounds__(256) k_tile_scatter(int64_t *cnt, const uint32
 }
 
 // Labels in the caller's order: the first set bit of the priority-ordered
-// inside mask -> id (0 when none; the points outside the union box have an
-// empty mask), -1 for the non-finite points (the tail of the sorted order).
+// inside mask -> id (0 when none, and for the points outside the union box,
+// the first tail of the sorted order), -1 for the non-finite points (the
+// second tail).
 __global__ void __launch_bounds__(256) k_resolve(LabelArgs a, int32_t *labels, const int32_t *row_ids) {
   const int64_t n = a.counters[CNT_N], off = a.counters[CNT_OFF], nfin = a.counters[CNT_NFIN];
+  const int64_t nin = a.counters[CNT_NIN];
   if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[CNT_NONFINITE] = n - nfin;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t o = a.perm[i];
@@ -2421,7 +2427,7 @@ __global__ void __launch_bounds__(256) k_resolve(LabelArgs a, int32_t *labels, c
       if (a.omega)
         for (int r = 0; r < a.ncomp; ++r) a.omega[(int64_t)r * a.omega_ld + o] = __int_as_float(0x7fc00000);
     } else {
-      const unsigned long long m = a.in_mask[i];
+      const unsigned long long m = i < nin ? a.in_mask[i] : 0ull;
       lab = m ? row_ids[__ffsll((long long)m) - 1] : 0;
       if (a.masks_out) a.masks_out[off + o] = m;
     }
@@ -2839,14 +2845,13 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   ++launches;
   zef_status st = scan_keys(ctx, b.hist, tile);
   if (st) return st;
-  k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm, b.in_mask, b.unc_mask,
-                              ctx->scale, ctx->d_status);
+  k_scatter<<<g, 256, 0, s>>>(plan.pts, b.counters, b.keys, b.hist, b.spts, b.perm, ctx->scale, ctx->d_status);
   ++launches;
   const int64_t tiles_cap = (ncap + tile - 1) / tile;
   const int gt = grid_for(ctx, tiles_cap * 32, 256);  // one warp per tile
   if (plan.opts.precision == ZEF_FP64_PLAIN) {
     // (tile, compartment) items for the plain FP64 kernel
-    k_tile_box<<<gt, 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile);
+    k_tile_box<<<gt, 256, 0, s>>>(b.spts, b.counters, b.tile_box, tile, b.in_mask, b.unc_mask);
     k_flags<<<grid_for(ctx, tiles_cap * C, 256), 256, 0, s>>>(b.counters, b.tile_box, ctx->d_comps, ctx->d_lpt, C,
                                                                ctx->d_dop, b.flags);
     launches += 2;
@@ -2856,7 +2861,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
     ++launches;
   } else {
     // tile items, largest estimated work first
-    k_tile_work<<<gt, 256, 0, s>>>(b.spts, b.counters, tile, ctx->d_comps, C, ctx->d_dop, b.flags, work_hist);
+    k_tile_work<<<gt, 256, 0, s>>>(b.spts, b.counters, tile, ctx->d_comps, C, ctx->d_dop, b.flags, work_hist,
+                                   b.in_mask, b.unc_mask);
     k_scan_work<<<1, 1024, 0, s>>>(work_hist, b.counters + CNT_ITEMS);
     k_tile_scatter<<<grid_for(ctx, tiles_cap, 256), 256, 0, s>>>(b.counters, b.flags, work_hist, b.items,
                                                                  ctx->d_status);
