@@ -480,28 +480,6 @@ def run_ours(args):
                             f"(rank 0 holds {n_local} of {N} points)") if sharded else \
             "replicas: every rank labels the whole workload"
 
-    # FP32 + rescue vs the plain FP64 kernel on the same subset
-    if args.fp64_points > 0 and rank == 0:
-        nsub = min(n_local, args.fp64_points)
-        c0 = n_local // 2 - nsub // 2
-        sub = pts[c0:c0 + nsub].contiguous()
-        lab_sub = torch.empty(nsub, dtype=torch.int32, device=dev)
-        _, _, s32 = ctx.label_points(sub, labels=lab_sub, opts=opts, stats=True)
-        l32 = lab_sub.clone()
-        _, _, s64 = ctx.label_points(sub, labels=lab_sub, opts=zef.make_opts(precision=zef.ZEF_FP64_PLAIN),
-                                     stats=True)
-        same = bool(torch.equal(l32, lab_sub))
-        line["fp64_plain"] = {"points": nsub, "ms_fp32_rescue": s32["ms_total"], "ms_fp64_plain": s64["ms_total"],
-                              "speedup": s64["ms_total"] / s32["ms_total"], "labels_equal": same,
-                              "fp64_pairs_per_s": s64["pairs_evaluated"] / (s64["ms_total"] * 1e-3)}
-
-    # measured FMA throughput of this GPU (cross-check of the FP32 peak; the
-    # FP64 rate sets the cost of the re-evaluation and of the plain FP64 kernel)
-    if rank == 0:
-        f32 = ctx.fma_rate(fp64=False)
-        f64 = ctx.fma_rate(fp64=True)
-        line["fma_microbench"] = {"fp32_tflops": f32, "fp64_tflops": f64, "fp32_frac_of_peak": f32 / peak}
-
     # end to end through the C ABI with host buffers: every step copies the
     # points from pinned host memory to the device and the labels back into
     # pinned host memory (copies inside the timed region)
@@ -524,6 +502,28 @@ def run_ours(args):
                        "host_memory": "pinned", "timer": "host clock around K calls, synchronized",
                        "labels_equal_device_run": bool(np.array_equal(lab_pin.numpy(), labels.cpu().numpy()))}
         del pts_pin, lab_pin
+
+    # FP32 + rescue vs the plain FP64 kernel on the same subset
+    if args.fp64_points > 0 and rank == 0:
+        nsub = min(n_local, args.fp64_points)
+        c0 = n_local // 2 - nsub // 2
+        sub = pts[c0:c0 + nsub].contiguous()
+        lab_sub = torch.empty(nsub, dtype=torch.int32, device=dev)
+        _, _, s32 = ctx.label_points(sub, labels=lab_sub, opts=opts, stats=True)
+        l32 = lab_sub.clone()
+        _, _, s64 = ctx.label_points(sub, labels=lab_sub, opts=zef.make_opts(precision=zef.ZEF_FP64_PLAIN),
+                                     stats=True)
+        same = bool(torch.equal(l32, lab_sub))
+        line["fp64_plain"] = {"points": nsub, "ms_fp32_rescue": s32["ms_total"], "ms_fp64_plain": s64["ms_total"],
+                              "speedup": s64["ms_total"] / s32["ms_total"], "labels_equal": same,
+                              "fp64_pairs_per_s": s64["pairs_evaluated"] / (s64["ms_total"] * 1e-3)}
+
+    # measured FMA throughput of this GPU (cross-check of the FP32 peak; the
+    # FP64 rate sets the cost of the re-evaluation and of the plain FP64 kernel)
+    if rank == 0:
+        f32 = ctx.fma_rate(fp64=False)
+        f64 = ctx.fma_rate(fp64=True)
+        line["fma_microbench"] = {"fp32_tflops": f32, "fp64_tflops": f64, "fp32_frac_of_peak": f32 / peak}
 
     if sharded:
         # the labels of the one workload, gathered once after the timed region

@@ -274,6 +274,96 @@ __device__ __forceinline__ void kahan_flush(PState &s) {
   s.grp = 0.f;
 }
 
+// ------------------------------------------------------------------ two points per instruction
+// sm_100 and later execute packed f32x2 add / mul / fma: one instruction does
+// the IEEE fp32 operation (same rounding, flush to zero as the rest of this
+// file) on two values, so the strip arithmetic of a lane's two points takes
+// half the issue slots of two scalar streams.  A pair lives in one 64-bit
+// register pair; lo() and hi() are its halves.
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float lo(f2 a) { return __uint_as_float((uint32_t)a.v); }
+__device__ __forceinline__ float hi(f2 a) { return __uint_as_float((uint32_t)(a.v >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
+// The strip state of a lane's two points (PState, each field a pair).
+struct PState2 {
+  f2 px, py, pz;
+  f2 ax, ay, az, bx, by, bz;
+  f2 ra, rb, sab;
+  float bad0, bad1;
+};
+
+__device__ __forceinline__ void window_init2(PState2 &s, float4 v0) {
+  const f2 vx = pk(v0.x, v0.x), vy = pk(v0.y, v0.y), vz = pk(v0.z, v0.z);
+  s.ax = s.bx = sub2(vx, s.px);
+  s.ay = s.by = sub2(vy, s.py);
+  s.az = s.bz = sub2(vz, s.pz);
+  const f2 q = fma2(s.ax, s.ax, fma2(s.ay, s.ay, mul2(s.az, s.az)));
+  const f2 r = mul2(q, pk(rsqrtf(lo(q)), rsqrtf(hi(q))));
+  s.ra = s.rb = r;
+  s.sab = add2(q, q);
+}
+
+// geom_step for both points: the same operations in the same order
+__device__ __forceinline__ void geom_step2(PState2 &s, const float4 V, const float4 Nn, f2 &N, f2 &D) {
+  const f2 cx = sub2(pk(V.x, V.x), s.px), cy = sub2(pk(V.y, V.y), s.py), cz = sub2(pk(V.z, V.z), s.pz);
+  const f2 qc = fma2(cx, cx, fma2(cy, cy, mul2(cz, cz)));
+  const f2 rc = mul2(qc, pk(rsqrtf(lo(qc)), rsqrtf(hi(qc))));
+  const f2 dac = fma2(s.ax, cx, fma2(s.ay, cy, mul2(s.az, cz)));
+  const f2 dbc = fma2(s.bx, cx, fma2(s.by, cy, mul2(s.bz, cz)));
+  N = fma2(pk(Nn.x, Nn.x), cx, fma2(pk(Nn.y, Nn.y), cy, mul2(pk(Nn.z, Nn.z), cz)));
+  D = fma2(s.sab, rc, fma2(dac, s.rb, mul2(dbc, s.ra)));
+  s.bad0 = fminf(s.bad0, fmaf(-Nn.w, lo(rc), fmaxf(fabsf(lo(N)), lo(D))));
+  s.bad1 = fminf(s.bad1, fmaf(-Nn.w, hi(rc), fmaxf(fabsf(hi(N)), hi(D))));
+  s.sab = fma2(s.rb, rc, dbc);
+  s.ax = s.bx; s.ay = s.by; s.az = s.bz;
+  s.bx = cx; s.by = cy; s.bz = cz;
+  s.ra = s.rb;
+  s.rb = rc;
+}
+
+// cmul_wrap for both points.  The real part a_r b_r - a_i b_i takes the
+// product a_i b_i, negated (0 - x: exact; only the sign of a zero can
+// differ from the scalar form, which neither the wraps nor the atan2 read),
+// into one fused multiply-add, as the scalar form does.
+__device__ __forceinline__ void cmul_wrap2(f2 ar, f2 ai, f2 br, f2 bi, f2 &cr, f2 &ci, uint32_t &kp0, uint32_t &kn0,
+                                           uint32_t &kp1, uint32_t &kn1) {
+  cr = fma2(ar, br, sub2(pk(0.f, 0.f), mul2(ai, bi)));
+  ci = fma2(ar, bi, mul2(ai, br));
+  const uint32_t x0 = __float_as_uint(lo(ai)), y0 = __float_as_uint(lo(bi)), z0 = __float_as_uint(lo(ci));
+  const uint32_t x1 = __float_as_uint(hi(ai)), y1 = __float_as_uint(hi(bi)), z1 = __float_as_uint(hi(ci));
+  kp0 += (~x0 & ~y0 & z0) >> 31;
+  kn0 += (x0 & y0 & ~z0) >> 31;
+  kp1 += (~x1 & ~y1 & z1) >> 31;
+  kn1 += (x1 & y1 & ~z1) >> 31;
+}
+
 struct LabelArgs {
   const Entry *entries;
   const float4 *tris;
@@ -987,6 +1077,14 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
     st[q].bad = __int_as_float(0x7f800000);
     st[q].kp = st[q].kn = 0u;
   }
+  PState2 st2;  // NA == 2: both slots' points and windows as pairs
+  if constexpr (NA == 2) {
+    st2.px = pk(st[0].px, st[1].px);
+    st2.py = pk(st[0].py, st[1].py);
+    st2.pz = pk(st[0].pz, st[1].pz);
+    st2.ax = st2.ay = st2.az = st2.bx = st2.by = st2.bz = st2.ra = st2.rb = st2.sab = pk(0.f, 0.f);
+    st2.bad0 = st2.bad1 = __int_as_float(0x7f800000);
+  }
   for (int ch = 0; ch < nchunks; ++ch) {
     const int b = ch & 1;
     const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
@@ -994,6 +1092,31 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
     if (b) ph1 ^= 1; else ph0 ^= 1;
     const Entry *E = wbuf + b * kWChunk;
     const int cnt = min(kWChunk, total - ch * kWChunk);  // a multiple of four
+    if constexpr (NA == 2) {
+      // both slots at once on packed pairs; the windows are carried across
+      // chunks in st2
+      for (int g = 0; g < cnt; g += kGroup) {
+#pragma unroll 1
+        for (int j = g; j < min(cnt, g + kGroup); j += 4) {
+          const Entry *e = E + j;
+          const float4 v0 = e[0].v, n0 = e[0].n, v1 = e[1].v, n1 = e[1].n;
+          const float4 v2 = e[2].v, n2 = e[2].n, v3 = e[3].v, n3 = e[3].n;
+          if (v0.w == 2.f) window_init2(st2, v0);
+          f2 N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+          geom_step2(st2, v0, n0, N0, D0);
+          geom_step2(st2, v1, n1, N1, D1);
+          cmul_wrap2(D0, N0, D1, N1, r01, i01, st[0].kp, st[0].kn, st[1].kp, st[1].kn);
+          geom_step2(st2, v2, n2, N0, D0);
+          geom_step2(st2, v3, n3, N1, D1);
+          cmul_wrap2(D0, N0, D1, N1, r23, i23, st[0].kp, st[0].kn, st[1].kp, st[1].kn);
+          cmul_wrap2(r01, i01, r23, i23, R, I, st[0].kp, st[0].kn, st[1].kp, st[1].kn);
+          st[0].grp += half_angle(lo(I), lo(R));
+          st[1].grp += half_angle(hi(I), hi(R));
+        }
+        kahan_flush(st[0]);
+        kahan_flush(st[1]);
+      }
+    } else {
     for (int g = 0; g < cnt; g += kGroup) {
 #pragma unroll 1
       for (int j = g; j < min(cnt, g + kGroup); j += 4) {
@@ -1020,8 +1143,13 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
 #pragma unroll
       for (int q = 0; q < NA; ++q) kahan_flush(st[q]);
     }
+    }
     __syncwarp();  // every lane is done with buffer b before it is refilled
     if (lane == 0 && ch + 2 < nchunks) fill(ch + 2, b);
+  }
+  if constexpr (NA == 2) {
+    st[0].bad = st2.bad0;
+    st[1].bad = st2.bad1;
   }
   return true;
 }
