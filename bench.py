@@ -264,13 +264,16 @@ def traffic_record(cfg, st, kernel):
     if not os.path.exists(tpath):
         return None
     try:
-        rec = json.load(open(tpath)).get(f"config{cfg}")
+        recs = json.load(open(tpath)).get(f"config{cfg}") or []
+        if isinstance(recs, dict):
+            recs = [recs]
         src = os.path.join(ROOT, "paper_2203_10000_gb300", "csrc", "zef_label.cu")
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         variant = 2 if kernel == 0 else kernel - 1
         shape = f"k_label32<{st['block_threads']},{st['points_per_thread']},{variant}>"
-        if rec and rec["source_sha256_prefix"] == sha and rec["kernel"] == shape:
-            return rec["bytes_per_launch"]
+        for rec in recs:
+            if rec["source_sha256_prefix"] == sha and rec["kernel"] == shape:
+                return rec["bytes_per_launch"]
     except Exception:
         return None
     return None
@@ -482,25 +485,47 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: every step copies the
     # points from pinned host memory to the device and the labels back into
-    # pinned host memory (copies inside the timed region)
+    # pinned host memory (copies inside the timed region).  The headline
+    # e2e is the pipelined entry point (zef_label_points_async: each step's
+    # copies on their own streams, overlapping the neighbouring steps'
+    # labeling); the synchronous single call is reported beside it.
     if not args.no_e2e:
         pts_pin = torch.from_numpy(pts_h).pin_memory()
-        lab_pin = torch.empty(n_local, dtype=torch.int32).pin_memory()
-        ctx.label_points(pts_pin, labels=lab_pin, opts=opts, stats=False)
+        lab_pin = [torch.empty(n_local, dtype=torch.int32).pin_memory() for _ in range(2)]
         ke = max(1, args.steps)
+        ctx.label_points(pts_pin, labels=lab_pin[0], opts=opts, stats=False)
         barrier()
         t0 = time.perf_counter()
         for _ in range(ke):
-            ctx.label_points(pts_pin, labels=lab_pin, opts=opts, stats=False)
+            ctx.label_points(pts_pin, labels=lab_pin[0], opts=opts, stats=False)
+        barrier()
+        t_single = (time.perf_counter() - t0) / ke
+        same_single = bool(np.array_equal(lab_pin[0].numpy(), labels.cpu().numpy()))
+        for k in range(2):                   # warm-up: the two staging slots
+            lab_pin[k].fill_(-7)
+            ctx.label_points_async(pts_pin, lab_pin[k], opts=opts)
+        ctx.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(ke):
+            ctx.label_points_async(pts_pin, lab_pin[k % 2], opts=opts)
+        ctx.synchronize()
         barrier()
         te = (time.perf_counter() - t0) / ke
         if ws > 1:
             from paper_2203_10000_gb300.shard import max_over_ranks
             te = max_over_ranks(te, device=dev)
+            t_single = max_over_ranks(t_single, device=dev)
+        ref_lab = labels.cpu().numpy()
         line["e2e"] = {"value": nominal_job / te, "unit": "pairs/s", "h2d_bytes_per_step": int(n_local * 12),
                        "d2h_bytes_per_step": int(n_local * 4), "ms_per_step": te * 1e3, "steps": ke,
+                       "api": "zef_label_points_async, K calls then zef_synchronize",
                        "host_memory": "pinned", "timer": "host clock around K calls, synchronized",
-                       "labels_equal_device_run": bool(np.array_equal(lab_pin.numpy(), labels.cpu().numpy()))}
+                       "labels_equal_device_run": bool(all(np.array_equal(lab_pin[k].numpy(), ref_lab)
+                                                           for k in range(min(2, ke)))),
+                       "single_call": {"api": "zef_label_points (synchronous)", "ms_per_step": t_single * 1e3,
+                                       "value": nominal_job / t_single,
+                                       "labels_equal_device_run": same_single}}
         del pts_pin, lab_pin
 
     # FP32 + rescue vs the plain FP64 kernel on the same subset

@@ -274,6 +274,25 @@ zef_status zef_compartment_priority(zef_ctx *ctx, const int32_t *ids, int32_t n)
 zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
                             float *omega, const zef_label_opts *opts, zef_label_stats *stats);
 
+/* Pipelined labeling of batches in host memory: the labels of
+   zef_label_points (Sec. 2.1.3 initial labeling, Sec. 2.1 priority) without
+   waiting for them.  The call enqueues the copy of pts into one of two
+   device staging slots (used in turn) on a copy-in stream, the labeling on
+   the context stream and the copy of the labels back on a copy-out stream,
+   and returns; so the copy-in of the next call and the copy-out of this one
+   run while the neighbouring calls label.
+     pts     [n][3] float32, host or device; host memory should be
+             page-locked (pageable memory is copied synchronously, without
+             overlap); it must stay unchanged until zef_synchronize returns
+     labels  [n] int32 out, host or device; complete after zef_synchronize
+     opts    nullable = defaults
+   No solid angles or statistics (use zef_label_points).  Argument errors
+   return at once; errors of the device work are returned by the next
+   zef_synchronize, which waits for all three streams.  A slot whose
+   capacity grows waits for its previous use and reallocates. */
+zef_status zef_label_points_async(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
+                                  const zef_label_opts *opts);
+
 /* Element labels by the four-nodes rule (Sec. 2.1.3: a tetrahedron whose
    four nodes all lie inside dS is an element of S) under the priority order
    of Sec. 2.1: the label of a tet is the first compartment in priority order
@@ -424,8 +443,9 @@ zef_status zef_taubin_smooth_surface(zef_ctx *ctx, float *nodes, int64_t n_nodes
 zef_status zef_inflate(zef_ctx *ctx, float *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                        int32_t compartment_id, float zeta, int64_t *moved);
 
-/* Wait for the context's stream and report any error a kernel recorded
-   (ZEF_ERR_TIMEOUT, ZEF_ERR_CAPACITY). */
+/* Wait for the context's stream (and the copy streams of
+   zef_label_points_async) and report any error a kernel recorded
+   (ZEF_ERR_TIMEOUT, ZEF_ERR_CAPACITY, ZEF_ERR_BOUNDS). */
 zef_status zef_synchronize(zef_ctx *ctx);
 
 /* Library version, encoded as major * 1000 + minor. */

@@ -217,9 +217,19 @@ void zef_destroy(zef_ctx *ctx) {
   }
   DeviceGuard g(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->s_in) cudaStreamSynchronize(ctx->s_in);
+  if (ctx->s_out) cudaStreamSynchronize(ctx->s_out);
   auto fr = [](void *p) {
     if (p) cudaFree(p);
   };
+  for (auto &sl : ctx->pipe) {
+    fr(sl.pts);
+    fr(sl.labels);
+    for (cudaEvent_t e : {sl.h2d, sl.done, sl.d2h})
+      if (e) cudaEventDestroy(e);
+  }
+  if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+  if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
   fr(ctx->d_entries);
   fr(ctx->d_tris);
   fr(ctx->d_nodes);
@@ -506,6 +516,10 @@ zef_status zef_synchronize(zef_ctx *ctx) {
   if (ctx->device == ZEF_HOST_ONLY) return ZEF_OK;
   DeviceGuard g(ctx->device);
   CK(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if (ctx->s_in) {
+    CK(cudaStreamSynchronize(ctx->s_in), "cudaStreamSynchronize(copy-in)");
+    CK(cudaStreamSynchronize(ctx->s_out), "cudaStreamSynchronize(copy-out)");
+  }
   uint32_t st[2] = {0, 0};
   CK(cudaMemcpy(st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost), "read status");
   if (st[0]) {
@@ -527,6 +541,13 @@ zef_status zef_label_points(zef_ctx *ctx, const float *pts, int64_t n, int32_t *
   if (!ctx) return ZEF_ERR_INVALID_ARG;
   ctx->err.clear();
   return zef::label_points_impl(ctx, pts, n, labels, omega, opts, stats, nullptr, false);
+}
+
+zef_status zef_label_points_async(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
+                                  const zef_label_opts *opts) {
+  if (!ctx) return ZEF_ERR_INVALID_ARG;
+  ctx->err.clear();
+  return zef::label_points_async_impl(ctx, pts, n, labels, opts);
 }
 
 zef_status zef_label_elements(zef_ctx *ctx, const float *nodes, int64_t n_nodes, const int32_t *tets,
@@ -593,27 +614,135 @@ namespace zef {
 // zef_label_points; with d_masks (device, nullable) the inside bits of every
 // point are written in the caller's order, and full_masks turns the priority
 // early exit off so that every bit is decided.
-zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels, float *omega,
-                             const zef_label_opts *opts, zef_label_stats *stats, unsigned long long *d_masks,
-                             bool full_masks) {
-  NvtxRange nvtx_("zef.label_points");
+// Checks shared by the labeling entry points; *o gets the options with
+// their defaults filled in.
+static zef_status check_label_call(zef_ctx *ctx, const float *pts, int64_t n, const int32_t *labels,
+                                   const zef_label_opts *opts, zef_label_opts *o) {
   if (ctx->comps.empty()) return fail(ctx, ZEF_ERR_NOT_READY, "no compartment registered");
   if (ctx->device == ZEF_HOST_ONLY) return fail(ctx, ZEF_ERR_NOT_READY, "host-only context cannot label");
   if (n < 0 || (n > 0 && (!pts || !labels)))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad points/labels arguments");
   if (n > ((int64_t)1 << 31) - 1) return fail(ctx, ZEF_ERR_INVALID_ARG, "too many points (max 2^31-1)");
-  zef_label_opts o;
-  if (opts) o = *opts; else std::memset(&o, 0, sizeof(o));
-  fill_default_opts(&o);
-  if (o.precision < 0 || o.precision > 2 || o.kernel < 0 || o.kernel > 2)
+  if (opts) *o = *opts; else std::memset(o, 0, sizeof(*o));
+  fill_default_opts(o);
+  if (o->precision < 0 || o->precision > 2 || o->kernel < 0 || o->kernel > 2)
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad precision or kernel");
-  if (o.flags & ~kLabelFlagsAll) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
-  if ((o.block_threads || o.points_per_thread) && !shape_valid(o.block_threads, o.points_per_thread))
+  if (o->flags & ~kLabelFlagsAll) return fail(ctx, ZEF_ERR_INVALID_ARG, "unknown label flags");
+  if ((o->block_threads || o->points_per_thread) && !shape_valid(o->block_threads, o->points_per_thread))
     return fail(ctx, ZEF_ERR_INVALID_ARG, "bad launch shape (threads 128/256, points 2/4)");
+  return ZEF_OK;
+}
+
+// Enqueue one labeling of the device points d_pts[n] on the context stream
+// (labels into d_lab, solid angles into d_om when non-null); *shape gets the
+// launch shape, *launches the library kernels enqueued.  Autotuning (first
+// call of a new shape key) synchronizes; nothing else does.
+static zef_status enqueue_labeling(zef_ctx *ctx, const float *d_pts, int64_t n, int32_t *d_lab, float *d_om,
+                                   const zef_label_opts &o, unsigned long long *d_masks, bool full_masks,
+                                   bool timed, LaunchShape *shape, int64_t *launches) {
+  LabelPlan plan;
+  plan.pts = d_pts;
+  plan.labels = d_lab;
+  plan.omega = d_om;
+  plan.omega_ld = n;
+  plan.n_cap = n;
+  plan.d_n = ctx->lb.counters + CNT_N;
+  plan.d_off = ctx->lb.counters + CNT_OFF;
+  plan.opts = o;
+  plan.masks = d_masks;
+  plan.full_masks = full_masks;
+  bool need_tune = false;
+  plan.shape = choose_shape(ctx, o, n, &need_tune);
+  plan.timed = timed;
+  zef_status st;
+  if (need_tune && (st = autotune(ctx, plan, &plan.shape))) return st;
+  const int64_t launches0 = ctx->launches;
+  if ((st = label_set_count(ctx, n, 0))) return st;
+  if ((st = label_enqueue(ctx, plan))) return st;
+  *shape = plan.shape;
+  *launches = ctx->launches - launches0;
+  return ZEF_OK;
+}
+
+// Pipelined labeling (zef_label_points_async): slot k = call parity.  The
+// copy-in stream waits until the labeling that last read slot k finished,
+// copies the points and records h2d; the context stream waits for h2d (and
+// for the copy-out of the slot's previous labels), labels and records done;
+// the copy-out stream waits for done, copies the labels and records d2h.
+zef_status label_points_async_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
+                                   const zef_label_opts *opts) {
+  NvtxRange nvtx_("zef.label_points_async");
+  zef_label_opts o;
+  zef_status st = check_label_call(ctx, pts, n, labels, opts, &o);
+  if (st) return st;
+  if (n == 0) return ZEF_OK;
+  DeviceGuard g(ctx->device);
+  if ((st = ensure_uploaded(ctx))) return st;
+  if ((st = label_reserve(ctx, n))) return st;
+  const bool dpts = is_device_ptr(pts, ctx->device), dlab = is_device_ptr(labels, ctx->device);
+  LaunchShape shape;
+  int64_t launches = 0;
+  if (dpts && dlab) return enqueue_labeling(ctx, pts, n, labels, nullptr, o, nullptr, false, false, &shape, &launches);
+  if (!ctx->s_in) {
+    CK(cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking), "cudaStreamCreate(copy-in)");
+    CK(cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking), "cudaStreamCreate(copy-out)");
+    for (auto &sl : ctx->pipe) {
+      CK(cudaEventCreateWithFlags(&sl.h2d, cudaEventDisableTiming), "cudaEventCreate");
+      CK(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming), "cudaEventCreate");
+      CK(cudaEventCreateWithFlags(&sl.d2h, cudaEventDisableTiming), "cudaEventCreate");
+    }
+  }
+  zef_ctx::PipeSlot &sl = ctx->pipe[ctx->pipe_next];
+  ctx->pipe_next ^= 1;
+  if (sl.cap < n) {
+    // the slot's previous copies and labeling must be over before it is freed
+    CK(cudaEventSynchronize(sl.done), "wait for the slot");
+    CK(cudaEventSynchronize(sl.d2h), "wait for the slot");
+    if (sl.pts) cudaFree(sl.pts);
+    if (sl.labels) cudaFree(sl.labels);
+    sl.pts = nullptr;
+    sl.labels = nullptr;
+    sl.cap = 0;
+    CK(cudaMalloc(&sl.pts, (size_t)n * 3 * sizeof(float)), "cudaMalloc(staging points)");
+    CK(cudaMalloc(&sl.labels, (size_t)n * sizeof(int32_t)), "cudaMalloc(staging labels)");
+    sl.cap = n;
+  }
+  const float *d_pts = pts;
+  if (!dpts) {
+    CK(cudaStreamWaitEvent(ctx->s_in, sl.done, 0), "cudaStreamWaitEvent");
+    CK(cudaMemcpyAsync(sl.pts, pts, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, ctx->s_in),
+       "copy points");
+    CK(cudaEventRecord(sl.h2d, ctx->s_in), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(ctx->stream, sl.h2d, 0), "cudaStreamWaitEvent");
+    d_pts = sl.pts;
+  }
+  int32_t *d_lab = labels;
+  if (!dlab) {
+    CK(cudaStreamWaitEvent(ctx->stream, sl.d2h, 0), "cudaStreamWaitEvent");
+    d_lab = sl.labels;
+  }
+  if ((st = enqueue_labeling(ctx, d_pts, n, d_lab, nullptr, o, nullptr, false, false, &shape, &launches))) return st;
+  CK(cudaEventRecord(sl.done, ctx->stream), "cudaEventRecord");
+  if (!dlab) {
+    CK(cudaStreamWaitEvent(ctx->s_out, sl.done, 0), "cudaStreamWaitEvent");
+    CK(cudaMemcpyAsync(labels, sl.labels, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->s_out),
+       "copy labels");
+    CK(cudaEventRecord(sl.d2h, ctx->s_out), "cudaEventRecord");
+  }
+  return ZEF_OK;
+}
+
+zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels, float *omega,
+                             const zef_label_opts *opts, zef_label_stats *stats, unsigned long long *d_masks,
+                             bool full_masks) {
+  NvtxRange nvtx_("zef.label_points");
+  zef_label_opts o;
+  zef_status st = check_label_call(ctx, pts, n, labels, opts, &o);
+  if (st) return st;
   if (stats) std::memset(stats, 0, sizeof(*stats));
   if (n == 0) return ZEF_OK;
   DeviceGuard g(ctx->device);
-  zef_status st = ensure_uploaded(ctx);
+  st = ensure_uploaded(ctx);
   if (st) return st;
   st = label_reserve(ctx, n);
   if (st) return st;
@@ -640,30 +769,10 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
     }
     d_om = b.omega_tmp;
   }
-  LabelPlan plan;
-  plan.pts = d_pts;
-  plan.labels = d_lab;
-  plan.omega = d_om;
-  plan.omega_ld = n;
-  plan.n_cap = n;
-  plan.d_n = b.counters + CNT_N;
-  plan.d_off = b.counters + CNT_OFF;
-  plan.opts = o;
-  plan.masks = d_masks;
-  plan.full_masks = full_masks;
-  bool need_tune = false;
-  plan.shape = choose_shape(ctx, o, n, &need_tune);
-  plan.timed = stats != nullptr;
-  if (need_tune) {
-    st = autotune(ctx, plan, &plan.shape);
-    if (st) return st;
-  }
-  const int64_t launches0 = ctx->launches;
-  st = label_set_count(ctx, n, 0);
+  LaunchShape shape;
+  int64_t launches = 0;
+  st = enqueue_labeling(ctx, d_pts, n, d_lab, d_om, o, d_masks, full_masks, stats != nullptr, &shape, &launches);
   if (st) return st;
-  st = label_enqueue(ctx, plan);
-  if (st) return st;
-  const int64_t launches = ctx->launches - launches0;
   if (!dlab)
     CK(cudaMemcpyAsync(labels, d_lab, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream),
        "copy labels");
@@ -692,8 +801,8 @@ zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t 
     stats->representative_pairs = h[CNT_REP_PAIRS];
     stats->lane_walk_items = h[CNT_LANE_TILES];
     stats->kernel_launches = launches;
-    stats->block_threads = plan.shape.threads;
-    stats->points_per_thread = plan.shape.ppt;
+    stats->block_threads = shape.threads;
+    stats->points_per_thread = shape.ppt;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[5]);
     stats->ms_total = ms;

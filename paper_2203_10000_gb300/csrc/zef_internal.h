@@ -272,6 +272,21 @@ struct zef_ctx {
   // autotuner cache: key -> shape
   std::vector<std::pair<uint64_t, zef::LaunchShape>> tune_cache;
 
+  // zef_label_points_async: a copy-in and a copy-out stream beside the
+  // context stream, and two staging slots used in turn, so that one call's
+  // copies overlap the neighbouring calls' labeling.  Events: h2d (slot's
+  // points landed), done (labeling that read the slot finished), d2h
+  // (slot's labels copied out).
+  struct PipeSlot {
+    float *pts = nullptr;
+    int32_t *labels = nullptr;
+    int64_t cap = 0;
+    cudaEvent_t h2d = nullptr, done = nullptr, d2h = nullptr;
+  };
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  PipeSlot pipe[2];
+  int pipe_next = 0;
+
   // element-label scratch (zef_label_elements)
   int32_t *el_node_labels = nullptr;
   unsigned long long *el_masks = nullptr;
@@ -305,6 +320,8 @@ zef_status ensure_uploaded(zef_ctx *ctx);
 zef_status label_points_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels, float *omega,
                              const zef_label_opts *opts, zef_label_stats *stats, unsigned long long *d_masks,
                              bool full_masks);
+zef_status label_points_async_impl(zef_ctx *ctx, const float *pts, int64_t n, int32_t *labels,
+                                   const zef_label_opts *opts);
 template <class T>
 zef_status ensure_buffer(zef_ctx *ctx, T **p, int64_t *cap, int64_t need);
 

@@ -109,6 +109,8 @@ _lib.zef_compartment_priority.restype = ctypes.c_int
 _lib.zef_label_points.argtypes = [_P, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                   ctypes.POINTER(LabelStats)]
 _lib.zef_label_points.restype = ctypes.c_int
+_lib.zef_label_points_async.argtypes = [_P, _P, _I64, _P, ctypes.POINTER(LabelOpts)]
+_lib.zef_label_points_async.restype = ctypes.c_int
 _lib.zef_label_elements.argtypes = [_P, _P, _I64, _P, _I64, _P, _P, ctypes.POINTER(LabelOpts),
                                     ctypes.POINTER(LabelStats)]
 _lib.zef_label_elements.restype = ctypes.c_int
@@ -233,11 +235,13 @@ class Context:
             raise ZefError(st, "zef_create failed")
         self.device = device
         self.ids = []
+        self._inflight = []   # buffers of label_points_async calls not yet synchronized
 
     def close(self):
         if self._h:
-            _lib.zef_destroy(self._h)
+            _lib.zef_destroy(self._h)   # waits for every stream of the context
             self._h = _P()
+        self._inflight = []
 
     def __del__(self):
         try:
@@ -357,6 +361,27 @@ class Context:
         self._check(_lib.zef_label_points(self._h, pp, n, lp, op, ctypes.byref(o),
                                           ctypes.byref(st) if stats else None))
         return labels, omega, (st.as_dict() if stats else None)
+
+    def label_points_async(self, pts, labels, opts: LabelOpts | None = None):
+        """Enqueue the labeling of pts into labels (both host or CUDA; host
+        tensors should be pinned) and return at once; the copies overlap the
+        neighbouring calls' labeling.  pts and labels are kept referenced and
+        must not be touched until synchronize() returns."""
+        pp, pk, _ = _contig(pts, np.float32, "float32")
+        if pk is not pts:
+            raise ValueError("label_points_async wants contiguous float32 points (no temporary copy)")
+        n = int(np.prod(pk.shape)) // 3
+        if _is_torch(labels):
+            if labels.dtype.itemsize != 4 or not labels.is_contiguous() or labels.numel() != n:
+                raise ValueError("labels must be a contiguous int32 tensor of n elements")
+            lp = labels.data_ptr()
+        else:
+            if labels.dtype != np.int32 or not labels.flags.c_contiguous or labels.size != n:
+                raise ValueError("labels must be a contiguous int32 array of n elements")
+            lp = labels.ctypes.data
+        o = opts if opts is not None else make_opts()
+        self._check(_lib.zef_label_points_async(self._h, pp, n, lp, ctypes.byref(o)))
+        self._inflight.append((pts, labels))
 
     def label_elements(self, nodes, tets, elem_labels=None, node_labels=None,
                        opts: LabelOpts | None = None, want_node_labels: bool = False,
@@ -493,4 +518,7 @@ class Context:
         return int(m.num_nodes), int(m.num_tets), [per[i].as_dict() for i in range(levels)]
 
     def synchronize(self):
-        self._check(_lib.zef_synchronize(self._h))
+        try:
+            self._check(_lib.zef_synchronize(self._h))
+        finally:
+            self._inflight.clear()

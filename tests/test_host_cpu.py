@@ -50,6 +50,27 @@ def test_host_only_context_registers_and_refuses_labeling(zef):
     with pytest.raises(zef.ZefError) as e:
         ctx.label_points(np.zeros((4, 3), np.float32))
     assert e.value.status == zef.ZEF_ERR_NOT_READY
+    with pytest.raises(zef.ZefError) as e:
+        ctx.label_points_async(np.zeros((4, 3), np.float32), np.zeros(4, np.int32))
+    assert e.value.status == zef.ZEF_ERR_NOT_READY
+    assert ctx._inflight == []
+    ctx.synchronize()   # nothing in flight on a host-only context
+
+
+def test_async_labeling_argument_checks(zef):
+    ctx = _host_ctx(zef)
+    pts = np.zeros((4, 3), np.float32)
+    with pytest.raises(ValueError):
+        ctx.label_points_async(pts, np.zeros(3, np.int32))        # wrong label count
+    with pytest.raises(ValueError):
+        ctx.label_points_async(pts, np.zeros(4, np.int64))        # wrong label type
+    with pytest.raises(ValueError):
+        ctx.label_points_async(pts.astype(np.float64), np.zeros(4, np.int32))  # would need a temporary
+    s = zs.config0().surfaces[0]
+    ctx.add_compartment(1, s.verts, s.tris)
+    with pytest.raises(zef.ZefError) as e:   # checks of the library itself
+        ctx.label_points_async(pts, np.zeros(4, np.int32), opts=zef.make_opts(kernel=7))
+    assert e.value.status in (zef.ZEF_ERR_INVALID_ARG, zef.ZEF_ERR_NOT_READY)
 
 
 def test_open_surface_rejected(zef):
