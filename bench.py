@@ -130,7 +130,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -139,6 +139,7 @@ class ClockSampler:
             try:
                 sm.append(float(parts[0]))
                 mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[4:8]):
@@ -146,6 +147,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(mx)) if mx else None,
+                "sm_min_mhz": float(min(sm)) if sm else None,
+                "power_w_median": float(np.median(pw)) if pw else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
@@ -494,6 +497,9 @@ def run_ours(args):
         lab_pin = [torch.empty(n_local, dtype=torch.int32).pin_memory() for _ in range(2)]
         ke = max(1, args.steps)
         ctx.label_points(pts_pin, labels=lab_pin[0], opts=opts, stats=False)
+        e2e_clk = ClockSampler(local)
+        e2e_clk.start()
+        time.sleep(1.0)
         barrier()
         t0 = time.perf_counter()
         for _ in range(ke):
@@ -512,6 +518,7 @@ def run_ours(args):
         ctx.synchronize()
         barrier()
         te = (time.perf_counter() - t0) / ke
+        e2e_clocks = e2e_clk.stop()
         if ws > 1:
             from paper_2203_10000_gb300.shard import max_over_ranks
             te = max_over_ranks(te, device=dev)
@@ -523,6 +530,7 @@ def run_ours(args):
                        "host_memory": "pinned", "timer": "host clock around K calls, synchronized",
                        "labels_equal_device_run": bool(all(np.array_equal(lab_pin[k].numpy(), ref_lab)
                                                            for k in range(min(2, ke)))),
+                       "clocks": e2e_clocks,
                        "single_call": {"api": "zef_label_points (synchronous)", "ms_per_step": t_single * 1e3,
                                        "value": nominal_job / t_single,
                                        "labels_equal_device_run": same_single}}
