@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--extra-configs", default="1,2",
                     help="secondary workloads measured after the headline (comma list, '' for none)")
     ap.add_argument("--points", type=int, default=0, help="limit points (0 = full workload)")
+    ap.add_argument("--omega-points", type=int, default=200_000,
+                    help="sample size of the FP32-sum accuracy check (0 = skip)")
     ap.add_argument("--fp64-points", type=int, default=100_000,
                     help="points of the FP32+rescue vs plain-FP64 comparison")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample points (0 = auto)")
@@ -535,6 +537,35 @@ def run_ours(args):
                                        "value": nominal_job / t_single,
                                        "labels_equal_device_run": same_single}}
         del pts_pin, lab_pin
+
+    # accuracy of the FP32 sums themselves: on a seeded sample, every pair
+    # with an FP32 sum of its own (ZEF_OMEGA_RAW, no FP64 re-evaluation)
+    # against 4 pi k, k the winding number of the default call (certified
+    # or re-evaluated in FP64; the exact Omega of a closed surface off the
+    # surface is 4 pi k)
+    if args.omega_points > 0 and rank == 0:
+        ns = min(n_local, args.omega_points)
+        idx = np.sort(np.random.default_rng(11).choice(n_local, ns, replace=False))
+        sub = pts[torch.from_numpy(idx).to(dev)].contiguous()
+        _, om_def, _ = ctx.label_points(sub, want_omega=True, opts=zef.make_opts(kernel=args.kernel), stats=False)
+        _, om_raw, _ = ctx.label_points(sub, want_omega=True, stats=False,
+                                        opts=zef.make_opts(kernel=args.kernel, omega_raw=True,
+                                                           precision=zef.ZEF_FP32_ONLY))
+        four_pi = 4.0 * np.pi
+        od = om_def.double().cpu().numpy()
+        orw = om_raw.double().cpu().numpy()
+        fin = np.isfinite(od) & np.isfinite(orw)
+        k = np.rint(od[fin] / four_pi)
+        raw = orw[fin]
+        own = raw != (k * four_pi).astype(np.float32).astype(np.float64)   # pairs with a sum of their own
+        err = np.abs(raw[own] - four_pi * k[own])
+        line["omega_fp32"] = {
+            "points": int(ns), "pairs": int(fin.sum()), "pairs_with_fp32_sum": int(own.sum()),
+            "max_abs_err_sr": float(err.max()) if err.size else 0.0,
+            "p9999_abs_err_sr": float(np.quantile(err, 0.9999)) if err.size else 0.0,
+            "above_1e-5": int((err > 1e-5).sum()),
+            "basis": "|Omega32 - 4 pi k| per (point, compartment) pair, ZEF_FP32_ONLY + ZEF_OMEGA_RAW; k from "
+                     "the default call; seeded uniform sample of the workload"}
 
     # FP32 + rescue vs the plain FP64 kernel on the same subset
     if args.fp64_points > 0 and rank == 0:
