@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=4)
-    ap.add_argument("--extra-configs", default="1,2",
+    ap.add_argument("--extra-configs", default="1,2,ary",
                     help="secondary workloads measured after the headline (comma list, '' for none)")
     ap.add_argument("--points", type=int, default=0, help="limit points (0 = full workload)")
     ap.add_argument("--omega-points", type=int, default=200_000,
@@ -71,11 +71,11 @@ def parse():
     return ap.parse_args()
 
 
-def workload(cfg: int, limit: int):
+def workload(cfg, limit: int):
     import zef_synth as zs
-    if cfg not in (0, 1, 2, 4):
-        raise SystemExit("bench workloads: configs 0, 1, 2, 4")
-    w = zs.make_config(cfg)
+    if cfg not in (0, 1, 2, 4, "ary"):
+        raise SystemExit("bench workloads: configs 0, 1, 2, 4 and ary")
+    w = zs.ary_spheres() if cfg == "ary" else zs.make_config(cfg)
     if limit and w.points.shape[0] > limit:
         # a centred window of the lattice order: the middle z-layers, where
         # every compartment's bounding box is crossed
@@ -259,6 +259,12 @@ def roofline(st, ms_label, peak, sms, clocks=None, traffic=None):
          "ms_per_launch": ms_label}
     if clocks and clocks.get("sm_mhz"):
         r["frac_at_sampled_clock"] = achieved / (sms * 256 * clocks["sm_mhz"] * 1e6 / 1e12)
+    try:   # the median SM clock of the driver's sustained GEMM loop (power-capped), for reference
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["clocks_under_load"]["sm_mhz_median"])
+        r["frac_at_measured_under_load_clock"] = achieved / (sms * 256 * mhz * 1e6 / 1e12)
+        r["measured_under_load_mhz"] = mhz
+    except Exception:
+        pass
     return r
 
 
@@ -635,10 +641,11 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     if rank == 0:
-        for cfg in [int(c) for c in args.extra_configs.split(",") if c.strip()]:
+        for tok in [c.strip() for c in args.extra_configs.split(",") if c.strip()]:
+            cfg = int(tok) if tok.isdigit() else tok
             if cfg == args.config:
                 continue
-            line[f"config{cfg}"] = secondary(zef, torch, dev, cfg, flush, stream, lambda: torch.cuda.synchronize(dev),
+            line[f"config{cfg}" if tok.isdigit() else cfg] = secondary(zef, torch, dev, cfg, flush, stream, lambda: torch.cuda.synchronize(dev),
                                              peak, sms, args.kernel)
 
     if rank == 0 and not args.no_refine:
