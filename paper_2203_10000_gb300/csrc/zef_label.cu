@@ -11,11 +11,12 @@
 //   k_keys         binning key of every point: its 21-bit Morton cell in the
 //                  union box of the surfaces, or the tail keys of the points
 //                  outside that box (outside every compartment: winding
-//                  number 0) and of the non-finite points; key histogram
+//                  number 0) and of the non-finite points, which it labels
+//                  at once; key histogram
 //   scan           exclusive scan of the histogram (records where the tails
 //                  start and the tile count)
-//   k_scatter      points into key order (float4, scaled) + permutation,
-//                  inside / uncertain masks cleared
+//   k_scatter      the points inside the union box into key order (float4,
+//                  scaled) + permutation
 //   k_tile_work/k_scan_work/k_tile_scatter
 //                  work list of the tiles of sorted points inside the union
 //                  box whose box meets some compartment's box and convex-hull
@@ -30,13 +31,15 @@
 //   k_rescue64_list (cap-tree form; k_rescue64_caps when the pair list
 //                  overflowed) / k_rescue64 (strip forms)
 //                  FP64 re-evaluation of the uncertain pairs
-//   k_resolve      priority resolve + un-permute
+//   k_resolve      priority resolve + un-permute of the sorted points
 //
 // FP32 hot loop.  Surfaces (whole, or the leaves and caps a tile's walk of the
 // cap tree lists) are stored as triangle strips (one new vertex per
 // triangle), staged into shared memory by 1-D bulk TMA copies
 // (cp.async.bulk + mbarrier, double buffered) and broadcast to every thread;
-// each thread holds P points in registers.  With the window (a, b, c) of the
+// each thread holds P points in registers.  (The tile representatives' passes
+// split the entries over the lanes instead and read them through the
+// read-only cache.)  With the window (a, b, c) of the
 // strip and R_k = v_k - p:
 //     N = R_c . n            (n = (v2 - v1) x (v3 - v1) of the triangle, host
 //                             precomputed in FP64; equal to R1 . (R2 x R3))
@@ -172,6 +175,14 @@ __device__ void record_timeout(uint32_t *status, uint32_t site) {
 }
 
 // ------------------------------------------------------------------ FP32 atan2 / 2
+// |v| from |v|^2: the square root instruction runs on the MUFU pipe, off the
+// FMA pipe that bounds the strip loop (q rsqrt(q) would add a multiply there)
+__device__ __forceinline__ float sqrt_mufu(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // atan2(N, D) in [-pi, pi]: x = min/max(|N|, |D|) in [0, 1], the polynomial
 // above, then the octant reflections x -> pi/2 - x (|N| > |D|), x -> pi - x
 // (D < 0) and the sign of N.  Measured maximum error 2.6 ulp (CUDA documents
@@ -211,7 +222,7 @@ __device__ __forceinline__ void window_init(PState &s, float4 v0) {
   s.ay = s.by = v0.y - s.py;
   s.az = s.bz = v0.z - s.pz;
   float q = fmaf(s.ax, s.ax, fmaf(s.ay, s.ay, s.az * s.az));
-  float r = q * rsqrtf(q);
+  float r = sqrt_mufu(q);
   s.ra = s.rb = r;
   s.sab = 2.f * q;
 }
@@ -219,7 +230,7 @@ __device__ __forceinline__ void window_init(PState &s, float4 v0) {
 __device__ __forceinline__ void vos_step(PState &s, const float4 V, const float4 Nn) {
   const float cx = V.x - s.px, cy = V.y - s.py, cz = V.z - s.pz;
   const float qc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-  const float rc = qc * rsqrtf(qc);
+  const float rc = sqrt_mufu(qc);
   const float dac = fmaf(s.ax, cx, fmaf(s.ay, cy, s.az * cz));
   const float dbc = fmaf(s.bx, cx, fmaf(s.by, cy, s.bz * cz));
   const float N = fmaf(Nn.x, cx, fmaf(Nn.y, cy, Nn.z * cz));
@@ -239,7 +250,7 @@ __device__ __forceinline__ void vos_step(PState &s, const float4 V, const float4
 __device__ __forceinline__ void geom_step(PState &s, const float4 V, const float4 Nn, float &N, float &D) {
   const float cx = V.x - s.px, cy = V.y - s.py, cz = V.z - s.pz;
   const float qc = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-  const float rc = qc * rsqrtf(qc);
+  const float rc = sqrt_mufu(qc);
   const float dac = fmaf(s.ax, cx, fmaf(s.ay, cy, s.az * cz));
   const float dbc = fmaf(s.bx, cx, fmaf(s.by, cy, s.bz * cz));
   N = fmaf(Nn.x, cx, fmaf(Nn.y, cy, Nn.z * cz));
@@ -325,7 +336,7 @@ __device__ __forceinline__ void window_init2(PState2 &s, float4 v0) {
   s.ay = s.by = sub2(vy, s.py);
   s.az = s.bz = sub2(vz, s.pz);
   const f2 q = fma2(s.ax, s.ax, fma2(s.ay, s.ay, mul2(s.az, s.az)));
-  const f2 r = mul2(q, pk(rsqrtf(lo(q)), rsqrtf(hi(q))));
+  const f2 r = pk(sqrt_mufu(lo(q)), sqrt_mufu(hi(q)));
   s.ra = s.rb = r;
   s.sab = add2(q, q);
 }
@@ -334,7 +345,7 @@ __device__ __forceinline__ void window_init2(PState2 &s, float4 v0) {
 __device__ __forceinline__ void geom_step2(PState2 &s, const float4 V, const float4 Nn, f2 &N, f2 &D) {
   const f2 cx = sub2(pk(V.x, V.x), s.px), cy = sub2(pk(V.y, V.y), s.py), cz = sub2(pk(V.z, V.z), s.pz);
   const f2 qc = fma2(cx, cx, fma2(cy, cy, mul2(cz, cz)));
-  const f2 rc = mul2(qc, pk(rsqrtf(lo(qc)), rsqrtf(hi(qc))));
+  const f2 rc = pk(sqrt_mufu(lo(qc)), sqrt_mufu(hi(qc)));
   const f2 dac = fma2(s.ax, cx, fma2(s.ay, cy, mul2(s.az, cz)));
   const f2 dbc = fma2(s.bx, cx, fma2(s.by, cy, mul2(s.bz, cz)));
   N = fma2(pk(Nn.x, Nn.x), cx, fma2(pk(Nn.y, Nn.y), cy, mul2(pk(Nn.z, Nn.z), cz)));
@@ -521,7 +532,7 @@ __device__ __forceinline__ void vos_term(float rx, float ry, float rz, float4 A,
   const float q1 = fmaf(x1, x1, fmaf(y1, y1, z1 * z1));
   const float q2 = fmaf(x2, x2, fmaf(y2, y2, z2 * z2));
   const float q3 = fmaf(x3, x3, fmaf(y3, y3, z3 * z3));
-  const float r1 = q1 * rsqrtf(q1), r2 = q2 * rsqrtf(q2), r3 = q3 * rsqrtf(q3);
+  const float r1 = sqrt_mufu(q1), r2 = sqrt_mufu(q2), r3 = sqrt_mufu(q3);
   const float cx = fmaf(y2, z3, -z2 * y3), cy = fmaf(z2, x3, -x2 * z3), cz = fmaf(x2, y3, -y2 * x3);
   const float N = fmaf(x1, cx, fmaf(y1, cy, z1 * cz));
   const float d12 = fmaf(x1, x2, fmaf(y1, y2, z1 * z2));
@@ -914,48 +925,32 @@ __device__ __forceinline__ void window_prime(PState &s, float4 A, float4 B) {
   s.bz = B.z - s.pz;
   const float qa = fmaf(s.ax, s.ax, fmaf(s.ay, s.ay, s.az * s.az));
   const float qb = fmaf(s.bx, s.bx, fmaf(s.by, s.by, s.bz * s.bz));
-  s.ra = qa * rsqrtf(qa);
-  s.rb = qb * rsqrtf(qb);
+  s.ra = sqrt_mufu(qa);
+  s.rb = sqrt_mufu(qb);
   s.sab = fmaf(s.ra, s.rb, fmaf(s.ax, s.bx, fmaf(s.ay, s.by, s.az * s.bz)));
 }
 
 // Sums of nr <= NR representative points over a range list of strip
-// segments, the entries split over the lanes instead of the points: the list
-// streams through the warp's double buffer in chunks of kWChunk entries and
-// lane l takes the group of four entries [4 l, 4 l + 4) of each chunk.  A
-// group opens its window from the two entries before it (the same segment:
-// segments hold whole groups of four) or restarts at a reset entry, so its
-// four (D + i N) factors are those the sequential stream forms; one atan2 per
-// group, wraps counted as in the point-by-point sums, a Kahan sum per lane.
-// The lanes' sums, wraps and conditioning minima are then combined and each
-// representative is certified by the tests of classify_store.  Returns false
-// when a bounded wait expired; bit r of *certain (r < nr) marks a certified
+// segments, the entries split over the lanes instead of the points: lane l
+// takes the group of four entries [4 l, 4 l + 4) of each run of kWChunk
+// entries of the flattened list.  A group lies inside one segment (segments
+// hold whole groups of four), contiguous in memory, and opens its window from
+// the two entries before it in that segment or restarts at a reset entry, so
+// its four (D + i N) factors are those the sequential stream forms; one
+// atan2 per group, wraps counted as in the point-by-point sums, a Kahan sum
+// per lane.  Each lane reads its own entries through the read-only cache
+// (its cursor over the ranges moves forward only): a warp finishes a run of
+// kWChunk entries about 32 times sooner than in the point-by-point sums, too
+// soon for the warp's bulk-copy pipeline, whose fills are issued by one lane,
+// to keep ahead of it.  The lanes' sums, wraps and conditioning minima are
+// then combined and each representative is certified by the tests of
+// classify_store: bit r of *certain (r < nr) marks a certified
 // representative, its winding number in k[r].
 template <int NR>
-__device__ __noinline__ bool rep_stream(const LabelArgs &a, const int2 *rng, int total, Entry *wbuf, uint64_t *bar,
-                                        uint32_t &ph0, uint32_t &ph1, int lane, const float (*rp)[3], int nr,
-                                        uint32_t *certain, int (&k)[NR]) {
-  const int nchunks = (total + kWChunk - 1) / kWChunk;
-  int fr = 0, fb = 0;  // lane 0's fill cursor over the ranges
-  auto fill = [&](int ch, int b) {
-    const int j0 = ch * kWChunk, j1 = min(total, j0 + kWChunk);
-    tma_expect(&bar[b], (uint32_t)(j1 - j0) * (uint32_t)sizeof(Entry));
-    int j = j0;
-    while (j < j1) {
-      while (j >= fb + rng[fr].y) {
-        fb += rng[fr].y;
-        ++fr;
-      }
-      const int take = min(j1 - j, fb + rng[fr].y - j);
-      tma_copy_1d(wbuf + b * kWChunk + (j - j0), a.cseg + (rng[fr].x + (j - fb)),
-                  (uint32_t)take * (uint32_t)sizeof(Entry), &bar[b]);
-      j += take;
-    }
-  };
-  if (lane == 0) {
-    if (nchunks > 0) fill(0, 0);
-    if (nchunks > 1) fill(1, 1);
-  }
+__device__ __noinline__ void rep_stream(const LabelArgs &a, const int2 *rng, int total, int lane,
+                                        const float (*rp)[3], int nr, uint32_t *certain, int (&k)[NR]) {
+  const int nruns = (total + kWChunk - 1) / kWChunk;
+  int cr = 0, cb = 0;  // the lane's cursor: range, and the range's first flattened entry
   float sum[NR], comp[NR], bad[NR];
   int wr[NR];
 #pragma unroll
@@ -964,50 +959,45 @@ __device__ __noinline__ bool rep_stream(const LabelArgs &a, const int2 *rng, int
     bad[r] = __int_as_float(0x7f800000);
     wr[r] = 0;
   }
-  float4 p2 = make_float4(0.f, 0.f, 0.f, 0.f), p1 = p2;  // the previous chunk's last two vertices
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int b = ch & 1;
-    const bool ok = mbar_wait(&bar[b], b ? ph1 : ph0);
-    if (__any_sync(0xffffffffu, !ok)) return false;
-    if (b) ph1 ^= 1; else ph0 ^= 1;
-    const Entry *E = wbuf + b * kWChunk;
-    const int cnt = min(kWChunk, total - ch * kWChunk);  // a multiple of four
-    const int j = 4 * lane;
-    if (j < cnt) {
-      const float4 v0 = E[j].v, n0 = E[j].n, v1 = E[j + 1].v, n1 = E[j + 1].n;
-      const float4 v2 = E[j + 2].v, n2 = E[j + 2].n, v3 = E[j + 3].v, n3 = E[j + 3].n;
-      const float4 A = j >= 2 ? E[j - 2].v : p2, B = j >= 1 ? E[j - 1].v : p1;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (r >= nr) break;
-        PState st;
-        st.px = rp[r][0];
-        st.py = rp[r][1];
-        st.pz = rp[r][2];
-        st.bad = __int_as_float(0x7f800000);
-        st.kp = st.kn = 0u;
-        if (v0.w == 2.f) window_init(st, v0);
-        else window_prime(st, A, B);
-        float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
-        geom_step(st, v0, n0, N0, D0);
-        geom_step(st, v1, n1, N1, D1);
-        cmul_wrap(D0, N0, D1, N1, r01, i01, st.kp, st.kn);
-        geom_step(st, v2, n2, N0, D0);
-        geom_step(st, v3, n3, N1, D1);
-        cmul_wrap(D0, N0, D1, N1, r23, i23, st.kp, st.kn);
-        cmul_wrap(r01, i01, r23, i23, R, I, st.kp, st.kn);
-        const float y = half_angle(I, R) - comp[r];
-        const float t = sum[r] + y;
-        comp[r] = (t - sum[r]) - y;
-        sum[r] = t;
-        wr[r] += (int)st.kp - (int)st.kn;
-        bad[r] = fminf(bad[r], st.bad);
-      }
+  for (int ch = 0; ch < nruns; ++ch) {
+    const int j = ch * kWChunk + 4 * lane;
+    if (j >= total) continue;
+    const int g = range_pos(rng, cr, cb, j);
+    if (!ZEF_BOUNDS_OK(g >= 0 && (int64_t)g + 4 <= a.n_cseg, a.status, 21)) continue;
+    const Entry *E = a.cseg + g;
+    const float4 v0 = __ldg(&E[0].v), n0 = __ldg(&E[0].n), v1 = __ldg(&E[1].v), n1 = __ldg(&E[1].n);
+    const float4 v2 = __ldg(&E[2].v), n2 = __ldg(&E[2].n), v3 = __ldg(&E[3].v), n3 = __ldg(&E[3].n);
+    float4 A = v0, B = v0;
+    if (v0.w != 2.f) {
+      A = __ldg(&E[-2].v);
+      B = __ldg(&E[-1].v);
     }
-    p2 = E[cnt - 2].v;  // every chunk holds at least four entries
-    p1 = E[cnt - 1].v;
-    __syncwarp();  // every lane is done with buffer b before it is refilled
-    if (lane == 0 && ch + 2 < nchunks) fill(ch + 2, b);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r >= nr) break;
+      PState st;
+      st.px = rp[r][0];
+      st.py = rp[r][1];
+      st.pz = rp[r][2];
+      st.bad = __int_as_float(0x7f800000);
+      st.kp = st.kn = 0u;
+      if (v0.w == 2.f) window_init(st, v0);
+      else window_prime(st, A, B);
+      float N0, D0, N1, D1, r01, i01, r23, i23, R, I;
+      geom_step(st, v0, n0, N0, D0);
+      geom_step(st, v1, n1, N1, D1);
+      cmul_wrap(D0, N0, D1, N1, r01, i01, st.kp, st.kn);
+      geom_step(st, v2, n2, N0, D0);
+      geom_step(st, v3, n3, N1, D1);
+      cmul_wrap(D0, N0, D1, N1, r23, i23, st.kp, st.kn);
+      cmul_wrap(r01, i01, r23, i23, R, I, st.kp, st.kn);
+      const float y = half_angle(I, R) - comp[r];
+      const float t = sum[r] + y;
+      comp[r] = (t - sum[r]) - y;
+      sum[r] = t;
+      wr[r] += (int)st.kp - (int)st.kn;
+      bad[r] = fminf(bad[r], st.bad);
+    }
   }
   uint32_t cert = 0;
 #pragma unroll
@@ -1035,7 +1025,6 @@ __device__ __noinline__ bool rep_stream(const LabelArgs &a, const int2 *rng, int
     }
   }
   *certain = cert;
-  return true;
 }
 
 // Point-by-point sums over a range list of strip segments: chunks of
@@ -1483,7 +1472,6 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       int kg[NG];
 #pragma unroll
       for (int g = 0; g < NG; ++g) kg[g] = 0;
-      bool rep_ok = true;
       if (a.coherence && V == 2) {
         // Coherence (cap-tree form): where no triangle's box meets a box of
         // points, the surface does not cross that box (convex, hence
@@ -1493,8 +1481,8 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         // box tests run over the leaf ranges alone; then one representative
         // (the tile's first usable point) when no triangle box meets the
         // tile's box, else one per group of 16 points that no triangle box
-        // meets.  The representatives' sums stream the whole list through the
-        // warp's buffer with the entries split over the lanes (rep_stream).
+        // meets.  The representatives' sums run over the whole list with the
+        // entries split over the lanes (rep_stream).
         const int nl = s_rtot[wid][2], ltot = s_rtot[wid][3];
         bool tile_hit = false;
         uint32_t touched = 0;
@@ -1534,11 +1522,10 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
           int rk[NG];
 #pragma unroll
           for (int g = 0; g < NG; ++g) rk[g] = 0;
-          for (int r0 = 0; r0 < nrep && rep_ok; r0 += 2) {
+          for (int r0 = 0; r0 < nrep; r0 += 2) {
             uint32_t c2 = 0;
             int k2[2] = {0, 0};
-            rep_ok = rep_stream<2>(a, s_rng[wid], rtotal, wbuf, bar, ph0, ph1, lane, s_rep[wid] + r0,
-                                   min(2, nrep - r0), &c2, k2);
+            rep_stream<2>(a, s_rng[wid], rtotal, lane, s_rep[wid] + r0, min(2, nrep - r0), &c2, k2);
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
               if (g == r0 && (c2 & 1u)) rk[g] = k2[0];
@@ -1678,10 +1665,6 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
           atomicAdd((unsigned long long *)(a.counters + CNT_PAIRS_EVAL), reps);
           atomicAdd((unsigned long long *)(a.counters + CNT_REP_PAIRS), reps);
         }
-      }
-      if (!rep_ok) {
-        timed_out = true;
-        break;
       }
       const uint32_t act = need & ~coh;
       if (!act) continue;
@@ -2338,46 +2321,70 @@ __device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key, bool va
 // Binning key of every point: the 21-bit Morton cell of the point in the
 // union box of the registered surfaces (7 bits per axis), kKeyOutside for a
 // finite point outside that box -- outside every compartment's box, so its
-// winding number is 0 for every surface and it needs no tile -- and
-// kKeyNonfinite for a point with a NaN or infinite coordinate.  Sorted by
-// key, the points inside the box come first, then those outside, then the
-// non-finite ones.
+// winding number is 0 for every surface -- and kKeyNonfinite for a point with
+// a NaN or infinite coordinate.  The points of the two tails are decided here
+// (label 0, or -1 and NaN solid angles for the non-finite ones; zero inside
+// bits) and take no further part: the sorted order holds the points inside
+// the box alone.  Each warp takes kBinU runs of 32 consecutive points per
+// pass, their loads and histogram increments issued together.
+constexpr int kBinU = 4;
+
 __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, UnionBox ub, uint32_t *keys,
-                                             uint32_t *hist) {
+                                             uint32_t *hist, int32_t *labels, unsigned long long *masks_out,
+                                             float *omega, int64_t omega_ld, int ncomp) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
   const int lane = threadIdx.x & 31;
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * kBinU;
   // warp-uniform loop: all lanes take part in the aggregated increments
-  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n;
-       i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = i0 + lane;
-    const bool valid = i < n;
-    const uint32_t spread = (uint32_t)(i0 >> 5) % kTailKeys;  // one tail key per warp and pass
-    uint32_t key = 0;
-    if (valid) {
-      const float *p = pts + 3 * (off + i);
-      const float v[3] = {p[0], p[1], p[2]};
-      if (!finite3(v[0], v[1], v[2])) {
-        key = kKeyNonfinite + spread;
-      } else if (v[0] < ub.lo[0] || v[0] > ub.hi[0] || v[1] < ub.lo[1] || v[1] > ub.hi[1] ||
-                 v[2] < ub.lo[2] || v[2] > ub.hi[2]) {
-        key = kKeyOutside + spread;
-      } else {
-        uint32_t q[3];
+  for (int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kBinU; w0 < n; w0 += step) {
+    float v[kBinU][3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) q[k] = (uint32_t)min((int)((v[k] - ub.lo[k]) * ub.sc[k]), (1 << kMortonBits) - 1);
-        key = spread7(q[0]) | (spread7(q[1]) << 1) | (spread7(q[2]) << 2);
+    for (int u = 0; u < kBinU; ++u) {
+      const int64_t i = w0 + 32 * u + lane;
+      if (i < n) {
+        const float *p = pts + 3 * (off + i);
+        v[u][0] = p[0];
+        v[u][1] = p[1];
+        v[u][2] = p[2];
       }
-      keys[i] = key;
     }
-    agg_inc(hist, key, valid, lane);
+    uint32_t key[kBinU];
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+      const int64_t i = w0 + 32 * u + lane;
+      const uint32_t spread = (uint32_t)((w0 >> 5) + u) % kTailKeys;  // one tail key per run of 32
+      key[u] = 0;
+      if (i < n) {
+        const bool fin = finite3(v[u][0], v[u][1], v[u][2]);
+        if (!fin) {
+          key[u] = kKeyNonfinite + spread;
+        } else if (v[u][0] < ub.lo[0] || v[u][0] > ub.hi[0] || v[u][1] < ub.lo[1] || v[u][1] > ub.hi[1] ||
+                   v[u][2] < ub.lo[2] || v[u][2] > ub.hi[2]) {
+          key[u] = kKeyOutside + spread;
+        } else {
+          uint32_t q[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            q[k] = (uint32_t)min((int)((v[u][k] - ub.lo[k]) * ub.sc[k]), (1 << kMortonBits) - 1);
+          key[u] = spread7(q[0]) | (spread7(q[1]) << 1) | (spread7(q[2]) << 2);
+        }
+        keys[i] = key[u];
+        if (key[u] >= kKeyOutside) {
+          labels[off + i] = fin ? 0 : -1;
+          if (masks_out) masks_out[off + i] = 0ull;
+          if (!fin && omega)
+            for (int r = 0; r < ncomp; ++r) omega[(int64_t)r * omega_ld + i] = __int_as_float(0x7fc00000);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) agg_inc(hist, key[u], w0 + 32 * u + lane < n, lane);
   }
 }
 
-// Points in key order, multiplied by the context's power-of-two scale
-// (exact), with their permutation (the inside / uncertain masks of the points
-// inside the union box are cleared by the tile pass, in sorted order).  A
-// non-finite input point becomes NaN; a finite one that the scale would push
-// past the float range is clamped (it lies outside every surface's box).
+// Points inside the union box in key order, multiplied by the context's
+// power-of-two scale (exact), with their permutation (their inside /
+// uncertain masks are cleared by the tile pass, in sorted order).
 __device__ __forceinline__ float scaled_coord(float x, float s) {
   return fminf(fmaxf(x * s, -3.0e38f), 3.0e38f);
 }
@@ -2387,24 +2394,36 @@ __global__ void __launch_bounds__(256) k_scatter(const float *pts, int64_t *cnt,
                                                 uint32_t *status) {
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
   const int lane = threadIdx.x & 31;
-  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n;
-       i0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = i0 + lane;
-    const bool valid = i < n;
-    const uint32_t pos = agg_inc(cursor, valid ? keys[i] : 0u, valid, lane);
-    if (!valid) continue;
-    const float *p = pts + 3 * (off + i);
-    const float x = p[0], y = p[1], z = p[2];
-    float4 q;
-    if (finite3(x, y, z)) {
-      q = make_float4(scaled_coord(x, scale), scaled_coord(y, scale), scaled_coord(z, scale), 0.f);
-    } else {
-      const float nan = __int_as_float(0x7fc00000);
-      q = make_float4(nan, nan, nan, 0.f);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x * kBinU;
+  for (int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kBinU; w0 < n; w0 += step) {
+    uint32_t key[kBinU];
+    bool in[kBinU];
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+      const int64_t i = w0 + 32 * u + lane;
+      key[u] = i < n ? keys[i] : kKeyOutside;
+      in[u] = key[u] < kKeyOutside;
     }
-    if (!ZEF_BOUNDS_OK((int64_t)pos < n, status, 17)) continue;
-    spts[pos] = q;
-    perm[pos] = (int32_t)i;
+    float v[kBinU][3];
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u)
+      if (in[u]) {
+        const float *p = pts + 3 * (off + w0 + 32 * u + lane);
+        v[u][0] = p[0];
+        v[u][1] = p[1];
+        v[u][2] = p[2];
+      }
+    uint32_t pos[kBinU];
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) pos[u] = agg_inc(cursor, key[u], in[u], lane);
+#pragma unroll
+    for (int u = 0; u < kBinU; ++u) {
+      if (!in[u]) continue;
+      if (!ZEF_BOUNDS_OK((int64_t)pos[u] < n, status, 17)) continue;
+      spts[pos[u]] = make_float4(scaled_coord(v[u][0], scale), scaled_coord(v[u][1], scale),
+                                 scaled_coord(v[u][2], scale), 0.f);
+      perm[pos[u]] = (int32_t)(w0 + 32 * u + lane);
+    }
   }
 }
 
@@ -2537,29 +2556,20 @@ __global__ void __launch_bounds__(256) k_tile_scatter(int64_t *cnt, const uint32
   }
 }
 
-// Labels in the caller's order: the first set bit of the priority-ordered
-// inside mask -> id (0 when none, and for the points outside the union box,
-// the first tail of the sorted order), -1 for the non-finite points (the
-// second tail).
+// Labels in the caller's order of the points inside the union box (the
+// sorted points): the first set bit of the priority-ordered inside mask -> id,
+// 0 when none.  The points outside the box and the non-finite ones were
+// labelled by k_keys.
 __global__ void __launch_bounds__(256) k_resolve(LabelArgs a, int32_t *labels, const int32_t *row_ids) {
   const int64_t n = a.counters[CNT_N], off = a.counters[CNT_OFF], nfin = a.counters[CNT_NFIN];
   const int64_t nin = a.counters[CNT_NIN];
   if (blockIdx.x == 0 && threadIdx.x == 0) a.counters[CNT_NONFINITE] = n - nfin;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nin; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t o = a.perm[i];
     if (!ZEF_BOUNDS_OK(o >= 0 && o < n, a.status, 18)) continue;
-    int32_t lab;
-    if (i >= nfin) {
-      lab = -1;
-      if (a.masks_out) a.masks_out[off + o] = 0ull;
-      if (a.omega)
-        for (int r = 0; r < a.ncomp; ++r) a.omega[(int64_t)r * a.omega_ld + o] = __int_as_float(0x7fc00000);
-    } else {
-      const unsigned long long m = i < nin ? a.in_mask[i] : 0ull;
-      lab = m ? row_ids[__ffsll((long long)m) - 1] : 0;
-      if (a.masks_out) a.masks_out[off + o] = m;
-    }
-    labels[off + o] = lab;
+    const unsigned long long m = a.in_mask[i];
+    if (a.masks_out) a.masks_out[off + o] = m;
+    labels[off + o] = m ? row_ids[__ffsll((long long)m) - 1] : 0;
   }
 }
 
@@ -2969,7 +2979,8 @@ zef_status label_enqueue(zef_ctx *ctx, const LabelPlan &plan) {
   const int g = grid_for(ctx, ncap, 256);
   // binning: keys in the surfaces' union box, key histogram, scan, scatter
   cudaMemsetAsync(b.hist, 0, (size_t)kHistLen * sizeof(uint32_t), s);
-  k_keys<<<g, 256, 0, s>>>(plan.pts, b.counters, ctx->ubox, b.keys, b.hist);
+  k_keys<<<g, 256, 0, s>>>(plan.pts, b.counters, ctx->ubox, b.keys, b.hist, plan.labels, plan.masks, plan.omega,
+                           plan.omega_ld, C);
   ++launches;
   zef_status st = scan_keys(ctx, b.hist, tile);
   if (st) return st;
