@@ -113,13 +113,12 @@ constexpr float kKappa = 1.0f / 8192.0f;  // conditioning threshold of a pair
 constexpr int kMortonBits = 7;    // bits per axis of the binning key
 constexpr int kBuckets = 1 << (3 * kMortonBits);
 // binning keys past the Morton cells: finite points outside the surfaces'
-// union box, then non-finite points (sorted to the tail in that order), each
-// spread over kTailKeys keys by warp so that their counts and cursors are not
-// one contended address
-constexpr uint32_t kTailKeys = 256;
-constexpr uint32_t kKeyOutside = (uint32_t)kBuckets;                // first of kTailKeys
-constexpr uint32_t kKeyNonfinite = (uint32_t)kBuckets + kTailKeys;  // first of kTailKeys
-constexpr int64_t kHistLen = (int64_t)kBuckets + 2 * kTailKeys;     // key histogram / cursor entries
+// union box, then non-finite points (the two tails of the sorted order, in
+// that order; their points are labelled by the key pass and not scattered,
+// so each tail's count is one histogram word, added once per block)
+constexpr uint32_t kKeyOutside = (uint32_t)kBuckets;
+constexpr uint32_t kKeyNonfinite = (uint32_t)kBuckets + 1;
+constexpr int64_t kHistLen = (int64_t)kBuckets + 2;  // key histogram / cursor entries
 constexpr int kWorkBuckets = 4096;                    // log-scale work buckets of the tile list
 // exclusive scan: threads per block, values per thread, values per block
 constexpr int kScanT = 256;

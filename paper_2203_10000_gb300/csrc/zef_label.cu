@@ -2325,16 +2325,24 @@ __device__ __forceinline__ uint32_t agg_inc(uint32_t *ctr, uint32_t key, bool va
 // a NaN or infinite coordinate.  The points of the two tails are decided here
 // (label 0, or -1 and NaN solid angles for the non-finite ones; zero inside
 // bits) and take no further part: the sorted order holds the points inside
-// the box alone.  Each warp takes kBinU runs of 32 consecutive points per
+// the box alone.  Their counts are summed per block in shared memory and
+// added once per block (all of them on one histogram word each: atomics of
+// every warp on a few neighbouring words kept one L2 slice busy for most of
+// the kernel).  Each warp takes kBinU runs of 32 consecutive points per
 // pass, their loads and histogram increments issued together.
 constexpr int kBinU = 4;
 
-__global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, UnionBox ub, uint32_t *keys,
-                                             uint32_t *hist, int32_t *labels, unsigned long long *masks_out,
+__global__ void __launch_bounds__(256) k_keys(const float *__restrict__ pts, int64_t *cnt, UnionBox ub,
+                                             uint32_t *__restrict__ keys, uint32_t *hist,
+                                             int32_t *__restrict__ labels, unsigned long long *masks_out,
                                              float *omega, int64_t omega_ld, int ncomp) {
+  __shared__ uint32_t s_tail[2];  // outside the union box, non-finite
+  if (threadIdx.x < 2) s_tail[threadIdx.x] = 0u;
+  __syncthreads();
   const int64_t n = cnt[CNT_N], off = cnt[CNT_OFF];
   const int lane = threadIdx.x & 31;
   const int64_t step = (int64_t)gridDim.x * blockDim.x * kBinU;
+  uint32_t n_out = 0, n_nonfin = 0;  // lane 0: the warp's tail points
   // warp-uniform loop: all lanes take part in the aggregated increments
   for (int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31)) * kBinU; w0 < n; w0 += step) {
     float v[kBinU][3];
@@ -2352,16 +2360,14 @@ __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, Un
 #pragma unroll
     for (int u = 0; u < kBinU; ++u) {
       const int64_t i = w0 + 32 * u + lane;
-      const uint32_t spread = (uint32_t)((w0 >> 5) + u) % kTailKeys;  // one tail key per run of 32
-      key[u] = 0;
+      key[u] = kKeyOutside;
+      bool fin = true;
       if (i < n) {
-        const bool fin = finite3(v[u][0], v[u][1], v[u][2]);
+        fin = finite3(v[u][0], v[u][1], v[u][2]);
         if (!fin) {
-          key[u] = kKeyNonfinite + spread;
-        } else if (v[u][0] < ub.lo[0] || v[u][0] > ub.hi[0] || v[u][1] < ub.lo[1] || v[u][1] > ub.hi[1] ||
-                   v[u][2] < ub.lo[2] || v[u][2] > ub.hi[2]) {
-          key[u] = kKeyOutside + spread;
-        } else {
+          key[u] = kKeyNonfinite;
+        } else if (!(v[u][0] < ub.lo[0] || v[u][0] > ub.hi[0] || v[u][1] < ub.lo[1] || v[u][1] > ub.hi[1] ||
+                     v[u][2] < ub.lo[2] || v[u][2] > ub.hi[2])) {
           uint32_t q[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k)
@@ -2376,9 +2382,20 @@ __global__ void __launch_bounds__(256) k_keys(const float *pts, int64_t *cnt, Un
             for (int r = 0; r < ncomp; ++r) omega[(int64_t)r * omega_ld + i] = __int_as_float(0x7fc00000);
         }
       }
+      n_out += __popc(__ballot_sync(0xffffffffu, i < n && fin && key[u] == kKeyOutside));
+      n_nonfin += __popc(__ballot_sync(0xffffffffu, i < n && !fin));
     }
 #pragma unroll
-    for (int u = 0; u < kBinU; ++u) agg_inc(hist, key[u], w0 + 32 * u + lane < n, lane);
+    for (int u = 0; u < kBinU; ++u) agg_inc(hist, key[u], w0 + 32 * u + lane < n && key[u] < kKeyOutside, lane);
+  }
+  if (lane == 0) {
+    if (n_out) atomicAdd(&s_tail[0], n_out);
+    if (n_nonfin) atomicAdd(&s_tail[1], n_nonfin);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_tail[0]) atomicAdd(hist + kKeyOutside, s_tail[0]);
+    if (s_tail[1]) atomicAdd(hist + kKeyNonfinite, s_tail[1]);
   }
 }
 
