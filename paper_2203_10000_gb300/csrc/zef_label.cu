@@ -1029,37 +1029,54 @@ __device__ __noinline__ void rep_stream(const LabelArgs &a, const int2 *rng, int
 
 // Point-by-point sums over a range list of strip segments: chunks of
 // kWChunk entries (4 KB) gathered into the warp's double buffer by one or
-// more bulk copies on one mbarrier; every lane steps its points' windows
+// more bulk copies on one mbarrier (one range piece per lane, issued by the
+// lanes together); every lane steps its points' windows
 // through the entries, multiplies the (D + i N) factors of four consecutive
 // windows with wrap counting and takes one atan2 per four, the group sums
 // Kahan-compensated every kGroup entries.  A segment opens with a reset
 // entry at a multiple of four (every segment holds whole groups of four),
 // which restarts the windows at its vertex.
 template <int NA>
-__device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 *rng, int total, Entry *wbuf,
-                                                 uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane,
+__device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 *rng, int total, int nrng,
+                                                 Entry *wbuf, uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane,
                                                  PState (&st)[NA]) {
   const int nchunks = (total + kWChunk - 1) / kWChunk;
-  int fr = 0, fb = 0;  // lane 0's fill cursor over the ranges
+  int fr = 0, fb = 0;  // the warp's cursor over the ranges: range, its first flattened entry (every lane)
+  // Bulk copies of the flattened entries [j0, j1) into buffer b, issued by
+  // the lanes together: lane l copies its share of range fr + l (the flattened
+  // starts of 32 ranges at a time from a warp prefix sum of their lengths).
   auto fill = [&](int ch, int b) {
     const int j0 = ch * kWChunk, j1 = min(total, j0 + kWChunk);
-    tma_expect(&bar[b], (uint32_t)(j1 - j0) * (uint32_t)sizeof(Entry));
-    int j = j0;
-    while (j < j1) {
-      while (j >= fb + rng[fr].y) {
-        fb += rng[fr].y;
-        ++fr;
+    if (lane == 0) tma_expect(&bar[b], (uint32_t)(j1 - j0) * (uint32_t)sizeof(Entry));
+    __syncwarp();
+    for (;;) {
+      const int r = fr + lane;
+      const int c = r < nrng ? rng[r].y : 0;
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
       }
-      const int take = min(j1 - j, fb + rng[fr].y - j);
-      tma_copy_1d(wbuf + b * kWChunk + (j - j0), a.cseg + (rng[fr].x + (j - fb)),
-                  (uint32_t)take * (uint32_t)sizeof(Entry), &bar[b]);
-      j += take;
+      const int beg = fb + incl - c, end = beg + c;
+      const int s0 = max(beg, j0), s1 = min(end, j1);
+      if (s1 > s0)
+        tma_copy_1d(wbuf + b * kWChunk + (s0 - j0), a.cseg + (rng[r].x + (s0 - beg)),
+                    (uint32_t)(s1 - s0) * (uint32_t)sizeof(Entry), &bar[b]);
+      const uint32_t past = __ballot_sync(0xffffffffu, end > j1);
+      if (past) {  // the range holding entry j1 opens the next chunk
+        const int L = __ffs(past) - 1;
+        fb = __shfl_sync(0xffffffffu, beg, L);
+        fr += L;
+        break;
+      }
+      fb = __shfl_sync(0xffffffffu, end, 31);
+      fr += 32;
+      if (fb >= j1 || fr >= nrng) break;
     }
   };
-  if (lane == 0) {
-    if (nchunks > 0) fill(0, 0);
-    if (nchunks > 1) fill(1, 1);
-  }
+  if (nchunks > 0) fill(0, 0);
+  if (nchunks > 1) fill(1, 1);
 #pragma unroll
   for (int q = 0; q < NA; ++q) {
     st[q].grp = st[q].sum = st[q].comp = 0.f;
@@ -1134,7 +1151,7 @@ __device__ __forceinline__ bool stream_sums_caps(const LabelArgs &a, const int2 
     }
     }
     __syncwarp();  // every lane is done with buffer b before it is refilled
-    if (lane == 0 && ch + 2 < nchunks) fill(ch + 2, b);
+    if (ch + 2 < nchunks) fill(ch + 2, b);
   }
   if constexpr (NA == 2) {
     st[0].bad = st2.bad0;
@@ -1264,7 +1281,7 @@ template <int NA, int V, int P>
 __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, const float *thr, Entry *wbuf,
                                             uint64_t *bar, uint32_t &ph0, uint32_t &ph1, int lane, int base, int n,
                                             uint32_t act, uint32_t list, int m, uint32_t &done, const int2 *rng,
-                                            int rtotal, int rtris) {
+                                            int rtotal, int rtris, int nrng) {
   PState st[NA];
   int idx[NA];
   const int half = lane >> 4;
@@ -1281,7 +1298,7 @@ __device__ __noinline__ bool eval_groups(const LabelArgs &a, const DevComp *cp, 
     idx[j] = (valid && finite3(p.x, p.y, p.z)) ? i : -1;
   }
   if constexpr (V == 2) {
-    if (!stream_sums_caps<NA>(a, rng, rtotal, wbuf, bar, ph0, ph1, lane, st))
+    if (!stream_sums_caps<NA>(a, rng, rtotal, nrng, wbuf, bar, ph0, ph1, lane, st))
       return false;
   } else {
     if (!stream_sums<NA, V>(a, cp, wbuf, bar, ph0, ph1, lane, st)) return false;
@@ -1340,7 +1357,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
   __shared__ int2 s_rng[NW][RN];   // form 2: the tile's range list of the compartment
   constexpr int LN = V == 2 ? kMaxLeafRanges : 1;
   __shared__ int2 s_lrng[NW][LN];  // form 2: its leaf ranges alone
-  __shared__ int s_rtot[NW][4];
+  __shared__ int s_rtot[NW][5];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, half = lane >> 4;
   Entry *wbuf = reinterpret_cast<Entry *>(smem_raw) + wid * 2 * kWChunk;
   uint64_t *bar = bars[wid];
@@ -1424,7 +1441,7 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
       }
       // form 2: the strip entries (and their triangles) standing for the
       // surface near this tile
-      int rtotal = 0, rtris = 0;
+      int rtotal = 0, rtris = 0, nrng = 0;
       if constexpr (V == 2) {
         if (lane == 0) {
           int tot = 0, nt = 0, nl = 0, lt = 0;
@@ -1434,10 +1451,12 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
           s_rtot[wid][1] = nt;
           s_rtot[wid][2] = nl;
           s_rtot[wid][3] = lt;
+          s_rtot[wid][4] = nr;
         }
         __syncwarp();
         rtotal = s_rtot[wid][0];
         rtris = s_rtot[wid][1];
+        nrng = s_rtot[wid][4];
         uint32_t todo = 0;
 #pragma unroll
         for (int q = 0; q < P; ++q)
@@ -1675,10 +1694,10 @@ __global__ void __launch_bounds__(NT, label32_min_blocks<NT, P>()) k_label32(Lab
         if ((act >> g) & 1u) list |= (uint32_t)g << (4 * m++);
       bool ok = true;
       switch ((m + 1) >> 1) {
-        case 1: ok = eval_groups<1, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
-        case 2: ok = eval_groups<(P >= 2 ? 2 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
-        case 3: ok = eval_groups<(P >= 3 ? 3 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
-        default: ok = eval_groups<P, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris); break;
+        case 1: ok = eval_groups<1, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris, nrng); break;
+        case 2: ok = eval_groups<(P >= 2 ? 2 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris, nrng); break;
+        case 3: ok = eval_groups<(P >= 3 ? 3 : 1), V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris, nrng); break;
+        default: ok = eval_groups<P, V, P>(a, cp, thr, wbuf, bar, ph0, ph1, lane, base, n, act, list, m, done, s_rng[wid], rtotal, rtris, nrng); break;
       }
       if (!ok) {
         timed_out = true;

@@ -341,17 +341,35 @@ def test_small_and_pinched_surfaces(zef, oracle_mod, kernel, walk):
 
 
 def test_nonfinite_points(zef, oracle_mod):
+    """Non-finite points get label -1 and NaN solid angles, points outside
+    the surfaces' union box label 0 and Omega 0 (both decided by the key
+    pass, outside the sorted order), with and without Omega, from device and
+    from host buffers."""
     w = zs.config0()
     pts = w.points[:3000].copy()
     pts[5] = [np.nan, 0, 0]
     pts[77] = [0, np.inf, 0]
     pts[2999] = [0, 0, -np.inf]
+    outside = [10, 11, 2998]
+    pts[10] = [50, 0, 0]
+    pts[11] = [0, -40, 3]
+    pts[2998] = [1e30, 1e30, 1e30]
     ctx = make_ctx(zef, w.surfaces, w.priority)
     lab, om, st = gpu_label(ctx, pts)
     olab, oom = oracle_mod.label_points(pts, w.surfaces, w.priority)
     assert np.array_equal(lab, olab)
     assert st["nonfinite_points"] == 3
     assert lab[5] == -1 and lab[77] == -1 and lab[2999] == -1
+    assert np.all(np.isnan(om[:, [5, 77, 2999]]))
+    assert np.all(lab[outside] == 0) and np.all(om[:, outside] == 0)
+    fin = np.isfinite(oom)
+    assert np.abs(om.astype(np.float64)[fin] - oom[fin]).max() <= OMEGA_TOL
+    # labels alone (priority early exit), device and host buffers
+    p = torch.from_numpy(pts).cuda()
+    lab_d, _, _ = ctx.label_points(p)
+    torch.cuda.synchronize()
+    lab_h, _, _ = ctx.label_points(pts)
+    assert np.array_equal(lab_d.cpu().numpy(), olab) and np.array_equal(lab_h, olab)
 
 
 def test_deterministic(zef):
