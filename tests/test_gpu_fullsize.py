@@ -111,3 +111,29 @@ def test_ary_spheres_full_lattice(zef, oracle_mod):
                           np.random.default_rng(22).choice(np.nonzero(~known)[0], 3000, replace=False)])
     olab, _ = oracle_mod.label_points(w.points[idx], w.surfaces, w.priority)
     assert np.array_equal(lab[idx], olab)
+
+
+@pytest.mark.parametrize("cfg", ["config2", "config4"])
+def test_full_size_labels_equal_with_and_without_early_exit(zef, cfg):
+    """Every label of the labels-only call (priority early exit: a point
+    certainly inside a compartment skips the later ones, and a tile whose
+    points are all decided leaves the compartment loop) equals the label of
+    the call that requests Omega, which evaluates every compartment for
+    every tile."""
+    w = getattr(zs, cfg)()
+    ctx = zef.Context(0)
+    for s in w.surfaces:
+        ctx.add_compartment(s.id, s.verts, s.tris)
+    ctx.set_priority(w.priority)
+    pts = torch.from_numpy(w.points).cuda()
+    fast, _, st_fast = ctx.label_points(pts, want_omega=False)
+    torch.cuda.synchronize()
+    fast = fast.cpu().numpy()
+    full, om, st_full = ctx.label_points(pts, want_omega=True)
+    torch.cuda.synchronize()
+    full = full.cpu().numpy()
+    del om
+    assert np.array_equal(fast, full), np.nonzero(fast != full)[0][:20]
+    assert st_fast["pairs_evaluated"] < st_full["pairs_evaluated"]
+    assert st_fast["coherent_pairs"] > 0
+    ctx.close()
