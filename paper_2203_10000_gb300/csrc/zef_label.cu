@@ -941,8 +941,8 @@ __device__ __forceinline__ void window_prime(PState &s, float4 A, float4 B) {
 // per lane.  Each lane reads its own entries through the read-only cache
 // (its cursor over the ranges moves forward only): a warp finishes a run of
 // kWChunk entries about 32 times sooner than in the point-by-point sums, too
-// soon for the warp's bulk-copy pipeline, whose fills are issued by one lane,
-// to keep ahead of it.  The lanes' sums, wraps and conditioning minima are
+// soon for the warp's double-buffered bulk copies to keep ahead of it (the
+// passes spent most of their time waiting on them).  The lanes' sums, wraps and conditioning minima are
 // then combined and each representative is certified by the tests of
 // classify_store: bit r of *certain (r < nr) marks a certified
 // representative, its winding number in k[r].
