@@ -3,8 +3,10 @@
 // (Sec. 2.2.2).
 //
 // Both work on the mesh's unique edges, gathered once per call into a CSR
-// adjacency: every tet inserts its six edges into an open-addressing table,
-// the first insertion of a key counts the edge at both nodes, the degrees are
+// adjacency: every tet inserts its six edges into an open-addressing table
+// (an edge's probe starts in the run of slots of its lower node, so the
+// edges of nearby tets, which share nodes with nearby numbers, land in nearby
+// slots), the first insertion of a key counts the edge at both nodes, the degrees are
 // scanned into row offsets, the table's keys are scattered into the rows and
 // each row is sorted, so that every sum over a node's neighbours runs in
 // ascending neighbour order (deterministic results).
@@ -65,12 +67,19 @@ __device__ __forceinline__ unsigned long long pp_mix(unsigned long long x) {
 struct Adj {
   unsigned long long *keys;  // open-addressing table of edge keys (lo << 32 | hi)
   unsigned long long mask;   // table size - 1
+  int shift;                 // log2 of the slots per node (table size >= n << shift)
   uint32_t *deg;             // [n + 1] degrees, scanned into row offsets
   uint32_t *fill;            // [n] scatter cursors
   int32_t *nbr;              // [2 E] neighbours, rows sorted ascending
   int64_t n;
   int64_t *words;            // PpWord
 };
+
+// First probe of edge (lo, hi), lo < hi: a slot of lo's run of 2^shift slots,
+// picked by a hash of hi (linear probing from there may leave the run).
+__device__ __forceinline__ unsigned long long edge_slot(const Adj &g, uint32_t lo, uint32_t hi) {
+  return (((unsigned long long)lo << g.shift) | (pp_mix(hi) & ((1ull << g.shift) - 1ull))) & g.mask;
+}
 
 // every tet's six edges into the table; the first insertion counts the edge
 // in both end nodes' degrees (the edge count is half the degree sum)
@@ -93,7 +102,7 @@ __global__ void __launch_bounds__(256) k_pp_edges(Adj g, const int32_t *tets, in
       const uint32_t a = (uint32_t)v[kEdgeLocal[e][0]], b = (uint32_t)v[kEdgeLocal[e][1]];
       if (a == b) continue;
       const unsigned long long key = ((unsigned long long)min(a, b) << 32) | max(a, b);
-      unsigned long long h = pp_mix(key) & g.mask;
+      unsigned long long h = edge_slot(g, min(a, b), max(a, b));
       for (unsigned long long it = 0; it <= g.mask; ++it) {
         const unsigned long long prev = atomicCAS(g.keys + h, kNoKey, key);
         if (prev == kNoKey) {
@@ -112,7 +121,7 @@ __global__ void __launch_bounds__(256) k_pp_edges(Adj g, const int32_t *tets, in
 __device__ __forceinline__ void insert_edge(const Adj &g, uint32_t a, uint32_t b) {
   if (a == b) return;
   const unsigned long long key = ((unsigned long long)min(a, b) << 32) | max(a, b);
-  unsigned long long h = pp_mix(key) & g.mask;
+  unsigned long long h = edge_slot(g, min(a, b), max(a, b));
   for (unsigned long long it = 0; it <= g.mask; ++it) {
     const unsigned long long prev = atomicCAS(g.keys + h, kNoKey, key);
     if (prev == kNoKey) {
@@ -505,6 +514,13 @@ zef_status pp_grow(zef_ctx *ctx, int idx, size_t bytes) {
   return ZEF_OK;
 }
 
+// log2 of the table slots per node: the largest s with n 2^s <= cap
+int slot_shift(int64_t cap, int64_t n) {
+  int sh = 0;
+  while (sh < 40 && (std::max<int64_t>(n, 1) << (sh + 1)) <= cap) ++sh;
+  return sh;
+}
+
 // Unique-edge CSR of the tets (buffers 0-4 of pp_buf); synchronizes.
 zef_status build_adjacency(zef_ctx *ctx, const int32_t *tets, int64_t m, int64_t n, Adj *out, int64_t *edges) {
   int64_t cap = 1024;
@@ -518,6 +534,7 @@ zef_status build_adjacency(zef_ctx *ctx, const int32_t *tets, int64_t m, int64_t
   Adj g;
   g.keys = (unsigned long long *)ctx->pp_buf[0];
   g.mask = (unsigned long long)(cap - 1);
+  g.shift = slot_shift(cap, n);
   g.deg = (uint32_t *)ctx->pp_buf[1];
   g.fill = (uint32_t *)ctx->pp_buf[2];
   g.n = n;
@@ -644,6 +661,7 @@ zef_status build_surface_adjacency(zef_ctx *ctx, const int32_t *tets, const int3
   Adj g;
   g.keys = (unsigned long long *)ctx->pp_buf[0];
   g.mask = (unsigned long long)(cap - 1);
+  g.shift = slot_shift(cap, n);
   g.deg = (uint32_t *)ctx->pp_buf[1];
   g.fill = (uint32_t *)ctx->pp_buf[2];
   g.n = n;
